@@ -1,0 +1,206 @@
+/*
+ * pycool.h -- C ABI of the GB300-native symplectic lattice stepper.
+ *
+ * The library evolves N_f real scalar fields phi_i and their momenta pi_i on a
+ * periodic n^3 lattice in a flat FRW background (scale factor a, momentum
+ * p_a), with the split-Hamiltonian symplectic integrators of J. Sainio,
+ * "PyCOOL" (arXiv:1201.5029):
+ *   - the three exact sub-flows Phi_H1, Phi_H2, Phi_H3 (Sec. 2.3, Eq. split-Phi),
+ *   - composed into the second-order stage
+ *       Phi1(h/2) Phi2(h/2) Phi3(h) Phi2(h/2) Phi1(h/2)   (Sec. 2.3, after Eq. split-Phi),
+ *   - composed into orders 4 (triple jump, Eq. Phi-rec), 6 and 8 (Table 1).
+ * Time is conformal time; dt is the conformal step d-eta.
+ *
+ * Conventions shared by every call:
+ *   - Field arrays are float64, layout [field][z][y][x] (x fastest), n^3 sites
+ *     per field, N_f fields (1 or 2, fixed by the model).
+ *   - Every call returns a pycool_status and never aborts.  Asynchronous errors
+ *     (a CUDA fault, a non-finite lattice sum) are latched in the simulation and
+ *     returned by the next pycool_sync / pycool_energies / pycool_get_fields.
+ *     After PYCOOL_E_CUDA the simulation answers PYCOOL_E_STATE until destroyed.
+ *   - A simulation is used by one host thread at a time.  Server calls are
+ *     thread-safe.
+ *   - All device work of a simulation is ordered on the CUDA stream given at
+ *     creation; no call other than pycool_sync/energies/get_fields(host)/
+ *     field_stats blocks the host.
+ */
+#ifndef PYCOOL_H
+#define PYCOOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PYCOOL_MAX_FIELDS 2
+#define PYCOOL_MAX_PARAMS 8
+
+typedef struct pycool_sim pycool_sim;
+typedef struct pycool_server pycool_server;
+
+typedef enum {
+  PYCOOL_OK = 0,
+  PYCOOL_E_INVALID = 1,      /* bad argument or configuration                      */
+  PYCOOL_E_UNSTABLE_DT = 2,  /* dt breaks the linear stability bound at a = 1     */
+  PYCOOL_E_NOMEM = 3,        /* device or host allocation failed / budget exceeded */
+  PYCOOL_E_CUDA = 4,         /* a CUDA call failed; the simulation is poisoned    */
+  PYCOOL_E_NONFINITE = 5,    /* a lattice sum became NaN or Inf                   */
+  PYCOOL_E_TIMEOUT = 6,      /* a wait ran past its deadline                      */
+  PYCOOL_E_STATE = 7,        /* call not valid in the current state               */
+  PYCOOL_E_BUSY = 8,         /* server queue full                                 */
+  PYCOOL_E_NOT_FOUND = 9     /* unknown ticket                                    */
+} pycool_status;
+
+/* Potentials (Sec. 3).  params[] per model:
+ *   FREE     : V = m2/2 phi^2                                      {m2}
+ *   CHAOTIC2 : V = m2/2 phi^2 + g2/2 phi^2 chi^2   (Sec. 3.1)      {m2, g2}
+ *   OSCILLON : V = m2/2 phi^2 - lam/4 phi^4 + g/6 phi^6 (Sec. 3.2) {m2, lam, g}
+ *   QBALL    : V = m2 |Phi|^2 (1 + K ln(|Phi|^2/M^2)),
+ *              |Phi|^2 = (phi_1^2 + phi_2^2)/2          (Sec. 3.3) {m2, K, M}
+ * FREE and OSCILLON have one field; CHAOTIC2 and QBALL have two. */
+typedef enum {
+  PYCOOL_MODEL_FREE = 0,
+  PYCOOL_MODEL_CHAOTIC2 = 1,
+  PYCOOL_MODEL_OSCILLON = 2,
+  PYCOOL_MODEL_QBALL = 3
+} pycool_model;
+
+/* Arithmetic of the bulk sweep.
+ *   FP64       : fields, momenta and all arithmetic in float64.
+ *   SPLIT_FP32 : phi_i = phi0_i + dphi_i, pi_i = pi0_i + dpi_i with the lattice
+ *                means phi0, pi0 in float64 and the fluctuations dphi, dpi
+ *                stored and updated in float32; lattice sums, a and p_a in
+ *                float64 (the homogeneous/perturbation split of Sec. 2.2,
+ *                Eq. phi-lin, used here for precision, not linearisation). */
+typedef enum { PYCOOL_FP64 = 0, PYCOOL_SPLIT_FP32 = 1 } pycool_precision;
+
+/* Discrete Laplacian D of Sec. 2.1, Eq. D (its coefficients are not printed):
+ *   7PT   : c = (-6, 1, 0, 0) for (centre, face, edge, corner) neighbours,
+ *   ISO27 : c = (-128, 14, 3, 1)/30 (isotropic at O(k^4)). */
+typedef enum { PYCOOL_STENCIL_7PT = 7, PYCOOL_STENCIL_ISO27 = 27 } pycool_stencil;
+
+typedef struct {
+  int32_t n;          /* lattice side, 1 <= n <= 1024; S = V_L = n^3 (Sec. 2.1)       */
+  int32_t model;      /* pycool_model                                                */
+  int32_t order;      /* integrator order: 2, 4, 6 or 8                              */
+  int32_t precision;  /* pycool_precision                                            */
+  int32_t stencil;    /* pycool_stencil                                              */
+  int32_t reserved;   /* must be 0                                                   */
+  double L;           /* comoving box side; dx = L/n                                 */
+  double dt;          /* conformal time step d-eta; may be negative (time reversal)  */
+  double mpl;         /* reduced Planck mass in program units; +INF = static a       */
+  double rho_rad0;    /* homogeneous radiation density today-units (Eq. H2)          */
+  double rho_mat0;    /* homogeneous matter density (Eq. H2)                         */
+  double params[PYCOOL_MAX_PARAMS]; /* model parameters, see pycool_model            */
+} pycool_config;
+
+/* Observables at a synchronised state (all fields at the same time eta).
+ * rho_kin[i]  = sum pi_i^2 / (2 a^6 S)
+ * rho_grad[i] = -sum phi_i D[phi_i] / (2 a^2 dx^2 S)     (Stokes identity, Sec. 2.1)
+ * rho_pot     = sum V / S
+ * rho         = sum_i (rho_kin[i] + rho_grad[i]) + rho_pot         (Eq. rho-pres)
+ * P           = sum_i (rho_kin[i] - rho_grad[i]/3) - rho_pot       (Eq. rho-pres)
+ * H           = a'/a^2 = -p_a / (6 S m_pl^2 a^2)                    (Eq. a)
+ * residual    = |(rho + rho_rad0/a^4 + rho_mat0/a^3) / (3 m_pl^2 H^2) - 1|  (Eq. res-curv)
+ * mean[i], variance[i]: lattice mean and variance of phi_i. */
+typedef struct {
+  double eta, a, pa, H;
+  double rho_kin[PYCOOL_MAX_FIELDS];
+  double rho_grad[PYCOOL_MAX_FIELDS];
+  double rho_pot, rho, P, residual;
+  double mean[PYCOOL_MAX_FIELDS];
+  double variance[PYCOOL_MAX_FIELDS];
+  int64_t steps_done;   /* completed time steps since set_initial */
+  int64_t sweeps_done;  /* fused stage sweeps launched (one per Phi^(2) stage) */
+} pycool_observables;
+
+/* ---- single simulation ------------------------------------------------------ */
+
+/* Number of Phi^(2) stages per time step for an order (1, 3, 7, 15), or -1. */
+int pycool_stages_per_step(int32_t order);
+
+/* Stage weights w_1..w_s of one step in the order applied (Eq. Phi-rec for
+ * order 4, Table 1 for orders 6 and 8).  w must hold 15 doubles. */
+pycool_status pycool_stage_weights(int32_t order, double* w, int32_t* count);
+
+/* Bytes of device memory a simulation needs: state_bytes holds the field
+ * buffers and the background record, workspace_bytes the per-block partial
+ * sums of the reductions.  Returns E_INVALID for a bad config. */
+pycool_status pycool_query_bytes(const pycool_config* cfg, size_t* state_bytes,
+                                 size_t* workspace_bytes);
+
+/* Create a simulation of the problem of Sec. 3 ("model file": lattice n, box L,
+ * dt, potential, integrator order).
+ *   dev_state / dev_workspace : device buffers of at least the queried sizes,
+ *       256-byte aligned, owned by the caller and valid until pycool_destroy;
+ *       NULL = the library allocates (and frees) its own.
+ *   cuda_stream : cudaStream_t the simulation's work is ordered on (NULL = the
+ *       legacy default stream).  Not retained beyond the simulation's life.
+ * Checks the linear stability bound |h| omega_max < 2 at a = 1 for every stage
+ * weight (omega_max^2 = max|symbol of D|/dx^2 + m2) -> E_UNSTABLE_DT.
+ * The device must be current on the calling thread. */
+pycool_status pycool_create(const pycool_config* cfg, void* dev_state, void* dev_workspace,
+                            void* cuda_stream, pycool_sim** out);
+
+/* Initial fields and momenta, float64 [field][z][y][x], N_f n^3 values each.
+ * on_device != 0: phi and pi are device pointers (read on the stream).
+ * on_device == 0: host pointers, copied before the call returns.
+ * a0 > 0 is the initial scale factor.  pa0 = NaN: p_a is the negative root of
+ * the Hamiltonian constraint H = 0 (Eq. H2; expanding branch, p_a < 0, Eq. p-a);
+ * for mpl = +INF, p_a = 0.  For SPLIT_FP32 the lattice mean of each field is
+ * taken as the float64 background and the rest rounded to float32. */
+pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, const double* pi,
+                                 int on_device, double a0, double pa0);
+
+/* Advance by `steps` time steps of the chosen order (one fused sweep per
+ * Phi^(2) stage, then one drift-only sweep that synchronises phi with pi).
+ * Asynchronous: returns once the work is queued on the stream. */
+pycool_status pycool_evolve(pycool_sim* sim, int64_t steps);
+
+/* Wait until the simulation's queued work is done, at most timeout_s seconds
+ * (<0: no limit).  Returns a latched error if any, else E_TIMEOUT or OK. */
+pycool_status pycool_sync(pycool_sim* sim, double timeout_s);
+
+/* Synchronise, then fill *out with the observables of the current state. */
+pycool_status pycool_energies(pycool_sim* sim, pycool_observables* out);
+
+/* Mean and variance of field `field` at the current state (synchronises). */
+pycool_status pycool_field_stats(pycool_sim* sim, int32_t field, double* mean,
+                                 double* variance);
+
+/* Copy the current fields and momenta out, float64 [field][z][y][x]
+ * (SPLIT_FP32: phi0 + dphi evaluated in float64).  on_device as for
+ * set_initial; host copies synchronise first.  Either pointer may be NULL. */
+pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double* pi, int on_device);
+
+/* Checkpoint of a synchronised state: the background record (eta, a, p_a,
+ * step counters, split background phi0/pi0) and the current fields and
+ * momenta in the sweep's own precision.  pycool_checkpoint_size gives the
+ * byte count; save copies into a host buffer of at least that size
+ * (synchronises; E_STATE if work is pending); load restores it into a
+ * simulation created with the same config, so that evolving on continues bit
+ * for bit as the saved simulation would have. */
+pycool_status pycool_checkpoint_size(pycool_sim* sim, size_t* size);
+pycool_status pycool_checkpoint_save(pycool_sim* sim, void* buf, size_t cap);
+pycool_status pycool_checkpoint_load(pycool_sim* sim, const void* buf, size_t size);
+
+/* Replace the stream the simulation's work is ordered on (synchronises first). */
+pycool_status pycool_set_stream(pycool_sim* sim, void* cuda_stream);
+
+/* Number of this library's kernels the simulation has launched so far
+ * (sweeps, arming and conversion kernels), for accounting; -1 for NULL. */
+int64_t pycool_kernel_launches(const pycool_sim* sim);
+
+/* Release the simulation and whatever the library allocated for it.  Waits for
+ * the simulation's queued work first.  NULL is ignored. */
+void pycool_destroy(pycool_sim* sim);
+
+/* Static description of a status code. */
+const char* pycool_strerror(pycool_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PYCOOL_H */

@@ -1,1 +1,342 @@
-"""GB300-native symplectic lattice stepper (PyCOOL method, arXiv:1201.5029)."""
+"""GB300-native symplectic lattice stepper (the method of PyCOOL, arXiv:1201.5029).
+
+Thin ctypes binding over the C ABI declared in ``include/pycool.h``: the same
+function names, argument marshalling only.  Every step of the evolution runs
+in the CUDA kernels of ``libpycool.so``; there is no CPU fallback.  If the
+library has not been built, importing the binding raises.
+
+Host arrays are numpy float64 arrays of shape (N_f, n, n, n) ([field][z][y][x]);
+device arrays are CUDA torch tensors of the same shape and dtype (pass
+``on_device=True``).  PyTorch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpycool.so")
+
+MAX_FIELDS = 2
+MAX_PARAMS = 8
+
+# status codes (pycool_status)
+OK, E_INVALID, E_UNSTABLE_DT, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_BUSY, \
+    E_NOT_FOUND = range(10)
+# models, precisions, stencils
+MODEL_FREE, MODEL_CHAOTIC2, MODEL_OSCILLON, MODEL_QBALL = range(4)
+FP64, SPLIT_FP32 = 0, 1
+STENCIL_7PT, STENCIL_ISO27 = 7, 27
+IC_WHITE = 0
+
+MODELS = {"free": MODEL_FREE, "chaotic2": MODEL_CHAOTIC2, "oscillon": MODEL_OSCILLON,
+          "qball": MODEL_QBALL}
+MODEL_NF = {MODEL_FREE: 1, MODEL_CHAOTIC2: 2, MODEL_OSCILLON: 1, MODEL_QBALL: 2}
+PRECISIONS = {"fp64": FP64, "split_fp32": SPLIT_FP32}
+STENCILS = {"7pt": STENCIL_7PT, "iso27": STENCIL_ISO27}
+
+
+class pycool_config(C.Structure):
+    _fields_ = [("n", C.c_int32), ("model", C.c_int32), ("order", C.c_int32),
+                ("precision", C.c_int32), ("stencil", C.c_int32), ("reserved", C.c_int32),
+                ("L", C.c_double), ("dt", C.c_double), ("mpl", C.c_double),
+                ("rho_rad0", C.c_double), ("rho_mat0", C.c_double),
+                ("params", C.c_double * MAX_PARAMS)]
+
+
+class pycool_energies_t(C.Structure):
+    _fields_ = [("eta", C.c_double), ("a", C.c_double), ("pa", C.c_double), ("H", C.c_double),
+                ("rho_kin", C.c_double * MAX_FIELDS), ("rho_grad", C.c_double * MAX_FIELDS),
+                ("rho_pot", C.c_double), ("rho", C.c_double), ("P", C.c_double),
+                ("residual", C.c_double),
+                ("mean", C.c_double * MAX_FIELDS), ("variance", C.c_double * MAX_FIELDS),
+                ("steps_done", C.c_int64), ("sweeps_done", C.c_int64)]
+
+    def as_dict(self, nf: int = MAX_FIELDS) -> dict:
+        return dict(eta=self.eta, a=self.a, pa=self.pa, H=self.H,
+                    rho_kin=list(self.rho_kin)[:nf], rho_grad=list(self.rho_grad)[:nf],
+                    rho_pot=self.rho_pot, rho=self.rho, P=self.P, residual=self.residual,
+                    mean=list(self.mean)[:nf], variance=list(self.variance)[:nf],
+                    steps_done=self.steps_done, sweeps_done=self.sweeps_done)
+
+
+class pycool_ic(C.Structure):
+    _fields_ = [("background", C.c_double * MAX_FIELDS), ("momentum", C.c_double * MAX_FIELDS),
+                ("noise", C.c_double), ("a0", C.c_double)]
+
+
+class PycoolError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {pycool_strerror(status)} (status {status})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libpycool.so is not built ({LIB_PATH}); run "
+            "`python -m paper_1201_5029_gb300.build` (or __graft_entry__.build()) first")
+    lib = C.CDLL(LIB_PATH)
+    P, S = C.c_void_p, C.c_int
+    sig = {
+        "pycool_stages_per_step": (C.c_int, [C.c_int32]),
+        "pycool_stage_weights": (S, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+        "pycool_query_bytes": (S, [C.POINTER(pycool_config), C.POINTER(C.c_size_t),
+                                   C.POINTER(C.c_size_t)]),
+        "pycool_create": (S, [C.POINTER(pycool_config), P, P, P, C.POINTER(P)]),
+        "pycool_set_initial": (S, [P, P, P, C.c_int, C.c_double, C.c_double]),
+        "pycool_evolve": (S, [P, C.c_int64]),
+        "pycool_sync": (S, [P, C.c_double]),
+        "pycool_energies": (S, [P, C.POINTER(pycool_energies_t)]),
+        "pycool_field_stats": (S, [P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "pycool_get_fields": (S, [P, P, P, C.c_int]),
+        "pycool_checkpoint_size": (S, [P, C.POINTER(C.c_size_t)]),
+        "pycool_checkpoint_save": (S, [P, P, C.c_size_t]),
+        "pycool_checkpoint_load": (S, [P, P, C.c_size_t]),
+        "pycool_set_stream": (S, [P, P]),
+        "pycool_kernel_launches": (C.c_int64, [P]),
+        "pycool_destroy": (None, [P]),
+        "pycool_strerror": (C.c_char_p, [S]),
+        "pycool_server_create": (S, [C.c_size_t, C.c_int32, C.POINTER(P)]),
+        "pycool_server_submit": (S, [P, C.POINTER(pycool_config), C.POINTER(pycool_ic),
+                                     C.c_uint64, C.c_int64, C.POINTER(C.c_uint64)]),
+        "pycool_server_wait": (S, [P, C.c_uint64, C.c_double, C.POINTER(pycool_energies_t)]),
+        "pycool_server_stats": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "pycool_server_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise PycoolError(status, what)
+
+
+def _ptr(arr, on_device: bool):
+    if arr is None:
+        return None
+    if on_device:
+        return C.c_void_p(int(arr.data_ptr()))
+    a = np.ascontiguousarray(arr, dtype=np.float64)
+    return C.c_void_p(a.ctypes.data), a
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- config helpers
+
+def make_config(n: int, L: float, model, params: Sequence[float], dt: float, order: int = 2,
+                precision="fp64", stencil="7pt", mpl: float = 1.0, rho_rad0: float = 0.0,
+                rho_mat0: float = 0.0) -> pycool_config:
+    c = pycool_config()
+    c.n = int(n)
+    c.model = MODELS[model] if isinstance(model, str) else int(model)
+    c.order = int(order)
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    c.stencil = STENCILS[stencil] if isinstance(stencil, str) else int(stencil)
+    c.reserved = 0
+    c.L, c.dt, c.mpl = float(L), float(dt), float(mpl)
+    c.rho_rad0, c.rho_mat0 = float(rho_rad0), float(rho_mat0)
+    for i, p in enumerate(params):
+        c.params[i] = float(p)
+    return c
+
+
+def config_from_workload(w: dict, **over) -> pycool_config:
+    w = dict(w)
+    w.update(over)
+    return make_config(n=w["n"], L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+                       order=w["order"], precision=w.get("precision", "fp64"),
+                       stencil=w.get("stencil", "7pt"), mpl=w.get("mpl", 1.0),
+                       rho_rad0=w.get("rho_rad0", 0.0), rho_mat0=w.get("rho_mat0", 0.0))
+
+
+# ---------------------------------------------------------------- the C ABI, same names
+
+def pycool_strerror(status: int) -> str:
+    return lib.pycool_strerror(int(status)).decode()
+
+
+def pycool_stages_per_step(order: int) -> int:
+    return lib.pycool_stages_per_step(int(order))
+
+
+def pycool_stage_weights(order: int) -> list:
+    w = (C.c_double * 15)()
+    n = C.c_int32()
+    _check(lib.pycool_stage_weights(int(order), w, C.byref(n)), "pycool_stage_weights")
+    return list(w)[: n.value]
+
+
+def pycool_query_bytes(cfg: pycool_config) -> Tuple[int, int]:
+    s, w = C.c_size_t(), C.c_size_t()
+    _check(lib.pycool_query_bytes(C.byref(cfg), C.byref(s), C.byref(w)), "pycool_query_bytes")
+    return s.value, w.value
+
+
+def pycool_create(cfg: pycool_config, dev_state: Optional[int] = None,
+                  dev_workspace: Optional[int] = None, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib.pycool_create(C.byref(cfg), dev_state, dev_workspace, _stream_ptr(stream),
+                             C.byref(h)), "pycool_create")
+    return h
+
+
+def pycool_set_initial(sim, phi, pi, on_device: bool = False, a0: float = 1.0,
+                       pa0: float = math.nan) -> None:
+    if on_device:
+        _check(lib.pycool_set_initial(sim, _ptr(phi, True), _ptr(pi, True), 1, a0, pa0),
+               "pycool_set_initial")
+        return
+    p1, keep1 = _ptr(phi, False)
+    p2, keep2 = _ptr(pi, False)
+    _check(lib.pycool_set_initial(sim, p1, p2, 0, a0, pa0), "pycool_set_initial")
+
+
+def pycool_evolve(sim, steps: int) -> None:
+    _check(lib.pycool_evolve(sim, int(steps)), "pycool_evolve")
+
+
+def pycool_sync(sim, timeout_s: float = -1.0) -> int:
+    """Returns the status (OK, E_TIMEOUT, E_NONFINITE...) without raising."""
+    return lib.pycool_sync(sim, float(timeout_s))
+
+
+def pycool_energies(sim, nf: int = MAX_FIELDS) -> dict:
+    e = pycool_energies_t()
+    _check(lib.pycool_energies(sim, C.byref(e)), "pycool_energies")
+    return e.as_dict(nf)
+
+
+def pycool_field_stats(sim, field: int) -> Tuple[float, float]:
+    m, v = C.c_double(), C.c_double()
+    _check(lib.pycool_field_stats(sim, int(field), C.byref(m), C.byref(v)), "pycool_field_stats")
+    return m.value, v.value
+
+
+def pycool_get_fields(sim, phi=None, pi=None, on_device: bool = False, shape=None):
+    """Copy the current fields out.  Host: pass shape=(N_f, n, n, n) to get new
+    numpy arrays, or pass float64 arrays to fill.  Device: pass CUDA tensors."""
+    if on_device:
+        _check(lib.pycool_get_fields(sim, _ptr(phi, True) if phi is not None else None,
+                                     _ptr(pi, True) if pi is not None else None, 1),
+               "pycool_get_fields")
+        return phi, pi
+    if phi is None and shape is not None:
+        phi = np.empty(shape, dtype=np.float64)
+    if pi is None and shape is not None:
+        pi = np.empty(shape, dtype=np.float64)
+    for a in (phi, pi):
+        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+            raise ValueError("host arrays must be C-contiguous float64")
+    _check(lib.pycool_get_fields(sim, phi.ctypes.data if phi is not None else None,
+                                 pi.ctypes.data if pi is not None else None, 0),
+           "pycool_get_fields")
+    return phi, pi
+
+
+def pycool_checkpoint_size(sim) -> int:
+    s = C.c_size_t()
+    _check(lib.pycool_checkpoint_size(sim, C.byref(s)), "pycool_checkpoint_size")
+    return s.value
+
+
+def pycool_checkpoint_save(sim) -> bytes:
+    n = pycool_checkpoint_size(sim)
+    buf = C.create_string_buffer(n)
+    _check(lib.pycool_checkpoint_save(sim, buf, n), "pycool_checkpoint_save")
+    return buf.raw
+
+
+def pycool_checkpoint_load(sim, blob: bytes) -> None:
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib.pycool_checkpoint_load(sim, buf, len(blob)), "pycool_checkpoint_load")
+
+
+def pycool_set_stream(sim, stream) -> None:
+    _check(lib.pycool_set_stream(sim, _stream_ptr(stream)), "pycool_set_stream")
+
+
+def pycool_kernel_launches(sim) -> int:
+    return int(lib.pycool_kernel_launches(sim))
+
+
+def pycool_destroy(sim) -> None:
+    lib.pycool_destroy(sim)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class Simulation:
+    """A simulation as an object; each method is one C-ABI call."""
+
+    def __init__(self, cfg: pycool_config, stream=None, dev_state=None, dev_workspace=None):
+        self.cfg = cfg
+        self.nf = MODEL_NF[cfg.model]
+        self.n = cfg.n
+        self.shape = (self.nf, cfg.n, cfg.n, cfg.n)
+        self.handle = pycool_create(cfg, dev_state, dev_workspace, stream)
+
+    def set_initial(self, phi, pi, on_device=False, a0=1.0, pa0=math.nan):
+        pycool_set_initial(self.handle, phi, pi, on_device, a0, pa0)
+
+    def evolve(self, steps):
+        pycool_evolve(self.handle, steps)
+
+    def sync(self, timeout_s=-1.0):
+        return pycool_sync(self.handle, timeout_s)
+
+    def energies(self):
+        return pycool_energies(self.handle, self.nf)
+
+    def field_stats(self, field):
+        return pycool_field_stats(self.handle, field)
+
+    def get_fields(self, phi=None, pi=None, on_device=False):
+        return pycool_get_fields(self.handle, phi, pi, on_device, shape=self.shape)
+
+    def checkpoint(self) -> bytes:
+        return pycool_checkpoint_save(self.handle)
+
+    def restore(self, blob: bytes):
+        pycool_checkpoint_load(self.handle, blob)
+
+    def kernel_launches(self) -> int:
+        return pycool_kernel_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            pycool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,643 @@
+// Host runtime behind include/pycool.h: simulation objects, device memory
+// layout, CUDA-graph replay of the sweep chain, observables, checkpoints.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/pycool.h"
+#include "internal.cuh"
+#include "runtime.h"
+
+#define PYCOOL_API extern "C" __attribute__((visibility("default")))
+
+using namespace pycool;
+
+namespace pycool {
+
+// ---------------------------------------------------------------------------
+// Stage weights (Sec. 2.3): leapfrog; the triple jump of Eq. Phi-rec with
+// n = 1 for order 4; the symmetric compositions of Table 1 for orders 6 and 8
+// (w_1 outermost, centre = 1 - 2 sum of the listed weights).
+// ---------------------------------------------------------------------------
+int stage_table(int order, double* w) {
+  switch (order) {
+    case 2:
+      w[0] = 1.0;
+      return 1;
+    case 4: {
+      const double c = std::cbrt(2.0);
+      w[0] = w[2] = 1.0 / (2.0 - c);
+      w[1] = -c / (2.0 - c);
+      return 3;
+    }
+    case 6: {
+      static const double half[3] = {0.78451361047755726382, 0.23557321335935813368,
+                                     -1.17767998417887100695};
+      double s = 0.0;
+      for (int i = 0; i < 3; ++i) { w[i] = w[6 - i] = half[i]; s += half[i]; }
+      w[3] = 1.0 - 2.0 * s;
+      return 7;
+    }
+    case 8: {
+      static const double half[7] = {0.74167036435061295345,  -0.40910082580003159400,
+                                     0.19075471029623837995,  -0.57386247111608226666,
+                                     0.29906418130365592384,  0.33462491824529818378,
+                                     0.31529309239676659663};
+      double s = 0.0;
+      for (int i = 0; i < 7; ++i) { w[i] = w[14 - i] = half[i]; s += half[i]; }
+      w[7] = 1.0 - 2.0 * s;
+      return 15;
+    }
+    default:
+      return -1;
+  }
+}
+
+int model_nfields(int model) {
+  switch (model) {
+    case PYCOOL_MODEL_FREE: return 1;
+    case PYCOOL_MODEL_CHAOTIC2: return 2;
+    case PYCOOL_MODEL_OSCILLON: return 1;
+    case PYCOOL_MODEL_QBALL: return 2;
+    default: return -1;
+  }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout_for(const pycool_config& c) {
+  Layout L;
+  const int nf = model_nfields(c.model);
+  const size_t S = (size_t)c.n * c.n * c.n;
+  const size_t word = c.precision == PYCOOL_SPLIT_FP32 ? 4 : 8;
+  L.geo = choose_geometry(c.n);
+  L.field_bytes = align256((size_t)nf * S * word);
+  L.off_bg = 0;
+  L.off_desc = align256(sizeof(Background));
+  L.off_fields = L.off_desc + align256(sizeof(SimDesc));
+  L.state_bytes = L.off_fields + 4 * L.field_bytes;
+  L.off_ticket = 0;
+  L.off_partials = 256;
+  L.ws_bytes = L.off_partials + align256((size_t)L.geo.ncta * kNQ * sizeof(double));
+  return L;
+}
+
+pycool_status validate(const pycool_config* c) {
+  if (!c) return PYCOOL_E_INVALID;
+  if (c->n < 1 || c->n > 1024) return PYCOOL_E_INVALID;
+  if (model_nfields(c->model) < 0) return PYCOOL_E_INVALID;
+  if (c->order != 2 && c->order != 4 && c->order != 6 && c->order != 8) return PYCOOL_E_INVALID;
+  if (c->precision != PYCOOL_FP64 && c->precision != PYCOOL_SPLIT_FP32) return PYCOOL_E_INVALID;
+  if (c->stencil != PYCOOL_STENCIL_7PT && c->stencil != PYCOOL_STENCIL_ISO27)
+    return PYCOOL_E_INVALID;
+  if (c->reserved != 0) return PYCOOL_E_INVALID;
+  if (!(c->L > 0.0) || !std::isfinite(c->L)) return PYCOOL_E_INVALID;
+  if (!std::isfinite(c->dt) || c->dt == 0.0) return PYCOOL_E_INVALID;
+  if (!(c->mpl > 0.0)) return PYCOOL_E_INVALID;
+  if (!std::isfinite(c->rho_rad0) || !std::isfinite(c->rho_mat0)) return PYCOOL_E_INVALID;
+  for (int i = 0; i < PYCOOL_MAX_PARAMS; ++i)
+    if (!std::isfinite(c->params[i])) return PYCOOL_E_INVALID;
+  if (c->model == PYCOOL_MODEL_QBALL && !(c->params[2] > 0.0)) return PYCOOL_E_INVALID;
+  // linear stability of every stage at a = 1: |h| omega_max < 2,
+  // omega_max^2 = max|symbol of D| / dx^2 + |m2|  (7pt: 12, iso27: 92/15)
+  double w[kMaxStages];
+  const int s = stage_table(c->order, w);
+  double wmax = 0.0;
+  for (int i = 0; i < s; ++i) wmax = std::fmax(wmax, std::fabs(w[i]));
+  const double dx = c->L / c->n;
+  const double sym = c->stencil == PYCOOL_STENCIL_7PT ? 12.0 : 92.0 / 15.0;
+  const double om = std::sqrt(sym / (dx * dx) + std::fabs(c->params[0]));
+  if (std::fabs(c->dt) * wmax * om >= 2.0) return PYCOOL_E_UNSTABLE_DT;
+  return PYCOOL_OK;
+}
+
+void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state, char* ws) {
+  std::memset(&d, 0, sizeof(d));
+  d.n = c.n;
+  d.nf = model_nfields(c.model);
+  d.model = c.model;
+  d.stencil = c.stencil;
+  d.prec = c.precision == PYCOOL_SPLIT_FP32 ? PREC_SPLIT : PREC_FP64;
+  d.nstages = stage_table(c.order, d.w);
+  d.tx = L.geo.tx; d.ty = L.geo.ty; d.zc = L.geo.zc;
+  d.tiles_x = L.geo.tiles_x; d.tiles_y = L.geo.tiles_y;
+  d.zchunks = L.geo.zchunks; d.ncta = L.geo.ncta;
+  d.S = (int64_t)c.n * c.n * c.n;
+  d.dt = c.dt;
+  const double dx = c.L / c.n;
+  d.dx2inv = 1.0 / (dx * dx);
+  d.VL = (double)d.S;
+  const bool stat = std::isinf(c.mpl);
+  d.mpl2 = stat ? INFINITY : c.mpl * c.mpl;
+  d.inv6VLm2 = stat ? 0.0 : 1.0 / (6.0 * d.VL * d.mpl2);
+  d.rho_r0 = c.rho_rad0;
+  d.rho_m0 = c.rho_mat0;
+  for (int i = 0; i < 8; ++i) d.params[i] = c.params[i];
+  char* f = state + L.off_fields;
+  d.phi[0] = f;
+  d.phi[1] = f + L.field_bytes;
+  d.pi[0] = f + 2 * L.field_bytes;
+  d.pi[1] = f + 3 * L.field_bytes;
+  d.bg = (Background*)(state + L.off_bg);
+  d.ticket = (unsigned int*)(ws + L.off_ticket);
+  d.partials = (double*)(ws + L.off_partials);
+}
+
+cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s) {
+  if (d.prec == PREC_SPLIT) return launch_sweep_split(d.model, d.stencil, t, grid, s);
+  return launch_sweep_fp64(d.model, d.stencil, t, grid, s);
+}
+
+__global__ void arm_kernel(Background* bg, long long nsweeps) {
+  if (bg->error || bg->mode != MODE_IDLE || nsweeps <= 0) return;
+  bg->sweeps_left = nsweeps;
+  bg->mode = MODE_SWEEP;
+}
+
+__global__ void split_combine_kernel(const float* __restrict__ d, double base0, double base1,
+                                     double* __restrict__ out, long long S, int nf) {
+  const long long total = S * nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    out[i] = (i < S ? base0 : base1) + (double)d[i];
+  }
+}
+
+cudaError_t launch_arm(Background* bg, long long nsweeps, cudaStream_t s) {
+  arm_kernel<<<1, 1, 0, s>>>(bg, nsweeps);
+  return cudaGetLastError();
+}
+
+void observables(const Background& b, const SimDesc& d, double mpl, double rho_r0,
+                 double rho_m0, pycool_observables* out) {
+  std::memset(out, 0, sizeof(*out));
+  const double S = (double)d.S, a = b.a;
+  const double dx2 = 1.0 / d.dx2inv;
+  out->eta = b.eta;
+  out->a = a;
+  out->pa = b.pa;
+  double kin = 0.0, grad = 0.0;
+  for (int f = 0; f < d.nf; ++f) {
+    out->rho_kin[f] = b.s_pi2[f] / (2.0 * std::pow(a, 6) * S);
+    out->rho_grad[f] = -b.s_phiD[f] / (2.0 * a * a * dx2 * S);
+    out->mean[f] = b.mean[f];
+    out->variance[f] = b.var[f];
+    kin += out->rho_kin[f];
+    grad += out->rho_grad[f];
+  }
+  out->rho_pot = b.s_V / S;
+  out->rho = kin + grad + out->rho_pot;
+  out->P = kin - grad / 3.0 - out->rho_pot;
+  if (std::isinf(mpl)) {
+    out->H = 0.0;
+    out->residual = NAN;
+  } else {
+    out->H = -b.pa / (6.0 * S * mpl * mpl * a * a);
+    const double rt = out->rho + rho_r0 / std::pow(a, 4) + rho_m0 / (a * a * a);
+    out->residual = std::fabs(rt / (3.0 * mpl * mpl * out->H * out->H) - 1.0);
+  }
+  out->steps_done = b.steps_done;
+  out->sweeps_done = b.sweeps_done;
+}
+
+}  // namespace pycool
+
+// ---------------------------------------------------------------------------
+// Simulation object
+// ---------------------------------------------------------------------------
+struct pycool_sim {
+  pycool_config cfg{};
+  Layout L{};
+  SimDesc hdesc{};
+  int nf = 0, nstages = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  char* state = nullptr;
+  char* ws = nullptr;
+  bool own_state = false, own_ws = false;
+  SimDesc* d_desc = nullptr;
+  Background* d_bg = nullptr;
+  LaunchTable table{};
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  cudaEvent_t done = nullptr;
+  bool initialised = false;
+  bool poisoned = false;
+  int64_t launches = 0;
+};
+
+static constexpr int kGraphLen = 16;
+
+static pycool_status cuda_fail(pycool_sim* s, cudaError_t e, const char* what) {
+  if (s) s->poisoned = true;
+  std::fprintf(stderr, "pycool: CUDA error in %s: %s\n", what, cudaGetErrorString(e));
+  return PYCOOL_E_CUDA;
+}
+
+#define CK(call)                                                     \
+  do {                                                               \
+    cudaError_t e__ = (call);                                        \
+    if (e__ != cudaSuccess) return cuda_fail(sim, e__, #call);       \
+  } while (0)
+
+PYCOOL_API int pycool_stages_per_step(int32_t order) {
+  double w[kMaxStages];
+  return stage_table(order, w);
+}
+
+PYCOOL_API pycool_status pycool_stage_weights(int32_t order, double* w, int32_t* count) {
+  if (!w || !count) return PYCOOL_E_INVALID;
+  const int s = stage_table(order, w);
+  if (s < 0) return PYCOOL_E_INVALID;
+  *count = s;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_query_bytes(const pycool_config* cfg, size_t* state_bytes,
+                                            size_t* workspace_bytes) {
+  const pycool_status st = validate(cfg);
+  if (st != PYCOOL_OK) return st;
+  const Layout L = layout_for(*cfg);
+  if (state_bytes) *state_bytes = L.state_bytes;
+  if (workspace_bytes) *workspace_bytes = L.ws_bytes;
+  return PYCOOL_OK;
+}
+
+static pycool_status build_graph(pycool_sim* sim) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < kGraphLen && le == cudaSuccess; ++i)
+    le = launch_sweep(sim->hdesc, sim->table, sim->L.geo.ncta, sim->cap_stream);
+  cudaError_t ee = cudaStreamEndCapture(sim->cap_stream, &g);
+  if (le != cudaSuccess) return cuda_fail(sim, le, "capture launch");
+  if (ee != cudaSuccess) return cuda_fail(sim, ee, "cudaStreamEndCapture");
+  cudaError_t ie = cudaGraphInstantiate(&sim->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return cuda_fail(sim, ie, "cudaGraphInstantiate");
+  sim->graph_len = kGraphLen;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state,
+                                       void* dev_workspace, void* cuda_stream,
+                                       pycool_sim** out) {
+  if (!out) return PYCOOL_E_INVALID;
+  *out = nullptr;
+  pycool_status st = validate(cfg);
+  if (st != PYCOOL_OK) return st;
+  if (((uintptr_t)dev_state & 255) || ((uintptr_t)dev_workspace & 255)) return PYCOOL_E_INVALID;
+  pycool_sim* sim = new (std::nothrow) pycool_sim();
+  if (!sim) return PYCOOL_E_NOMEM;
+  sim->cfg = *cfg;
+  sim->L = layout_for(*cfg);
+  sim->nf = model_nfields(cfg->model);
+  sim->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&sim->device);
+  if (e != cudaSuccess) { delete sim; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+  sim->state = (char*)dev_state;
+  sim->ws = (char*)dev_workspace;
+  if (!sim->state) {
+    if (cudaMalloc((void**)&sim->state, sim->L.state_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete sim;
+      return PYCOOL_E_NOMEM;
+    }
+    sim->own_state = true;
+  }
+  if (!sim->ws) {
+    if (cudaMalloc((void**)&sim->ws, sim->L.ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      if (sim->own_state) cudaFree(sim->state);
+      delete sim;
+      return PYCOOL_E_NOMEM;
+    }
+    sim->own_ws = true;
+  }
+  fill_desc(sim->hdesc, *cfg, sim->L, sim->state, sim->ws);
+  sim->nstages = sim->hdesc.nstages;
+  sim->d_desc = (SimDesc*)(sim->state + sim->L.off_desc);
+  sim->d_bg = (Background*)(sim->state + sim->L.off_bg);
+  Background b;
+  std::memset(&b, 0, sizeof(b));
+  b.a = 1.0;
+  b.mode = MODE_IDLE;
+  st = PYCOOL_OK;
+  do {
+    if ((e = cudaMemcpyAsync(sim->d_desc, &sim->hdesc, sizeof(SimDesc), cudaMemcpyHostToDevice,
+                             sim->stream)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream)) !=
+        cudaSuccess) break;
+    if ((e = cudaMemsetAsync(sim->ws, 0, sim->L.ws_bytes, sim->stream)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(sim->stream)) != cudaSuccess) break;
+    if ((e = cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      break;
+    if ((e = cudaEventCreateWithFlags(&sim->done, cudaEventDisableTiming)) != cudaSuccess) break;
+  } while (0);
+  if (e != cudaSuccess) {
+    cuda_fail(sim, e, "pycool_create");
+    pycool_destroy(sim);
+    return PYCOOL_E_CUDA;
+  }
+  sim->table.count = 1;
+  sim->table.cta_offset[0] = 0;
+  sim->table.cta_offset[1] = sim->L.geo.ncta;
+  sim->table.desc[0] = sim->d_desc;
+  st = build_graph(sim);
+  if (st != PYCOOL_OK) {
+    pycool_destroy(sim);
+    return st;
+  }
+  *out = sim;
+  return PYCOOL_OK;
+}
+
+static pycool_status read_bg(pycool_sim* sim, Background* b) {
+  CK(cudaMemcpyAsync(b, sim->d_bg, sizeof(Background), cudaMemcpyDeviceToHost, sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  return PYCOOL_OK;
+}
+
+static pycool_status launch_one(pycool_sim* sim) {
+  CK(launch_sweep(sim->hdesc, sim->table, sim->L.geo.ncta, sim->stream));
+  sim->launches += 1;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, const double* pi,
+                                            int on_device, double a0, double pa0) {
+  if (!sim || !phi || !pi) return PYCOOL_E_INVALID;
+  if (sim->poisoned) return PYCOOL_E_STATE;
+  if (!(a0 > 0.0) || !std::isfinite(a0)) return PYCOOL_E_INVALID;
+  const size_t S = (size_t)sim->hdesc.S;
+  const int nf = sim->nf;
+  const size_t count = (size_t)nf * S;
+  Background b;
+  std::memset(&b, 0, sizeof(b));
+  b.a = a0;
+  b.init_pa = std::isnan(pa0) ? 1 : 0;
+  b.pa = std::isnan(pa0) ? 0.0 : pa0;
+  b.mode = MODE_FLUSH;  // the first launch only reduces (h_prev = 0 -> no drift)
+  b.cur = 0;
+  CK(cudaStreamSynchronize(sim->stream));
+  if (sim->hdesc.prec == PREC_FP64) {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(sim->hdesc.phi[0], phi, count * sizeof(double), kind, sim->stream));
+    CK(cudaMemcpyAsync(sim->hdesc.pi[0], pi, count * sizeof(double), kind, sim->stream));
+    for (int f = 0; f < nf; ++f) {
+      double v = 0.0;
+      if (on_device)
+        CK(cudaMemcpy(&v, phi + (size_t)f * S, sizeof(double), cudaMemcpyDeviceToHost));
+      else
+        v = phi[(size_t)f * S];
+      b.shift[f] = v;
+    }
+  } else {
+    // split form: phi0 = lattice mean (float64), dphi = phi - phi0 in float32
+    std::vector<double> hphi, hpi;
+    const double* sp = phi;
+    const double* sq = pi;
+    if (on_device) {
+      hphi.resize(count);
+      hpi.resize(count);
+      CK(cudaMemcpy(hphi.data(), phi, count * sizeof(double), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(hpi.data(), pi, count * sizeof(double), cudaMemcpyDeviceToHost));
+      sp = hphi.data();
+      sq = hpi.data();
+    }
+    std::vector<float> dphi(count), dpi(count);
+    for (int f = 0; f < nf; ++f) {
+      for (int which = 0; which < 2; ++which) {
+        const double* src = (which == 0 ? sp : sq) + (size_t)f * S;
+        double s = 0.0, comp = 0.0;
+        for (size_t i = 0; i < S; ++i) {
+          const double x = src[i], t = s + x;
+          comp += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
+          s = t;
+        }
+        const double mean = (s + comp) / (double)S;
+        float* dst = (which == 0 ? dphi.data() : dpi.data()) + (size_t)f * S;
+        for (size_t i = 0; i < S; ++i) dst[i] = (float)(src[i] - mean);
+        if (which == 0) b.phi0[f] = mean; else b.pi0[f] = mean;
+      }
+    }
+    CK(cudaMemcpy(sim->hdesc.phi[0], dphi.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sim->hdesc.pi[0], dpi.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
+  CK(cudaMemsetAsync(sim->hdesc.ticket, 0, sizeof(unsigned int), sim->stream));
+  pycool_status st = launch_one(sim);
+  if (st != PYCOOL_OK) return st;
+  CK(cudaEventRecord(sim->done, sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  sim->initialised = true;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_evolve(pycool_sim* sim, int64_t steps) {
+  if (!sim || steps < 0) return PYCOOL_E_INVALID;
+  if (sim->poisoned) return PYCOOL_E_STATE;
+  if (!sim->initialised) return PYCOOL_E_STATE;
+  if (steps == 0) return PYCOOL_OK;
+  const long long nsweeps = (long long)steps * sim->nstages;
+  CK(launch_arm(sim->d_bg, nsweeps, sim->stream));
+  sim->launches += 1;
+  long long left = nsweeps + 1;  // + the synchronising flush
+  while (left >= sim->graph_len) {
+    CK(cudaGraphLaunch(sim->graph, sim->stream));
+    sim->launches += sim->graph_len;
+    left -= sim->graph_len;
+  }
+  for (; left > 0; --left) {
+    pycool_status st = launch_one(sim);
+    if (st != PYCOOL_OK) return st;
+  }
+  CK(cudaEventRecord(sim->done, sim->stream));
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_sync(pycool_sim* sim, double timeout_s) {
+  if (!sim) return PYCOOL_E_INVALID;
+  if (sim->poisoned) return PYCOOL_E_STATE;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(sim->done);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return cuda_fail(sim, q, "cudaEventQuery");
+    if (timeout_s >= 0.0) {
+      const double el =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_s) return PYCOOL_E_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  Background b;
+  pycool_status st = read_bg(sim, &b);
+  if (st != PYCOOL_OK) return st;
+  if (b.error) return PYCOOL_E_NONFINITE;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_energies(pycool_sim* sim, pycool_observables* out) {
+  if (!sim || !out) return PYCOOL_E_INVALID;
+  if (!sim->initialised) return PYCOOL_E_STATE;
+  pycool_status st = pycool_sync(sim, -1.0);
+  if (st != PYCOOL_OK) return st;
+  Background b;
+  st = read_bg(sim, &b);
+  if (st != PYCOOL_OK) return st;
+  observables(b, sim->hdesc, sim->cfg.mpl, sim->cfg.rho_rad0, sim->cfg.rho_mat0, out);
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_field_stats(pycool_sim* sim, int32_t field, double* mean,
+                                            double* variance) {
+  if (!sim || field < 0 || field >= sim->nf) return PYCOOL_E_INVALID;
+  pycool_observables e;
+  pycool_status st = pycool_energies(sim, &e);
+  if (st != PYCOOL_OK) return st;
+  if (mean) *mean = e.mean[field];
+  if (variance) *variance = e.variance[field];
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double* pi,
+                                           int on_device) {
+  if (!sim) return PYCOOL_E_INVALID;
+  if (!sim->initialised) return PYCOOL_E_STATE;
+  pycool_status st = pycool_sync(sim, -1.0);
+  if (st != PYCOOL_OK && st != PYCOOL_E_NONFINITE) return st;
+  Background b;
+  st = read_bg(sim, &b);
+  if (st != PYCOOL_OK) return st;
+  const size_t S = (size_t)sim->hdesc.S;
+  const size_t count = (size_t)sim->nf * S;
+  const void* src_phi = sim->hdesc.phi[b.cur & 1];
+  const void* src_pi = sim->hdesc.pi[(b.cur >> 1) & 1];
+  if (sim->hdesc.prec == PREC_FP64) {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (phi) CK(cudaMemcpyAsync(phi, src_phi, count * sizeof(double), kind, sim->stream));
+    if (pi) CK(cudaMemcpyAsync(pi, src_pi, count * sizeof(double), kind, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    return b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK;
+  }
+  // split: phi0 + dphi evaluated in float64
+  for (int which = 0; which < 2; ++which) {
+    double* dst = which == 0 ? phi : pi;
+    if (!dst) continue;
+    const float* src = (const float*)(which == 0 ? src_phi : src_pi);
+    const double* base = which == 0 ? b.phi0 : b.pi0;
+    if (on_device) {
+      split_combine_kernel<<<1024, 256, 0, sim->stream>>>(src, base[0], base[1], dst,
+                                                          (long long)S, sim->nf);
+      CK(cudaGetLastError());
+      sim->launches += 1;
+      CK(cudaStreamSynchronize(sim->stream));
+    } else {
+      std::vector<float> tmp(count);
+      CK(cudaMemcpyAsync(tmp.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost,
+                         sim->stream));
+      CK(cudaStreamSynchronize(sim->stream));
+      for (int f = 0; f < sim->nf; ++f)
+        for (size_t i = 0; i < S; ++i) dst[(size_t)f * S + i] = base[f] + (double)tmp[(size_t)f * S + i];
+    }
+  }
+  return b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_checkpoint_size(pycool_sim* sim, size_t* size) {
+  if (!sim || !size) return PYCOOL_E_INVALID;
+  const size_t word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  *size = sizeof(Background) + 2 * (size_t)sim->nf * (size_t)sim->hdesc.S * word;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_checkpoint_save(pycool_sim* sim, void* buf, size_t cap) {
+  if (!sim || !buf) return PYCOOL_E_INVALID;
+  if (!sim->initialised) return PYCOOL_E_STATE;
+  size_t need = 0;
+  pycool_checkpoint_size(sim, &need);
+  if (cap < need) return PYCOOL_E_INVALID;
+  pycool_status st = pycool_sync(sim, -1.0);
+  if (st != PYCOOL_OK) return st;
+  Background b;
+  st = read_bg(sim, &b);
+  if (st != PYCOOL_OK) return st;
+  if (b.mode != MODE_IDLE) return PYCOOL_E_STATE;
+  const size_t word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  const size_t fb = (size_t)sim->nf * (size_t)sim->hdesc.S * word;
+  char* p = (char*)buf;
+  std::memcpy(p, &b, sizeof(b));
+  CK(cudaMemcpy(p + sizeof(b), sim->hdesc.phi[b.cur & 1], fb, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(p + sizeof(b) + fb, sim->hdesc.pi[(b.cur >> 1) & 1], fb, cudaMemcpyDeviceToHost));
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_checkpoint_load(pycool_sim* sim, const void* buf, size_t size) {
+  if (!sim || !buf) return PYCOOL_E_INVALID;
+  if (sim->poisoned) return PYCOOL_E_STATE;
+  size_t need = 0;
+  pycool_checkpoint_size(sim, &need);
+  if (size != need) return PYCOOL_E_INVALID;
+  Background b;
+  std::memcpy(&b, buf, sizeof(b));
+  if (b.mode != MODE_IDLE || b.error) return PYCOOL_E_INVALID;
+  const size_t word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  const size_t fb = (size_t)sim->nf * (size_t)sim->hdesc.S * word;
+  const char* p = (const char*)buf;
+  CK(cudaStreamSynchronize(sim->stream));
+  CK(cudaMemcpy(sim->hdesc.phi[b.cur & 1], p + sizeof(b), fb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->hdesc.pi[(b.cur >> 1) & 1], p + sizeof(b) + fb, fb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice));
+  CK(cudaMemset(sim->hdesc.ticket, 0, sizeof(unsigned int)));
+  CK(cudaEventRecord(sim->done, sim->stream));
+  sim->initialised = true;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API int64_t pycool_kernel_launches(const pycool_sim* sim) {
+  return sim ? sim->launches : -1;
+}
+
+PYCOOL_API pycool_status pycool_set_stream(pycool_sim* sim, void* cuda_stream) {
+  if (!sim) return PYCOOL_E_INVALID;
+  pycool_status st = pycool_sync(sim, -1.0);
+  if (st != PYCOOL_OK && st != PYCOOL_E_NONFINITE && st != PYCOOL_E_STATE) return st;
+  sim->stream = (cudaStream_t)cuda_stream;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API void pycool_destroy(pycool_sim* sim) {
+  if (!sim) return;
+  cudaStreamSynchronize(sim->stream);
+  if (sim->graph) cudaGraphExecDestroy(sim->graph);
+  if (sim->done) cudaEventDestroy(sim->done);
+  if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
+  if (sim->own_state && sim->state) cudaFree(sim->state);
+  if (sim->own_ws && sim->ws) cudaFree(sim->ws);
+  cudaGetLastError();
+  delete sim;
+}
+
+PYCOOL_API const char* pycool_strerror(pycool_status s) {
+  switch (s) {
+    case PYCOOL_OK: return "ok";
+    case PYCOOL_E_INVALID: return "invalid argument or configuration";
+    case PYCOOL_E_UNSTABLE_DT: return "time step breaks the linear stability bound";
+    case PYCOOL_E_NOMEM: return "out of memory";
+    case PYCOOL_E_CUDA: return "CUDA error (simulation poisoned)";
+    case PYCOOL_E_NONFINITE: return "non-finite lattice sum (evolution stopped)";
+    case PYCOOL_E_TIMEOUT: return "timed out";
+    case PYCOOL_E_STATE: return "call not valid in the current state";
+    case PYCOOL_E_BUSY: return "busy";
+    case PYCOOL_E_NOT_FOUND: return "unknown ticket";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,104 @@
+// Device-side records shared by the sweep kernels and the host runtime.
+//
+// One simulation = one SimDesc (immutable, device memory) + one Background
+// (mutable, device memory) + double-buffered field arrays + a partial-sum
+// workspace.  Every sweep kernel reads its simulation's Background at start,
+// streams its tile, writes one partial per reduced quantity, and the last
+// block to finish (atomic ticket, no spin-wait) folds the partials in a fixed
+// order and advances the Background.  So a whole evolve() is a chain of
+// identical launches with no host round trip, and replays as a CUDA graph.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pycool {
+
+constexpr int kMaxFields = 2;
+constexpr int kMaxStages = 15;
+constexpr int kThreads = 256;      // threads per block, every kernel
+constexpr int kMaxTX = 32;         // tile width (x, contiguous)
+constexpr int kMaxTY = 8;          // tile height (y)
+constexpr int kNQ = 12;            // reduction slots per block
+constexpr int kMaxMembers = 64;    // simulations per batched launch
+
+enum Mode : int32_t { MODE_IDLE = 0, MODE_SWEEP = 1, MODE_FLUSH = 2 };
+enum Prec : int32_t { PREC_FP64 = 0, PREC_SPLIT = 1 };
+
+// Mutable background record.  a, p_a, eta and the pending half-stage are the
+// scalar part of the state (Sec. 2.3, Eq. split-Phi: Phi_H1 moves a, Phi_H2 and
+// Phi_H3 kick p_a).  Between two sweeps the state is "staggered": the trailing
+// Phi_H2(h/2) Phi_H1(h/2) of the last stage (step h_prev) is still pending and
+// is applied, merged with the next stage's leading Phi_H1 Phi_H2, at the start
+// of the next sweep.
+struct alignas(16) Background {
+  double a, pa, eta;
+  double sum_pi2;            // sum over fields and sites of pi^2 (current pi)
+  double h_prev;             // pending half-stage step; 0 = synchronised
+  int64_t stage;             // stage-table index of the next sweep
+  int64_t sweeps_left;       // sweeps before the synchronising flush
+  int64_t sweeps_done, steps_done;
+  int32_t mode;              // Mode
+  int32_t cur;               // bit 0: buffer holding phi, bit 1: buffer holding pi
+  int32_t error;             // 1: a lattice sum was not finite (evolution stopped)
+  int32_t init_pa;           // 1: the next flush sets p_a from H = 0
+  // Sums of the last flush (synchronised state), per field.
+  double s_pi2[kMaxFields], s_phiD[kMaxFields], s_V;
+  double mean[kMaxFields], var[kMaxFields];         // field mean and variance
+  double shift[kMaxFields];                         // FP64 form: shift K of the variance sums
+  // Split form: lattice-mean background and pending re-centring shifts.
+  double phi0[kMaxFields], pi0[kMaxFields];
+  double mu_phi[kMaxFields], mu_pi[kMaxFields];
+  double pad[4];
+};
+
+struct alignas(16) SimDesc {
+  int32_t n, nf, model, stencil, prec, nstages;
+  int32_t tx, ty, zc, tiles_x, tiles_y, zchunks, ncta, pad0;
+  int64_t S;                  // n^3
+  double dt, dx2inv, VL, inv6VLm2, mpl2, rho_r0, rho_m0;
+  double params[8];
+  double w[kMaxStages];
+  void* phi[2];
+  void* pi[2];
+  double* partials;           // ncta * kNQ
+  unsigned int* ticket;
+  Background* bg;
+};
+
+struct LaunchTable {
+  int32_t count;
+  int32_t cta_offset[kMaxMembers + 1];
+  const SimDesc* desc[kMaxMembers];
+};
+
+// Geometry of the z-streamed tiling, a function of n alone (so the reduction
+// order of a lattice does not depend on what it is batched with).
+struct Geometry {
+  int tx, ty, zc, tiles_x, tiles_y, zchunks, ncta;
+};
+
+inline Geometry choose_geometry(int n) {
+  Geometry g;
+  g.tx = n >= kMaxTX ? kMaxTX : n;
+  g.ty = n >= kMaxTY ? kMaxTY : n;
+  g.tiles_x = (n + g.tx - 1) / g.tx;
+  g.tiles_y = (n + g.ty - 1) / g.ty;
+  const int tiles = g.tiles_x * g.tiles_y;
+  const int target = 2 * 152;  // at least two waves on 152 SMs when possible
+  int zc = 64;
+  while (zc > 4 && (long long)tiles * ((n + zc - 1) / zc) < target) zc /= 2;
+  if (zc > n) zc = n;
+  g.zc = zc;
+  g.zchunks = (n + zc - 1) / zc;
+  g.ncta = tiles * g.zchunks;
+  return g;
+}
+
+// Launchers (one translation unit per precision).
+cudaError_t launch_sweep_fp64(int model, int stencil, const LaunchTable& t, int grid,
+                              cudaStream_t s);
+cudaError_t launch_sweep_split(int model, int stencil, const LaunchTable& t, int grid,
+                               cudaStream_t s);
+
+}  // namespace pycool

@@ -1,0 +1,192 @@
+// Potentials of the three models of Sec. 3 (plus a free massive field), on the
+// device.  Written independently of the CPU oracle.
+//
+//   FREE     V = m2/2 phi^2                                    p = {m2}
+//   CHAOTIC2 V = m2/2 phi^2 + g2/2 phi^2 chi^2      (Sec. 3.1)  p = {m2, g2}
+//   OSCILLON V = m2/2 phi^2 - lam/4 phi^4 + g/6 phi^6 (Sec. 3.2) p = {m2, lam, g}
+//   QBALL    V = m2 u (1 + K ln(u/M^2)), u = |Phi|^2 = (phi1^2 + phi2^2)/2
+//                                                    (Sec. 3.3)  p = {m2, K, M}
+//
+// Pot<M>::eval gives V and dV/dphi_i in float64.  Pot<M>::SplitK / diff give,
+// in float32, the differences dV'_i = V'_i(phi0 + d) - V'_i(phi0) and
+// dV = V(phi0 + d) - V(phi0) around a float64 background phi0, written so that
+// every term carries at least one factor of d (no cancellation for small d):
+// this is the bulk arithmetic of the split-FP32 form, where phi = phi0 + d
+// (the homogeneous/perturbation split of Sec. 2.2, Eq. phi-lin).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pycool {
+
+enum ModelId { M_FREE = 0, M_CHAOTIC2 = 1, M_OSCILLON = 2, M_QBALL = 3 };
+
+template <int M> struct Pot;
+
+// ---------------------------------------------------------------- FREE
+template <> struct Pot<M_FREE> {
+  static constexpr int NF = 1;
+  struct K { double m2, hm2; };
+  __device__ static K prep(const double* p) { return K{p[0], 0.5 * p[0]}; }
+  __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
+    dV[0] = k.m2 * f[0];
+    V = k.hm2 * f[0] * f[0];
+  }
+  struct SplitK { float m2, hm2, p0, two_p0; };
+  __device__ static SplitK split_prep(const double* p, const double* phi0) {
+    return SplitK{(float)p[0], (float)(0.5 * p[0]), (float)phi0[0], (float)(2.0 * phi0[0])};
+  }
+  __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {
+    dVd[0] = k.m2 * d[0];
+    dVv = k.hm2 * (d[0] * (k.two_p0 + d[0]));
+  }
+};
+
+// ---------------------------------------------------------------- CHAOTIC2
+template <> struct Pot<M_CHAOTIC2> {
+  static constexpr int NF = 2;
+  struct K { double m2, g2; };
+  __device__ static K prep(const double* p) { return K{p[0], p[1]}; }
+  __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
+    const double ph2 = f[0] * f[0];
+    const double t = fma(k.g2, f[1] * f[1], k.m2);       // m2 + g2 chi^2
+    dV[0] = f[0] * t;                                   // m2 phi + g2 phi chi^2
+    dV[1] = (k.g2 * ph2) * f[1];                        // g2 phi^2 chi
+    V = 0.5 * (ph2 * t);                                // phi^2 (m2 + g2 chi^2) / 2
+  }
+  struct SplitK { float m2, g2, hm2, hg2, p0, c0, two_p0, two_c0, p0sq, c0sq; };
+  __device__ static SplitK split_prep(const double* p, const double* b) {
+    SplitK k;
+    k.m2 = (float)p[0]; k.g2 = (float)p[1];
+    k.hm2 = (float)(0.5 * p[0]); k.hg2 = (float)(0.5 * p[1]);
+    k.p0 = (float)b[0]; k.c0 = (float)b[1];
+    k.two_p0 = (float)(2.0 * b[0]); k.two_c0 = (float)(2.0 * b[1]);
+    k.p0sq = (float)(b[0] * b[0]); k.c0sq = (float)(b[1] * b[1]);
+    return k;
+  }
+  // P = phi^2, Q = chi^2:  dP = d_phi (2 phi0 + d_phi),  dQ = d_chi (2 chi0 + d_chi)
+  //   dV'_phi = m2 d_phi + g2 (d_phi Q + phi0 dQ)
+  //   dV'_chi = g2 (dP chi + P0 d_chi)
+  //   dV      = m2/2 dP + g2/2 (dP Q + P0 dQ)
+  __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {
+    const float dp = d[0], dc = d[1];
+    const float dP = dp * (k.two_p0 + dp);
+    const float dQ = dc * (k.two_c0 + dc);
+    const float Q = k.c0sq + dQ;
+    const float ch = k.c0 + dc;
+    dVd[0] = fmaf(k.m2, dp, k.g2 * fmaf(dp, Q, k.p0 * dQ));
+    dVd[1] = k.g2 * fmaf(dP, ch, k.p0sq * dc);
+    dVv = fmaf(k.hm2, dP, k.hg2 * fmaf(dP, Q, k.p0sq * dQ));
+  }
+};
+
+// ---------------------------------------------------------------- OSCILLON
+template <> struct Pot<M_OSCILLON> {
+  static constexpr int NF = 1;
+  struct K { double m2, lam, g, hm2, qlam, sg; };
+  __device__ static K prep(const double* p) {
+    return K{p[0], p[1], p[2], 0.5 * p[0], 0.25 * p[1], p[2] / 6.0};
+  }
+  __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
+    const double x2 = f[0] * f[0];
+    dV[0] = f[0] * fma(x2, fma(k.g, x2, -k.lam), k.m2);   // m2 x - lam x^3 + g x^5
+    V = x2 * fma(x2, fma(k.sg, x2, -k.qlam), k.hm2);      // m2/2 x^2 - lam/4 x^4 + g/6 x^6
+  }
+  // (x0 + d)^n - x0^n = d * sum_{j=0}^{n-1} C(n, j+1) x0^{n-1-j} d^j  (Horner in d)
+  struct SplitK { float m2, lam, g, hm2, qlam, sg, c2, c3[2], c4[3], c5[4], c6[5]; };
+  __device__ static SplitK split_prep(const double* p, const double* b) {
+    const double x = b[0], x2 = x * x, x3 = x2 * x, x4 = x3 * x, x5 = x4 * x;
+    SplitK k;
+    k.m2 = (float)p[0]; k.lam = (float)p[1]; k.g = (float)p[2];
+    k.hm2 = (float)(0.5 * p[0]); k.qlam = (float)(0.25 * p[1]); k.sg = (float)(p[2] / 6.0);
+    k.c2 = (float)(2 * x);
+    k.c3[0] = (float)(3 * x2); k.c3[1] = (float)(3 * x);
+    k.c4[0] = (float)(4 * x3); k.c4[1] = (float)(6 * x2); k.c4[2] = (float)(4 * x);
+    k.c5[0] = (float)(5 * x4); k.c5[1] = (float)(10 * x3); k.c5[2] = (float)(10 * x2);
+    k.c5[3] = (float)(5 * x);
+    k.c6[0] = (float)(6 * x5); k.c6[1] = (float)(15 * x4); k.c6[2] = (float)(20 * x3);
+    k.c6[3] = (float)(15 * x2); k.c6[4] = (float)(6 * x);
+    return k;
+  }
+  __device__ static void diff(const SplitK& k, const float* dd, float* dVd, float& dVv) {
+    const float d = dd[0];
+    const float D2 = d * (k.c2 + d);
+    const float D3 = d * fmaf(d, k.c3[1] + d, k.c3[0]);
+    const float D4 = d * fmaf(d, fmaf(d, k.c4[2] + d, k.c4[1]), k.c4[0]);
+    const float D5 = d * fmaf(d, fmaf(d, fmaf(d, k.c5[3] + d, k.c5[2]), k.c5[1]), k.c5[0]);
+    const float D6 =
+        d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, k.c6[4] + d, k.c6[3]), k.c6[2]), k.c6[1]), k.c6[0]);
+    dVd[0] = fmaf(k.m2, d, fmaf(k.g, D5, -k.lam * D3));
+    dVv = fmaf(k.hm2, D2, fmaf(k.sg, D6, -k.qlam * D4));
+  }
+};
+
+// ---------------------------------------------------------------- QBALL
+template <> struct Pot<M_QBALL> {
+  static constexpr int NF = 2;
+  struct K { double m2, K1, mK, lnM2; };
+  __device__ static K prep(const double* p) {
+    return K{p[0], 1.0 + p[1], p[0] * p[1], log(p[2] * p[2])};
+  }
+  // u = (f1^2 + f2^2)/2 ; V' = m2 (1 + K + K ln(u/M^2)) f_i ; V = m2 u (1 + K ln(u/M^2))
+  __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
+    const double u = 0.5 * fma(f[0], f[0], f[1] * f[1]);
+    if (u > 0.0) {
+      const double l = log(u) - k.lnM2;
+      const double kl = k.mK * l;                          // m2 K ln(u/M^2)
+      const double fac = fma(k.m2, k.K1, kl);              // m2 (1 + K) + m2 K ln
+      dV[0] = fac * f[0];
+      dV[1] = fac * f[1];
+      V = u * (k.m2 + kl);
+    } else {
+      dV[0] = 0.0; dV[1] = 0.0; V = 0.0;
+    }
+  }
+  // du = d1 (p1 + d1/2) + d2 (p2 + d2/2),  l = log1p(du/u0)
+  //   dV'_i = m2 [ A d_i + K l (p_i + d_i) ],  A = 1 + K + K L0
+  //   dV    = m2 [ B du + K l (u0 + du) ],      B = 1 + K L0,  L0 = ln(u0/M^2)
+  struct SplitK { float m2, K, A, B, p1, p2, u0, inv_u0; int direct; float lnM2; };
+  __device__ static SplitK split_prep(const double* p, const double* b) {
+    SplitK k;
+    const double u0 = 0.5 * (b[0] * b[0] + b[1] * b[1]);
+    k.m2 = (float)p[0]; k.K = (float)p[1];
+    k.p1 = (float)b[0]; k.p2 = (float)b[1];
+    k.lnM2 = (float)log(p[2] * p[2]);
+    k.direct = !(u0 > 1e-30);
+    const double L0 = k.direct ? 0.0 : log(u0) - log(p[2] * p[2]);
+    k.A = (float)(1.0 + p[1] + p[1] * L0);
+    k.B = (float)(1.0 + p[1] * L0);
+    k.u0 = (float)u0;
+    k.inv_u0 = k.direct ? 0.f : (float)(1.0 / u0);
+    return k;
+  }
+  __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {
+    if (k.direct) {  // background at the origin: V(phi0) = V'(phi0) = 0
+      const float u = 0.5f * fmaf(d[0], d[0], d[1] * d[1]);
+      if (u > 0.f) {
+        const float l = logf(u) - k.lnM2;
+        const float fac = k.m2 * fmaf(k.K, l, 1.f + k.K);
+        dVd[0] = fac * d[0]; dVd[1] = fac * d[1];
+        dVv = k.m2 * u * fmaf(k.K, l, 1.f);
+      } else {
+        dVd[0] = 0.f; dVd[1] = 0.f; dVv = 0.f;
+      }
+      return;
+    }
+    const float du = fmaf(d[0], fmaf(0.5f, d[0], k.p1), d[1] * fmaf(0.5f, d[1], k.p2));
+    const float u = k.u0 + du;
+    if (u > 0.f) {
+      const float l = log1pf(du * k.inv_u0);
+      const float Kl = k.K * l;
+      dVd[0] = k.m2 * fmaf(k.A, d[0], Kl * (k.p1 + d[0]));
+      dVd[1] = k.m2 * fmaf(k.A, d[1], Kl * (k.p2 + d[1]));
+      dVv = k.m2 * fmaf(k.B, du, Kl * u);
+    } else {  // |Phi| = 0 here: V = V' = 0
+      dVd[0] = -k.m2 * k.A * k.p1;
+      dVd[1] = -k.m2 * k.A * k.p2;
+      dVv = -k.m2 * k.B * k.u0;
+    }
+  }
+};
+
+}  // namespace pycool

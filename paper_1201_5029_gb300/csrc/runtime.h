@@ -1,0 +1,31 @@
+// Host-side helpers shared by the single-simulation API and the server.
+#pragma once
+
+#include <cstddef>
+
+#include "../../include/pycool.h"
+#include "internal.cuh"
+
+namespace pycool {
+
+// Device memory layout of one simulation.
+//   state     : [Background][SimDesc][phi buf 0][phi buf 1][pi buf 0][pi buf 1]
+//   workspace : [ticket (256 B)][partials: ncta * kNQ doubles]
+struct Layout {
+  Geometry geo;
+  size_t field_bytes;
+  size_t off_bg, off_desc, off_fields, state_bytes;
+  size_t off_ticket, off_partials, ws_bytes;
+};
+
+int stage_table(int order, double* w);
+int model_nfields(int model);
+Layout layout_for(const pycool_config& c);
+pycool_status validate(const pycool_config* c);
+void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state, char* ws);
+cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s);
+cudaError_t launch_arm(Background* bg, long long nsweeps, cudaStream_t s);
+void observables(const Background& b, const SimDesc& d, double mpl, double rho_r0,
+                 double rho_m0, pycool_observables* out);
+
+}  // namespace pycool

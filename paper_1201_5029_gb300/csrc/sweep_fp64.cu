@@ -1,0 +1,9 @@
+// FP64 instances of the fused stage sweep (every model x stencil).
+#include "sweep.cuh"
+
+namespace pycool {
+cudaError_t launch_sweep_fp64(int model, int stencil, const LaunchTable& t, int grid,
+                              cudaStream_t s) {
+  return launch_sweep_impl<PREC_FP64>(model, stencil, t, grid, s);
+}
+}  // namespace pycool

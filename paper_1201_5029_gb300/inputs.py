@@ -107,7 +107,7 @@ def _filter(noise: np.ndarray, L: float, m2: float, power: float) -> np.ndarray:
     f = np.fft.rfftn(noise)
     f *= w ** power
     f[0, 0, 0] = 0.0
-    return np.fft.irfftn(f, s=noise.shape)
+    return np.fft.irfftn(f, s=noise.shape, axes=(0, 1, 2))
 
 
 def spectral_ics(w: dict, n: Optional[int] = None, seed: Optional[int] = None

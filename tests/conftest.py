@@ -1,3 +1,4 @@
+import importlib.util
 import os
 import sys
 
@@ -6,8 +7,29 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+
+def _ensure_library_built():
+    """Compile libpycool.so in-tree if it is missing or stale (nvcc cross-compiles)."""
+    spec = importlib.util.spec_from_file_location(
+        "_pycool_build", os.path.join(ROOT, "paper_1201_5029_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
 
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than ~20 s on CPU")
+    _ensure_library_built()
+
+
+def gpu_available() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
