@@ -1,0 +1,379 @@
+"""Throughput of the symplectic lattice step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload preheat128]
+                    [--impl ours|reference]
+
+Workload (default): the two-field chaotic-preheating problem on a 128^3
+lattice, L = 10/m, 4th-order Yoshida triple jump (3 stages per step),
+d-eta = 0.01, seeded spectral initial fluctuations; both the FP64 form and the
+split-FP32 form.  A "step" is one time step through the C ABI: evolve(1) =
+3 fused stage sweeps + the synchronising flush sweep (every row of the hot
+path: background update, fused sweep, reductions, flush/energies).
+
+Metric: site-updates/s per stage = n^3 x stages / time, whole job (all ranks).
+The 128^3 state is smaller than L2, so L2 is flushed (256 MiB write) between
+timed steps; each step is timed with CUDA events on the simulation's stream.
+
+--impl reference times the CPU oracle (oracle/pycool_oracle.py, the method as
+written in the paper) on the host cores on the same workload, one time step
+per timed step.
+
+Multi-GPU: the simulations are independent (replicas only, no collective on
+the data path); under torchrun each rank runs its own replica and rank 0
+reports the whole-job rate over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s per stage vs HBM roofline (FP64, split-FP32); serving p50/p99"
+UNIT = "site-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# FP64 floating-point operations per site and stage sweep (FMA = 2), counted
+# from the sweep kernel's arithmetic with the 7-point stencil:
+#   drift 2/field, Laplacian 7/field (4 adds in-plane, 1 FMA, 2 adds across z),
+#   kick 4/field, sums pi^2 and phi D 4/field + 1 for V, plus the potential:
+#   chaotic2 9, oscillon 11, qball 12 (+ one float64 log, not counted), free 3.
+FP64_FLOPS_PER_SITE = {"chaotic2": 44.0, "oscillon": 29.0, "qball": 47.0, "free": 21.0}
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (recipe nominal); measured 1.19 with a DFMA loop
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 100 ms during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pycool_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_form(P, torch, w, precision, steps, warmup, flush_buf, phi, pi, stream):
+    """Time `steps` evolve(1) calls of one form; returns a dict of measurements."""
+    cfg = P.config_from_workload(w, precision=precision)
+    sim = P.Simulation(cfg, stream=stream)
+    sim.set_initial(phi, pi)
+    for _ in range(warmup):
+        sim.evolve(1)
+    assert sim.sync() == P.OK
+    s = P.pycool_stages_per_step(w["order"])
+    launches0 = sim.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush_buf.add_(1)           # 256 MiB read+write: evicts the lattice from L2
+        ev[i][0].record(stream)
+        sim.evolve(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    st = sim.sync()
+    launches = sim.kernel_launches() - launches0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    e = sim.energies()
+    sim.close()
+    return dict(ms=ms, total_ms=sum(ms), launches=launches, stages=s, status=st, energies=e)
+
+
+def e2e_form(P, torch, w, precision, steps, phi_pin, pi_pin, out_phi, out_pi, stream):
+    """Through the public API with host buffers: H2D of the inputs, one time step,
+    D2H of the result, every step."""
+    cfg = P.config_from_workload(w, precision=precision)
+    sim = P.Simulation(cfg, stream=stream)
+    sim.set_initial(phi_pin, pi_pin)
+    sim.evolve(1)
+    sim.get_fields(out_phi, out_pi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.set_initial(phi_pin, pi_pin)     # H2D from pinned host memory
+        sim.evolve(1)
+        sim.get_fields(out_phi, out_pi)      # D2H of the step's result
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    return dt
+
+
+def cpu_baseline(w, phi, pi, budget_s=15.0):
+    """The oracle as it stands, on the host cores: whole time steps of the workload."""
+    from oracle import pycool_oracle as O
+    cfg = O.LatticeConfig(n=w["n"], L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+                          order=w["order"], mpl=w["mpl"])
+    st = O.make_state(cfg, phi, pi)
+    s = len(O.stage_weights(w["order"]))
+    done, t0 = 0, time.perf_counter()
+    while True:
+        O.step(cfg, st)
+        done += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or done >= 20:
+            break
+    rate = w["n"] ** 3 * s * done / el
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} full time step(s) of the {w['n']}^3 workload ({s} stages each), "
+                      f"{el:.1f} s, numpy FP64, single thread"}
+
+
+def reference_arm(args, w):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    from paper_1201_5029_gb300 import inputs as I
+    from oracle import pycool_oracle as O
+    phi, pi = I.initial_fields(w)
+    cfg = O.LatticeConfig(n=w["n"], L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+                          order=w["order"], mpl=w["mpl"])
+    st = O.make_state(cfg, phi, pi)
+    s = len(O.stage_weights(w["order"]))
+    # one warm-up step at most: the oracle has no caches to warm
+    for _ in range(min(args.warmup, 1)):
+        O.step(cfg, st)
+    # each timed step is one full time step; stop early once the sample is
+    # bounded (~2 minutes) so the whole run ends within a few minutes
+    done, t0 = 0, time.perf_counter()
+    while done < args.steps:
+        O.step(cfg, st)
+        done += 1
+        if time.perf_counter() - t0 > 120.0:
+            break
+    el = time.perf_counter() - t0
+    value = w["n"] ** 3 * s * done / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{done} full time step(s) of the {w['n']}^3 workload "
+                                   f"({el:.1f} s; numpy FP64, single thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(w):
+    return {"workload": f"{w['name']}: {w['model']} {len(w['background'])}-field, "
+                        f"{w['n']}^3 periodic lattice, L={w['L']}, order {w['order']} "
+                        f"(Yoshida), dt={w['dt']}, m_pl={w['mpl']}",
+            "n": w["n"], "fields": len(w["background"]), "order": w["order"],
+            "stencil": "7pt", "ic": w.get("ic", "white"), "seed": w["seed"],
+            "step": "evolve(1): one fused sweep per stage + synchronising flush",
+            "l2": "flushed between timed steps (256 MiB write); state < L2",
+            "parallelism": "replicas (independent lattice per GPU)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="preheat128")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms", default="fp64,split_fp32",
+                    help="comma list of forms to time (profiling a single kernel)")
+    args = ap.parse_args()
+    forms = [f for f in args.forms.split(",") if f]
+    args.warmup = max(args.warmup, 3)
+
+    from paper_1201_5029_gb300 import inputs as I
+    w = I.workload(args.workload)
+    w["name"] = args.workload
+    if args.impl == "reference":
+        return reference_arm(args, w)
+
+    import numpy as np
+    import torch
+    import paper_1201_5029_gb300 as P
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    stream = torch.cuda.current_stream()
+    phi, pi = I.initial_fields(w)
+    nf = phi.shape[0]
+    S = w["n"] ** 3
+    flush_buf = torch.zeros(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks, peak_kind = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    res = {}
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for prec in forms:
+            res[prec] = run_form(P, torch, w, prec, args.steps, args.warmup, flush_buf, phi, pi,
+                                 stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+    clocks = clk.summary()
+
+    # slowest rank decides
+    tot = {k: v["total_ms"] for k, v in res.items()}
+    if ws > 1:
+        t = torch.tensor([tot[f] for f in forms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = {f: float(t[i]) for i, f in enumerate(forms)}
+    if forms != ["fp64", "split_fp32"]:
+        if rank == 0:  # profiling run: a short line per form, no baselines
+            for f in forms:
+                r = res[f]
+                print(json.dumps({"form": f, "value": ws * S * r["stages"] * args.steps /
+                                  (tot[f] / 1e3), "unit": UNIT, "ms_per_step": tot[f] / args.steps,
+                                  "launches": r["launches"], "status": r["status"]}), flush=True)
+        return 0
+
+    def summarize(prec, word, bytes_flush_per_site):
+        r = res[prec]
+        s = r["stages"]
+        total_s = tot[prec] / 1e3
+        rate = ws * S * s * args.steps / total_s
+        # algorithmic bytes: read + write phi and pi per sweep; the flush reads both, writes phi
+        sweep_bytes = 4 * nf * word * S
+        flush_bytes = bytes_flush_per_site * nf * word * S
+        per_rank_bytes = args.steps * (s * sweep_bytes + flush_bytes)
+        launches = r["launches"]
+        sweeps = args.steps * (s + 1)
+        avg_launch_s = total_s / sweeps
+        gbs = per_rank_bytes / total_s / 1e9
+        return rate, gbs, avg_launch_s, launches, sweep_bytes
+
+    r64, gbs64, t64, l64, b64 = summarize("fp64", 8, 3)
+    r32, gbs32, t32, l32, b32 = summarize("split_fp32", 4, 3)
+    flops_site = FP64_FLOPS_PER_SITE.get(w["model"], 40.0)
+    s = res["fp64"]["stages"]
+    fp64_tflops = S * s * args.steps * flops_site / (tot["fp64"] / 1e3) / 1e12
+    roof64 = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS,
+              "unit": "TFLOP/s", "frac": fp64_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+              "kernel": "sweep_tma<chaotic2,7pt,fp64>",
+              "peak_kind": "recipe nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)",
+              "hbm_frac": gbs64 / hbm, "achieved_gbs": gbs64,
+              "flops_per_site_stage": flops_site}
+    roof32 = {"bound": "hbm", "achieved": gbs32, "peak": hbm, "unit": "GB/s",
+              "frac": gbs32 / hbm, "traffic": None, "kernel": "sweep_tma<chaotic2,7pt,split>",
+              "peak_kind": f"{peak_kind} (copy test)", "note": "state fits in L2 (flushed "
+              "between steps, not between the sweeps of a step)"}
+
+    # e2e through the public API with host buffers (FP64 form)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        phi_pin = torch.from_numpy(phi).pin_memory().numpy()
+        pi_pin = torch.from_numpy(pi).pin_memory().numpy()
+        out_phi = torch.empty(phi.shape, dtype=torch.float64).pin_memory().numpy()
+        out_pi = torch.empty(pi.shape, dtype=torch.float64).pin_memory().numpy()
+        k = args.e2e_steps
+        dt = e2e_form(P, torch, w, "fp64", k, phi_pin, pi_pin, out_phi, out_pi, stream)
+        e2e = {"value": ws * S * s * k / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(phi.nbytes + pi.nbytes),
+               "d2h_bytes_per_step": int(out_phi.nbytes + out_pi.nbytes),
+               "form": "fp64", "steps": k,
+               "note": "set_initial(host) + evolve(1) + get_fields(host) per step"}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(w, phi, pi)
+        line = {
+            "metric": METRIC, "value": r64, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot["fp64"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded spectral initial fluctuations, no dataset)",
+            "config": _config(w),
+            "roofline": roof64,
+            "forms": {
+                "fp64": {"value": r64, "unit": UNIT, "ms_per_step": tot["fp64"] / args.steps,
+                         "algorithmic_gbs": gbs64, "hbm_frac": gbs64 / hbm, "roofline": roof64,
+                         "status": res["fp64"]["status"]},
+                "split_fp32": {"value": r32, "unit": UNIT,
+                               "ms_per_step": tot["split_fp32"] / args.steps,
+                               "dtype": "f32 fluctuations + f64 background/sums",
+                               "roofline": roof32, "status": res["split_fp32"]["status"],
+                               "speedup_vs_fp64": r32 / r64},
+            },
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(l64 + l32),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -76,7 +76,7 @@ Layout layout_for(const pycool_config& c) {
   const int nf = model_nfields(c.model);
   const size_t S = (size_t)c.n * c.n * c.n;
   const size_t word = c.precision == PYCOOL_SPLIT_FP32 ? 4 : 8;
-  L.geo = choose_geometry(c.n);
+  L.geo = choose_geometry(c.n, (int)word, nf);
   L.field_bytes = align256((size_t)nf * S * word);
   L.off_bg = 0;
   L.off_desc = align256(sizeof(Background));
@@ -125,6 +125,7 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.stencil = c.stencil;
   d.prec = c.precision == PYCOOL_SPLIT_FP32 ? PREC_SPLIT : PREC_FP64;
   d.nstages = stage_table(c.order, d.w);
+  d.tma = L.geo.tma; d.vx = L.geo.vx; d.txt = L.geo.txt;
   d.tx = L.geo.tx; d.ty = L.geo.ty; d.zc = L.geo.zc;
   d.tiles_x = L.geo.tiles_x; d.tiles_y = L.geo.tiles_y;
   d.zchunks = L.geo.zchunks; d.ncta = L.geo.ncta;
@@ -146,12 +147,52 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.pi[1] = f + 3 * L.field_bytes;
   d.bg = (Background*)(state + L.off_bg);
   d.ticket = (unsigned int*)(ws + L.off_ticket);
+  d.fault = (int32_t*)(ws + L.off_ticket + 128);
   d.partials = (double*)(ws + L.off_partials);
 }
 
+// TMA descriptors for the four field buffers (see SimDesc::tmap).  The driver
+// entry point is looked up at run time, so the library needs no libcuda at link.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_tensor_maps(SimDesc& d) {
+  if (!d.tma) return cudaSuccess;
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = (EncodeTiledFn)p;
+  }
+  const size_t word = d.prec == PREC_SPLIT ? 4 : 8;
+  const CUtensorMapDataType dt =
+      d.prec == PREC_SPLIT ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t dims[3] = {(cuuint64_t)d.n, (cuuint64_t)d.n, (cuuint64_t)d.n * d.nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)d.n * word, (cuuint64_t)d.n * d.n * word};
+  const cuuint32_t box_tile[3] = {(cuuint32_t)d.tx, (cuuint32_t)d.ty, 1};
+  const cuuint32_t box_row[3] = {(cuuint32_t)d.tx, 1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* bufs[4] = {d.phi[0], d.phi[1], d.pi[0], d.pi[1]};
+  for (int b = 0; b < 4; ++b) {
+    for (int k = 0; k < 2; ++k) {
+      const CUresult r = fn(&d.tmap[b][k], dt, 3, bufs[b], dims, strides, k == 0 ? box_tile : box_row,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s) {
-  if (d.prec == PREC_SPLIT) return launch_sweep_split(d.model, d.stencil, t, grid, s);
-  return launch_sweep_fp64(d.model, d.stencil, t, grid, s);
+  if (d.prec == PREC_SPLIT) return launch_sweep_split(d.model, d.stencil, d.vx, d.tma, t, grid, s);
+  return launch_sweep_fp64(d.model, d.stencil, d.vx, d.tma, t, grid, s);
 }
 
 __global__ void arm_kernel(Background* bg, long long nsweeps) {
@@ -322,6 +363,14 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
     sim->own_ws = true;
   }
   fill_desc(sim->hdesc, *cfg, sim->L, sim->state, sim->ws);
+  e = encode_tensor_maps(sim->hdesc);
+  if (e != cudaSuccess) {
+    cuda_fail(nullptr, e, "cuTensorMapEncodeTiled");
+    if (sim->own_state) cudaFree(sim->state);
+    if (sim->own_ws) cudaFree(sim->ws);
+    delete sim;
+    return PYCOOL_E_CUDA;
+  }
   sim->nstages = sim->hdesc.nstages;
   sim->d_desc = (SimDesc*)(sim->state + sim->L.off_desc);
   sim->d_bg = (Background*)(sim->state + sim->L.off_bg);
@@ -477,6 +526,12 @@ PYCOOL_API pycool_status pycool_sync(pycool_sim* sim, double timeout_s) {
       if (el > timeout_s) return PYCOOL_E_TIMEOUT;
     }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  int32_t fault = 0;
+  CK(cudaMemcpy(&fault, sim->hdesc.fault, sizeof(fault), cudaMemcpyDeviceToHost));
+  if (fault) {  // a device-side wait gave up: the state can no longer be trusted
+    sim->poisoned = true;
+    return PYCOOL_E_TIMEOUT;
   }
   Background b;
   pycool_status st = read_bg(sim, &b);

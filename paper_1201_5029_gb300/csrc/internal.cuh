@@ -9,15 +9,17 @@
 // identical launches with no host round trip, and replays as a CUDA graph.
 #pragma once
 
-#include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 namespace pycool {
 
 constexpr int kMaxFields = 2;
 constexpr int kMaxStages = 15;
 constexpr int kThreads = 256;      // threads per block, every kernel
-constexpr int kMaxTX = 32;         // tile width (x, contiguous)
+constexpr int kMaxTXT = 32;        // threads per tile row (x, contiguous)
 constexpr int kMaxTY = 8;          // tile height (y)
 constexpr int kNQ = 12;            // reduction slots per block
 constexpr int kMaxMembers = 64;    // simulations per batched launch
@@ -52,9 +54,16 @@ struct alignas(16) Background {
   double pad[4];
 };
 
-struct alignas(16) SimDesc {
+struct alignas(64) SimDesc {
+  // TMA descriptors of the four field buffers (phi 0, phi 1, pi 0, pi 1), each as
+  // [0] a TX x TY x 1 box (the tile) and [1] a TX x 1 x 1 box (one halo row).
+  // The tensor is the buffer viewed as x: n, y: n, z: N_f n (fields stacked in z).
+  CUtensorMap tmap[4][2];
   int32_t n, nf, model, stencil, prec, nstages;
-  int32_t tx, ty, zc, tiles_x, tiles_y, zchunks, ncta, pad0;
+  int32_t tma;                // 1: TMA-staged kernel (n % 32 == 0), 0: plain loads
+  int32_t vx;                 // sites per thread along x (TMA kernel)
+  int32_t txt;                // threads per tile row
+  int32_t tx, ty, zc, tiles_x, tiles_y, zchunks, ncta;
   int64_t S;                  // n^3
   double dt, dx2inv, VL, inv6VLm2, mpl2, rho_r0, rho_m0;
   double params[8];
@@ -63,6 +72,7 @@ struct alignas(16) SimDesc {
   void* pi[2];
   double* partials;           // ncta * kNQ
   unsigned int* ticket;
+  int32_t* fault;             // set when a device-side wait gave up
   Background* bg;
 };
 
@@ -72,22 +82,37 @@ struct LaunchTable {
   const SimDesc* desc[kMaxMembers];
 };
 
-// Geometry of the z-streamed tiling, a function of n alone (so the reduction
-// order of a lattice does not depend on what it is batched with).
+// Geometry of the z-streamed tiling, a function of (n, word size, N_f) alone,
+// so the reduction order of a lattice does not depend on what it is batched
+// with.  A block is 256 threads.
+//   TMA kernel (n % 32 == 0): 32 lanes x 8 rows, each lane owns vx sites along
+//     x (vx * N_f * word <= 16 bytes), tile = 32 vx x 8, n % (32 vx) == 0.
+//   plain kernel (other n): one site per thread, txt x ty threads (ragged tiles).
 struct Geometry {
-  int tx, ty, zc, tiles_x, tiles_y, zchunks, ncta;
+  int tma, vx, txt, tx, ty, zc, tiles_x, tiles_y, zchunks, ncta;
 };
 
-inline Geometry choose_geometry(int n) {
+inline Geometry choose_geometry(int n, int word, int nf) {
   Geometry g;
-  g.tx = n >= kMaxTX ? kMaxTX : n;
-  g.ty = n >= kMaxTY ? kMaxTY : n;
+  g.tma = (n % 32 == 0) ? 1 : 0;
+  g.vx = 1;
+  if (g.tma) {
+    for (int v = 16 / (word * nf); v >= 2; v /= 2)
+      if (n % (32 * v) == 0) { g.vx = v; break; }
+    g.txt = 32;
+    g.ty = kMaxTY;
+  } else {
+    g.txt = n >= 32 ? 32 : n;
+    g.ty = n >= kMaxTY ? kMaxTY : n;
+  }
+  g.tx = g.txt * g.vx;
   g.tiles_x = (n + g.tx - 1) / g.tx;
   g.tiles_y = (n + g.ty - 1) / g.ty;
   const int tiles = g.tiles_x * g.tiles_y;
-  const int target = 2 * 152;  // at least two waves on 152 SMs when possible
+  const int target = 2 * 152;           // two blocks per SM on 152 SMs
+  const int min_zc = n >= 128 ? 16 : 4;  // bound the z-halo re-read overhead
   int zc = 64;
-  while (zc > 4 && (long long)tiles * ((n + zc - 1) / zc) < target) zc /= 2;
+  while (zc > min_zc && (long long)tiles * ((n + zc - 1) / zc) < target) zc /= 2;
   if (zc > n) zc = n;
   g.zc = zc;
   g.zchunks = (n + zc - 1) / zc;
@@ -96,9 +121,9 @@ inline Geometry choose_geometry(int n) {
 }
 
 // Launchers (one translation unit per precision).
-cudaError_t launch_sweep_fp64(int model, int stencil, const LaunchTable& t, int grid,
+cudaError_t launch_sweep_fp64(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
                               cudaStream_t s);
-cudaError_t launch_sweep_split(int model, int stencil, const LaunchTable& t, int grid,
+cudaError_t launch_sweep_split(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
                                cudaStream_t s);
 
 }  // namespace pycool

@@ -52,7 +52,7 @@ template <> struct Pot<M_CHAOTIC2> {
     const double t = fma(k.g2, f[1] * f[1], k.m2);       // m2 + g2 chi^2
     dV[0] = f[0] * t;                                   // m2 phi + g2 phi chi^2
     dV[1] = (k.g2 * ph2) * f[1];                        // g2 phi^2 chi
-    V = 0.5 * (ph2 * t);                                // phi^2 (m2 + g2 chi^2) / 2
+    V = ph2 * (0.5 * t);                                // phi^2 (m2 + g2 chi^2) / 2
   }
   struct SplitK { float m2, g2, hm2, hg2, p0, c0, two_p0, two_c0, p0sq, c0sq; };
   __device__ static SplitK split_prep(const double* p, const double* b) {

@@ -16,22 +16,32 @@
 // reducing the sums the energies of Eq. rho-pres need.
 //
 // Tiling: a block owns a TX x TY column tile and a z-chunk of ZC planes and
-// streams z upward (Sec. 2.4 marches z the same way).  The drifted plane
-// phi*(z) with a one-site halo lives in shared memory (double-buffered, one
-// barrier per plane); the Laplacian of Eq. D is split by z-offset into
+// streams z upward (the paper's GPU code marches z the same way).  The drifted
+// plane phi*(z) lives in shared memory; the Laplacian of Eq. D is split by
+// z-offset into
 //     S_mid(p) = c0 ctr + c1 sum(4 faces) + c2 sum(4 corners)   (in-plane)
 //     S_off(p) = c1 ctr + c2 sum(4 faces) + c3 sum(4 corners)   (for planes z+-1)
-// so D(z) = S_off(z-1) + S_mid(z) + S_off(z+1) needs only one resident plane.
-// Periodic wrap is done with modular indices; ragged tiles (n not a multiple
-// of the tile) load wrapped values and mask their outputs.
+// so D(z) = S_off(z-1) + S_mid(z) + S_off(z+1) needs one resident plane and
+// two registers per site.
 //
-// Reductions: per-thread column sums -> warp butterfly -> fixed-order sum of
-// the 8 warps -> one partial per block and quantity.  The last block to arrive
-// (atomic ticket; nobody waits) sums the partials in block order (Neumaier),
-// applies the p_a kick of Phi_H3 and advances the Background.  Results are
-// bitwise reproducible and depend only on the lattice, not on the batch.
+// Two kernels share this arithmetic:
+//   sweep_tma   (n a multiple of 32): each plane's tile and its two halo rows
+//               arrive by TMA (cp.async.bulk.tensor, mbarrier completion) in a
+//               3-slot shared-memory ring, two planes ahead of the compute;
+//               x-neighbours come from warp shuffles (one warp = one tile row)
+//               and the two halo columns from plain loads.  No periodic wrap
+//               is ever asked of the TMA: halo rows are fetched at wrapped y.
+//   sweep_plain (any n): plain loads with modular indices, ragged tiles masked.
+//
+// Reductions: per-thread column sums (Kahan in float) -> warp butterfly ->
+// fixed-order sum of the 8 warps -> one partial per block and quantity.  The
+// last block to arrive (atomic ticket; nobody waits) sums the partials in
+// block order (Neumaier), applies the p_a kick of Phi_H3 and advances the
+// Background.  Results are bitwise reproducible and depend only on the
+// lattice, not on what it is batched with.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -60,8 +70,9 @@ __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, 
   const double h = (mode == MODE_SWEEP) ? d.w[b.stage] * d.dt : 0.0;
   double a = b.a;
   double pa = b.pa;
+  const double s2 = b.sum_pi2;
   // trailing Phi_H2(h_prev/2) of the previous stage: p_a += [sum pi^2/a^3 - V_L rho_m] h_prev/2
-  pa = pa + (b.sum_pi2 / (a * a * a) - d.VL * d.rho_m0) * (0.5 * hp);
+  pa = pa + (s2 / (a * a * a) - d.VL * d.rho_m0) * (0.5 * hp);
   double c = 0.5 * hp / (a * a);
   if (mode != MODE_SWEEP) {
     // trailing Phi_H1(h_prev/2): a -= p_a h_prev / (12 V_L m^2)
@@ -72,7 +83,7 @@ __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, 
   // Phi_H1(h_prev/2) Phi_H1(h/2) merged (p_a is constant under H1)
   a = a - pa * d.inv6VLm2 * (0.5 * (hp + h));
   // leading Phi_H2(h/2)
-  pa = pa + (b.sum_pi2 / (a * a * a) - d.VL * d.rho_m0) * (0.5 * h);
+  pa = pa + (s2 / (a * a * a) - d.VL * d.rho_m0) * (0.5 * h);
   c = c + 0.5 * h / (a * a);
   k.c = c;
   k.kD = a * a * h * d.dx2inv;
@@ -80,6 +91,13 @@ __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, 
   k.a = a; k.pa = pa; k.h = h;
   return k;
 }
+
+// Explicitly typed fused multiply-add: float arithmetic must stay on the FP32
+// pipe (GB300's FP64 rate is ~1/60 of FP32).
+__device__ __forceinline__ float madd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+__device__ __forceinline__ bool is_fin(double x) { return isfinite(x); }
 
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NQ doubles; result in out[0..NQ) (shared).
@@ -108,16 +126,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* sred, double*
   __syncthreads();
 }
 
-__device__ __forceinline__ bool is_fin(double x) { return isfinite(x); }
-
-template <int STENCIL, typename T> struct StencilC;
-template <typename T> struct StencilC<7, T> {
-  static constexpr bool kCorners = false;
-};
-template <typename T> struct StencilC<27, T> {
-  static constexpr bool kCorners = true;
-};
-
 // Reduction slot layout.
 template <int NF, int PREC> struct Slots;
 template <int NF> struct Slots<NF, PREC_FP64> {
@@ -132,269 +140,215 @@ template <int NF> struct Slots<NF, PREC_SPLIT> {
   static constexpr int NQ = 5 * NF + 1;
 };
 
+template <typename T, int V> struct Vec;
+template <> struct Vec<float, 1> { using type = float; };
+template <> struct Vec<float, 2> { using type = float2; };
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<double, 1> { using type = double; };
+template <> struct Vec<double, 2> { using type = double2; };
+
+// Load / store VX consecutive elements (aligned to VX * sizeof(T)).
+template <typename T, int VX>
+__device__ __forceinline__ void vload(const T* p, T (&v)[VX]) {
+  using VT = typename Vec<T, VX>::type;
+  const VT x = *reinterpret_cast<const VT*>(p);
+  const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+  for (int j = 0; j < VX; ++j) v[j] = e[j];
+}
+template <typename T, int VX>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[VX]) {
+  using VT = typename Vec<T, VX>::type;
+  VT x;
+  T* e = reinterpret_cast<T*>(&x);
+#pragma unroll
+  for (int j = 0; j < VX; ++j) e[j] = v[j];
+  *reinterpret_cast<VT*>(p) = x;
+}
+
+// Kahan-compensated accumulation for the float path; plain for double.
+template <typename T> struct Acc {
+  T s, c;
+  __device__ __forceinline__ void zero() { s = 0; c = 0; }
+  __device__ __forceinline__ void add(T x) {
+    if constexpr (sizeof(T) == 4) {
+      const T y = x - c;
+      const T t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // ---------------------------------------------------------------------------
-// The sweep kernel.
+// Per-launch context: the coefficients every block derives from the
+// Background (identically), and the per-site update.
 // ---------------------------------------------------------------------------
-template <int MODEL, int STENCIL, int PREC>
-__global__ void __launch_bounds__(kThreads)
-sweep_kernel(const LaunchTable tab) {
+template <int MODEL, int PREC>
+struct Ctx {
   using P = Pot<MODEL>;
-  constexpr int NF = P::NF;
+  static constexpr int NF = P::NF;
   using T = typename std::conditional<PREC == PREC_FP64, double, float>::type;
   using SL = Slots<NF, PREC>;
-  constexpr int NQ = SL::NQ;
-  constexpr bool CORNERS = StencilC<STENCIL, T>::kCorners;
-
-  __shared__ T sm[2][NF][kMaxTY + 2][kMaxTX + 2];
-  __shared__ double sred[(kThreads / 32) * NQ];
-  __shared__ double sout[NQ];
-  __shared__ int s_last;
-
-  // ---- which simulation and tile ------------------------------------------
-  int mem = 0;
-  {
-    const int b = blockIdx.x;
-    int lo = 0, hi = tab.count - 1;
-    while (lo < hi) {  // largest m with cta_offset[m] <= b
-      const int mid = (lo + hi + 1) >> 1;
-      if (tab.cta_offset[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    mem = lo;
-  }
-  const SimDesc& d = *tab.desc[mem];
-  const int cta = blockIdx.x - tab.cta_offset[mem];
-  Background* bgp = d.bg;
-  const Background bg = *bgp;
-  const int mode = bg.mode;
-  if (mode == MODE_IDLE) return;
-
-  const int n = d.n;
-  const int TX = d.tx, TY = d.ty;
-  const int tile = cta % (d.tiles_x * d.tiles_y);
-  const int zch = cta / (d.tiles_x * d.tiles_y);
-  const int x0 = (tile % d.tiles_x) * TX;
-  const int y0 = (tile / d.tiles_x) * TY;
-  const int z0 = zch * d.zc;
-  const int zend = min(n, z0 + d.zc);
-  const int tid = threadIdx.x;
-  const bool active = tid < TX * TY;
-  const int lx = active ? tid % TX : 0;
-  const int ly = active ? tid / TX : 0;
-  const int gx = x0 + lx, gy = y0 + ly;
-  const bool valid = active && gx < n && gy < n;
-  const int wx = gx >= n ? gx - n : gx;
-  const int wy = gy >= n ? gy - n : gy;
-  const size_t S = (size_t)d.S;
-  const size_t nn = (size_t)n * n;
-
-  const int ib = bg.cur;  // bit0: phi buffer, bit1: pi buffer
-  const T* __restrict__ phi_in = (const T*)d.phi[ib & 1];
-  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
-  const T* __restrict__ pi_in = (const T*)d.pi[(ib >> 1) & 1];
-  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
-
-  // ---- scalar coefficients -------------------------------------------------
-  const Coef k = prestage(bg, d, mode);
-  const typename P::K pk = P::prep(d.params);
+  Coef k;
+  typename P::K pk;
   T cdrift, kD, kV;
   T mu_phi[NF], mu_pi[NF];
-  double phi0s[NF], pi0s[NF], V0 = 0.0;  // split background after drift / kick
-  typename P::SplitK sk;
-  if constexpr (PREC == PREC_SPLIT) {
-    cdrift = (T)k.c; kD = (T)k.kD; kV = (T)k.kV;
-    double phi0p[NF], pi0p[NF], dV0[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      mu_phi[f] = (float)bg.mu_phi[f];
-      mu_pi[f] = (float)bg.mu_pi[f];
-      phi0p[f] = bg.phi0[f] + (double)mu_phi[f];
-      pi0p[f] = bg.pi0[f] + (double)mu_pi[f];
-      phi0s[f] = fma(k.c, pi0p[f], phi0p[f]);
-    }
-    P::eval(pk, phi0s, dV0, V0);
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-      pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], pi0p[f]) : pi0p[f];
-    sk = P::split_prep(d.params, phi0s);
-  } else {
-    cdrift = k.c; kD = k.kD; kV = k.kV;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) { mu_phi[f] = 0; mu_pi[f] = 0; }
-  }
   T shiftK[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) shiftK[f] = (PREC == PREC_FP64) ? (T)bg.shift[f] : (T)0;
+  double phi0s[NF], pi0s[NF], V0;  // split form: background after drift / kick
+  typename P::SplitK sk;
 
-  // stencil weights (Eq. D): 7pt (-6, 1, 0, 0); iso27 (-128, 14, 3, 1)/30
-  const T c0 = CORNERS ? (T)(-128.0 / 30.0) : (T)(-6.0);
-  const T c1 = CORNERS ? (T)(14.0 / 30.0) : (T)1.0;
-  const T c2 = CORNERS ? (T)(3.0 / 30.0) : (T)0.0;
-  const T c3 = CORNERS ? (T)(1.0 / 30.0) : (T)0.0;
-
-  // halo ring of the tile: (TX+2) cells below, (TX+2) above, TY left, TY right
-  const int nhalo = 2 * (TX + 2) + 2 * TY;
-  int hx = 0, hy = 0;
-  if (tid < nhalo) {
-    int t = tid;
-    if (t < TX + 2) { hx = t - 1; hy = -1; }
-    else if ((t -= TX + 2) < TX + 2) { hx = t - 1; hy = TY; }
-    else if ((t -= TX + 2) < TY) { hx = -1; hy = t; }
-    else { t -= TY; hx = TX; hy = t; }
-  }
-  int hgx = x0 + hx, hgy = y0 + hy;
-  hgx = hgx < 0 ? hgx + n : (hgx >= n ? hgx - n : hgx);
-  hgy = hgy < 0 ? hgy + n : (hgy >= n ? hgy - n : hgy);
-
-  // per-thread accumulators
-  T acc[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = (T)0;
-
-  // rotating registers (per field)
-  T so_mm[NF], so_m[NF], smid_m[NF], ph_m[NF], pi_m[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) { so_mm[f] = so_m[f] = smid_m[f] = ph_m[f] = pi_m[f] = (T)0; }
-
-  for (int p = z0 - 1; p <= zend; ++p) {
-    const int buf = (p - z0 + 1) & 1;
-    const int zw = p < 0 ? p + n : (p >= n ? p - n : p);
-    const size_t zoff = (size_t)zw * nn;
-    T cur_ph[NF], cur_pi[NF];
-    // own cell
-    if (active) {
-      const size_t o = zoff + (size_t)wy * n + wx;
+  __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode) {
+    k = prestage(bg, d, mode);
+    pk = P::prep(d.params);
+    V0 = 0.0;
+    if constexpr (PREC == PREC_SPLIT) {
+      cdrift = (T)k.c; kD = (T)k.kD; kV = (T)k.kV;
+      double phi0p[NF], pi0p[NF], dV0[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        T ph = phi_in[f * S + o], pv = pi_in[f * S + o];
-        if constexpr (PREC == PREC_SPLIT) { ph -= mu_phi[f]; pv -= mu_pi[f]; }
-        cur_pi[f] = pv;
-        cur_ph[f] = fma(cdrift, pv, ph);
-        sm[buf][f][ly + 1][lx + 1] = cur_ph[f];
+        // re-centring: the float means mu move into the float64 background
+        mu_phi[f] = (float)bg.mu_phi[f];
+        mu_pi[f] = (float)bg.mu_pi[f];
+        phi0p[f] = bg.phi0[f] + (double)mu_phi[f];
+        pi0p[f] = bg.pi0[f] + (double)mu_pi[f];
+        phi0s[f] = fma(k.c, pi0p[f], phi0p[f]);   // background drift
+        shiftK[f] = 0;
       }
-    }
-    // halo cells
-    if (tid < nhalo) {
-      const size_t o = zoff + (size_t)hgy * n + hgx;
+      P::eval(pk, phi0s, dV0, V0);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)  // background kick (D[phi0] = 0)
+        pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], pi0p[f]) : pi0p[f];
+      sk = P::split_prep(d.params, phi0s);
+    } else {
+      cdrift = k.c; kD = k.kD; kV = k.kV;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        T ph = phi_in[f * S + o], pv = pi_in[f * S + o];
-        if constexpr (PREC == PREC_SPLIT) { ph -= mu_phi[f]; pv -= mu_pi[f]; }
-        sm[buf][f][hy + 1][hx + 1] = fma(cdrift, pv, ph);
+        mu_phi[f] = 0; mu_pi[f] = 0; phi0s[f] = 0; pi0s[f] = 0;
+        shiftK[f] = (T)bg.shift[f];
       }
-    }
-    __syncthreads();
-    T so_new[NF], smid_new[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const T ctr = sm[buf][f][ly + 1][lx + 1];
-      const T faces = (sm[buf][f][ly][lx + 1] + sm[buf][f][ly + 2][lx + 1]) +
-                      (sm[buf][f][ly + 1][lx] + sm[buf][f][ly + 1][lx + 2]);
-      if constexpr (CORNERS) {
-        const T corners = (sm[buf][f][ly][lx] + sm[buf][f][ly][lx + 2]) +
-                          (sm[buf][f][ly + 2][lx] + sm[buf][f][ly + 2][lx + 2]);
-        smid_new[f] = fma(c2, corners, fma(c1, faces, c0 * ctr));
-        so_new[f] = fma(c3, corners, fma(c2, faces, c1 * ctr));
-      } else {
-        smid_new[f] = fma(c0, ctr, faces);
-        so_new[f] = ctr;
-      }
-    }
-    if (p >= z0 + 1 && valid) {
-      // output plane z = p - 1
-      const int z = p - 1;
-      const size_t o = (size_t)z * nn + (size_t)gy * n + gx;
-      T D[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) D[f] = (so_mm[f] + so_new[f]) + smid_m[f];
-      if (mode == MODE_SWEEP) {
-        T pin[NF];
-        if constexpr (PREC == PREC_FP64) {
-          double dV[NF], V;
-          P::eval(pk, ph_m, dV, V);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            pin[f] = fma(kD, D[f], fma(-kV, dV[f], pi_m[f]));
-            acc[SL::PI2 + f] = fma(pin[f], pin[f], acc[SL::PI2 + f]);
-            acc[SL::PHID + f] = fma(ph_m[f], D[f], acc[SL::PHID + f]);
-          }
-          acc[SL::V] += V;
-        } else {
-          float dVd[NF], dVv;
-          P::diff(sk, ph_m, dVd, dVv);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            pin[f] = fmaf(kD, D[f], fmaf(-kV, dVd[f], pi_m[f]));
-            acc[SL::DPI + f] += pin[f];
-            acc[SL::DPI2 + f] = fmaf(pin[f], pin[f], acc[SL::DPI2 + f]);
-            acc[SL::PHID + f] = fmaf(ph_m[f], D[f], acc[SL::PHID + f]);
-            acc[SL::DPHI + f] += ph_m[f];
-            acc[SL::DPHI2 + f] = fmaf(ph_m[f], ph_m[f], acc[SL::DPHI2 + f]);
-          }
-          acc[SL::V] += dVv;
-        }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          phi_out[f * S + o] = ph_m[f];
-          pi_out[f * S + o] = pin[f];
-        }
-      } else {  // flush: drift only, pi unchanged
-        if constexpr (PREC == PREC_FP64) {
-          double dV[NF], V;
-          P::eval(pk, ph_m, dV, V);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            acc[SL::PI2 + f] = fma(pi_m[f], pi_m[f], acc[SL::PI2 + f]);
-            acc[SL::PHID + f] = fma(ph_m[f], D[f], acc[SL::PHID + f]);
-            const T dd = ph_m[f] - shiftK[f];
-            acc[SL::DPHI + f] += dd;
-            acc[SL::DPHI2 + f] = fma(dd, dd, acc[SL::DPHI2 + f]);
-          }
-          acc[SL::V] += V;
-        } else {
-          float dVd[NF], dVv;
-          P::diff(sk, ph_m, dVd, dVv);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            acc[SL::DPI + f] += pi_m[f];
-            acc[SL::DPI2 + f] = fmaf(pi_m[f], pi_m[f], acc[SL::DPI2 + f]);
-            acc[SL::PHID + f] = fmaf(ph_m[f], D[f], acc[SL::PHID + f]);
-            acc[SL::DPHI + f] += ph_m[f];
-            acc[SL::DPHI2 + f] = fmaf(ph_m[f], ph_m[f], acc[SL::DPHI2 + f]);
-          }
-          acc[SL::V] += dVv;
-        }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) phi_out[f * S + o] = ph_m[f];
-      }
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      so_mm[f] = so_m[f];
-      so_m[f] = so_new[f];
-      smid_m[f] = smid_new[f];
-      ph_m[f] = cur_ph[f];
-      pi_m[f] = cur_pi[f];
     }
   }
 
-  // ---- block partials -------------------------------------------------------
-  double accd[NQ];
+  // The kick of Phi_H3 and the per-site sums for one site.
+  //   phj: drifted fields, D: Laplacian, pim: momenta -> pin: new momenta
+  __device__ __forceinline__ void site(int mode, const T (&phj)[NF], const T (&D)[NF],
+                                       const T (&pim)[NF], T (&pin)[NF], T* ps) const {
+    if constexpr (PREC == PREC_FP64) {
+      double dV[NF], V;
+      P::eval(pk, phj, dV, V);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) accd[q] = (double)acc[q];
+      for (int f = 0; f < NF; ++f) {
+        if (mode == MODE_SWEEP) {
+          pin[f] = madd(kD, D[f], madd(-kV, (T)dV[f], pim[f]));
+          ps[SL::PI2 + f] = madd(pin[f], pin[f], ps[SL::PI2 + f]);
+        } else {
+          pin[f] = pim[f];
+          ps[SL::PI2 + f] = madd(pim[f], pim[f], ps[SL::PI2 + f]);
+          const T dd = phj[f] - shiftK[f];
+          ps[SL::DPHI + f] += dd;
+          ps[SL::DPHI2 + f] = madd(dd, dd, ps[SL::DPHI2 + f]);
+        }
+        ps[SL::PHID + f] = madd(phj[f], D[f], ps[SL::PHID + f]);
+      }
+      ps[SL::V] += V;
+    } else {
+      float dVd[NF], dVv;
+      P::diff(sk, phj, dVd, dVv);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        pin[f] = (mode == MODE_SWEEP) ? madd(kD, D[f], madd(-kV, dVd[f], pim[f])) : pim[f];
+        ps[SL::DPI + f] += pin[f];
+        ps[SL::DPI2 + f] = madd(pin[f], pin[f], ps[SL::DPI2 + f]);
+        ps[SL::PHID + f] = madd(phj[f], D[f], ps[SL::PHID + f]);
+        ps[SL::DPHI + f] += phj[f];
+        ps[SL::DPHI2 + f] = madd(phj[f], phj[f], ps[SL::DPHI2 + f]);
+      }
+      ps[SL::V] += dVv;
+    }
+  }
+};
+
+// Error-free addition of float pairs (hi, lo): TwoSum on the high parts.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (bh - bp);
+  lo = (lo + bl) + err;
+  hi = s;
+}
+
+// Block sums of the float path without the FP64 pipe in the hot part: each
+// thread's Kahan pair (s, -c) goes through a warp butterfly of float pairs;
+// lane 0 of each warp widens its pair to one double; NQ threads add the 8
+// warps in order.  Result in out[0..NQ) (shared).
+template <int NQ>
+__device__ __forceinline__ void block_sum_pairs(const Acc<float>* acc, double* sred,
+                                                double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    float hi = acc[q].s, lo = -acc[q].c;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, hi, m);
+      const float bl = __shfl_xor_sync(0xffffffffu, lo, m);
+      pair_add(hi, lo, bh, bl);
+    }
+    if (lane == 0) sred[warp * NQ + q] = (double)hi + (double)lo;
+  }
   __syncthreads();
-  block_sum<NQ>(accd, sred, sout);
+  if (threadIdx.x < NQ) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += sred[w * NQ + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Block sums of a kernel: float64 butterfly for the FP64 form (per-thread
+// double sums), float pairs for the split form.
+template <int PREC, int NQ, typename T>
+__device__ __forceinline__ void block_partials(const Acc<T>* acc, const T* accd_s, double* sred,
+                                               double* sout) {
+  __syncthreads();
+  if constexpr (PREC == PREC_FP64) {
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = (double)accd_s[q];
+    block_sum<NQ>(v, sred, sout);
+  } else {
+    block_sum_pairs<NQ>(reinterpret_cast<const Acc<float>*>(acc), sred, sout);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block finish: partials, ticket, and (last block) the background update.
+// sout holds this block's NQ sums on entry.
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC, typename C>
+__device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int mode, int cta,
+                                             double* sred, double* sout, int* s_last) {
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  const int tid = threadIdx.x;
   if (tid < NQ) d.partials[(size_t)cta * kNQ + tid] = sout[tid];
   __threadfence();
   __syncthreads();
   if (tid == 0) {
     const unsigned int t = atomicAdd(d.ticket, 1u);
-    s_last = (t == (unsigned int)(d.ncta - 1));
+    *s_last = (t == (unsigned int)(d.ncta - 1));
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!*s_last) return;
   __threadfence();
 
-  // ---- last block: fixed-order fold of the partials -----------------------
+  // ---- last block: fixed-order fold of the partials ------------------------
   double tot[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -410,7 +364,9 @@ sweep_kernel(const LaunchTable tab) {
   block_sum<NQ>(tot, sred, sout);
   if (tid != 0) return;
 
-  Background nb = *bgp;  // (identical to bg: nobody else writes it during the launch)
+  Background* bgp = d.bg;
+  const Background bg = *bgp;
+  Background nb = bg;
   const double Sd = (double)d.S;
   double sum_pi2 = 0.0, sum_phiD = 0.0, sum_V = 0.0;
   double fpi2[NF], fphiD[NF], fdphi[NF], fdphi2[NF];
@@ -427,16 +383,18 @@ sweep_kernel(const LaunchTable tab) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       // sum (pi0 + dpi)^2 = S pi0^2 + 2 pi0 sum dpi + sum dpi^2
-      fpi2[f] = fma(Sd * pi0s[f], pi0s[f], fma(2.0 * pi0s[f], sout[SL::DPI + f], sout[SL::DPI2 + f]));
+      fpi2[f] = fma(Sd * cx.pi0s[f], cx.pi0s[f],
+                    fma(2.0 * cx.pi0s[f], sout[SL::DPI + f], sout[SL::DPI2 + f]));
       fphiD[f] = sout[SL::PHID + f];  // sum (phi0 + d) D[d] = sum d D[d]  (sum D = 0)
       fdphi[f] = sout[SL::DPHI + f];
       fdphi2[f] = sout[SL::DPHI2 + f];
     }
-    sum_V = fma(Sd, V0, sout[SL::V]);  // sum V = S V(phi0) + sum dV
+    sum_V = fma(Sd, cx.V0, sout[SL::V]);  // sum V = S V(phi0) + sum dV
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) { sum_pi2 += fpi2[f]; sum_phiD += fphiD[f]; }
 
+  const Coef& k = cx.k;
   double a = k.a, pa = k.pa;
   bool ok = is_fin(sum_pi2) && is_fin(sum_phiD) && is_fin(sum_V);
   if (mode == MODE_SWEEP) {
@@ -467,7 +425,7 @@ sweep_kernel(const LaunchTable tab) {
       nb.s_pi2[f] = fpi2[f];
       nb.s_phiD[f] = fphiD[f];
       // shifted-data mean and variance: K = shift (FP64) or phi0 (split)
-      const double K = (PREC == PREC_FP64) ? bg.shift[f] : phi0s[f];
+      const double K = (PREC == PREC_FP64) ? bg.shift[f] : cx.phi0s[f];
       const double m1 = fdphi[f] / Sd;
       nb.mean[f] = K + m1;
       nb.var[f] = fdphi2[f] / Sd - m1 * m1;
@@ -483,13 +441,13 @@ sweep_kernel(const LaunchTable tab) {
   if constexpr (PREC == PREC_SPLIT) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      nb.phi0[f] = phi0s[f];
+      nb.phi0[f] = cx.phi0s[f];
       nb.mu_phi[f] = fdphi[f] / Sd;
       if (mode == MODE_SWEEP) {
-        nb.pi0[f] = pi0s[f];
+        nb.pi0[f] = cx.pi0s[f];
         nb.mu_pi[f] = sout[SL::DPI + f] / Sd;
       }
-      ok = ok && is_fin(phi0s[f]) && is_fin(pi0s[f]);
+      ok = ok && is_fin(cx.phi0s[f]) && is_fin(cx.pi0s[f]);
     }
   }
   ok = ok && is_fin(a) && is_fin(pa);
@@ -502,21 +460,838 @@ sweep_kernel(const LaunchTable tab) {
   __threadfence();
 }
 
-// Launch helper: dispatch (model, stencil) at runtime to a template instance.
+__device__ __forceinline__ int member_of(const LaunchTable& tab, int b) {
+  int lo = 0, hi = tab.count - 1;
+  while (lo < hi) {  // largest m with cta_offset[m] <= b
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab.cta_offset[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// ---------------------------------------------------------------------------
+// TMA / mbarrier primitives (inline PTX, sm_90+).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: gives up after ~2^31 clocks (about a second) and reports it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int STENCIL> struct StencilW {
+  static constexpr bool kCorners = (STENCIL == 27);
+};
+
+// ---------------------------------------------------------------------------
+// TMA-staged sweep (n % 32 == 0).  256 threads = 8 warps; warp w owns tile row
+// y0 + w, lane l owns sites x0 + l*VX .. +VX-1.
+// ---------------------------------------------------------------------------
+template <int MODEL, int STENCIL, int PREC, int VX>
+__global__ void __launch_bounds__(kThreads, 2) sweep_tma(const LaunchTable tab) {
+  using C = Ctx<MODEL, PREC>;
+  using T = typename C::T;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int TY = kMaxTY;          // 8 rows, one per warp
+  constexpr int TX = 32 * VX;         // tile width
+  constexpr int ROWS = TY + 2;        // with the two halo rows
+  constexpr int NSLOT = 3;
+  constexpr uint32_t kPlaneBytes = 2u * NF * ROWS * TX * sizeof(T);
+
+  __shared__ __align__(128) T stage[NSLOT][2][NF][ROWS][TX];   // [slot][phi/pi][f][row][x]
+  __shared__ T colb[NSLOT][NF][2][ROWS];                        // halo columns x0-1, x0+TX
+  __shared__ __align__(8) uint64_t mbar[NSLOT];
+  __shared__ double sred[(kThreads / 32) * NQ];
+  __shared__ double sout[NQ];
+  __shared__ int s_last, s_fault;
+
+  const int mem = member_of(tab, blockIdx.x);
+  const SimDesc& d = *tab.desc[mem];
+  const int cta = blockIdx.x - tab.cta_offset[mem];
+  const Background& bgr = *d.bg;
+  const int mode = bgr.mode;
+  if (mode == MODE_IDLE) return;
+
+  const int n = d.n;
+  const int tile = cta % (d.tiles_x * d.tiles_y);
+  const int zch = cta / (d.tiles_x * d.tiles_y);
+  const int x0 = (tile % d.tiles_x) * TX;
+  const int y0 = (tile / d.tiles_x) * TY;
+  const int z0 = zch * d.zc;
+  const int zend = min(n, z0 + d.zc);
+  const int Q = zend - z0 + 2;                 // planes z0-1 .. zend
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, ly = tid >> 5;
+  const int gx = x0 + lane * VX, gy = y0 + ly;
+  const size_t S = (size_t)d.S;
+  const size_t nn = (size_t)n * n;
+
+  __shared__ C s_ctx;   // scalar context: computed once, by one thread (FP64 pipe is scarce)
+  if (threadIdx.x == 0) s_ctx.init(bgr, d, mode);
+  __syncthreads();
+  const C cx = s_ctx;
+  const int ib = bgr.cur;  // bit0: phi buffer, bit1: pi buffer
+  const T* __restrict__ phi_in = (const T*)d.phi[ib & 1];
+  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
+  const T* __restrict__ pi_in = (const T*)d.pi[(ib >> 1) & 1];
+  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
+  const CUtensorMap* tphi_main = &d.tmap[ib & 1][0];
+  const CUtensorMap* tphi_row = &d.tmap[ib & 1][1];
+  const CUtensorMap* tpi_main = &d.tmap[2 + ((ib >> 1) & 1)][0];
+  const CUtensorMap* tpi_row = &d.tmap[2 + ((ib >> 1) & 1)][1];
+  const int yl = wrapi(y0 - 1, n), yh = wrapi(y0 + TY, n);
+
+  // stencil weights (Eq. D): 7pt (-6, 1, 0, 0); iso27 (-128, 14, 3, 1)/30
+  const T c0 = CORNERS ? (T)(-128.0 / 30.0) : (T)(-6.0);
+  const T c1 = CORNERS ? (T)(14.0 / 30.0) : (T)1.0;
+  const T c2 = CORNERS ? (T)(3.0 / 30.0) : (T)0.0;
+  const T c3 = CORNERS ? (T)(1.0 / 30.0) : (T)0.0;
+
+  // halo columns: threads [64, 64 + 2 ROWS): side = left/right, row = y0-1 .. y0+TY
+  const bool hcol = tid >= 64 && tid < 64 + 2 * ROWS;
+  int hc_side = 0, hc_row = 0;
+  size_t hc_off = 0;
+  if (hcol) {
+    const int t = tid - 64;
+    hc_side = t / ROWS;
+    hc_row = t % ROWS;
+    const int xx = hc_side == 0 ? wrapi(x0 - 1, n) : wrapi(x0 + TX, n);
+    const int yy = wrapi(y0 - 1 + hc_row, n);
+    hc_off = (size_t)yy * n + xx;
+  }
+  T sp[NF], sq[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) { sp[f] = 0; sq[f] = 0; }
+  auto load_col = [&](int p) {
+    if (hcol) {
+      const size_t o = (size_t)wrapi(p, n) * nn + hc_off;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) { sp[f] = phi_in[f * S + o]; sq[f] = pi_in[f * S + o]; }
+    }
+  };
+  auto issue = [&](int q) {  // one thread: all TMA copies of plane z0 - 1 + q
+    const int s = q % NSLOT;
+    const int zw = wrapi(z0 - 1 + q, n);
+    mbar_expect_tx(&mbar[s], kPlaneBytes);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int zz = f * n + zw;
+      tma_load_3d(&stage[s][0][f][1][0], tphi_main, x0, y0, zz, &mbar[s]);
+      tma_load_3d(&stage[s][0][f][0][0], tphi_row, x0, yl, zz, &mbar[s]);
+      tma_load_3d(&stage[s][0][f][ROWS - 1][0], tphi_row, x0, yh, zz, &mbar[s]);
+      tma_load_3d(&stage[s][1][f][1][0], tpi_main, x0, y0, zz, &mbar[s]);
+      tma_load_3d(&stage[s][1][f][0][0], tpi_row, x0, yl, zz, &mbar[s]);
+      tma_load_3d(&stage[s][1][f][ROWS - 1][0], tpi_row, x0, yh, zz, &mbar[s]);
+    }
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < NSLOT; ++s) mbar_init(&mbar[s], 1);
+    fence_mbar_init();
+    tensormap_acquire(tphi_main);
+    tensormap_acquire(tphi_row);
+    tensormap_acquire(tpi_main);
+    tensormap_acquire(tpi_row);
+    s_fault = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(0);
+    if (Q > 1) issue(1);
+  }
+  load_col(z0 - 1);
+
+  Acc<T> acc[NQ];
+  T accd_s[NQ];   // float64 path: plain per-thread sums
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { acc[q].zero(); accd_s[q] = (T)0; }
+  // rotating registers: part_m = S_off(z-1) + S_mid(z) of the plane z = p - 1
+  // awaiting output; so_m = S_off(p - 1) (iso27 only; it is phi* for 7pt);
+  // ph_m / pi_m = drifted phi and (re-centred) momentum of plane p - 1.
+  T part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int j = 0; j < VX; ++j) part_m[f][j] = so_m[f][j] = ph_m[f][j] = pi_m[f][j] = (T)0;
+
+  int q = 0;
+  for (; q < Q; ++q) {
+    const int s = q % NSLOT;
+    const int p = z0 - 1 + q;
+    if (!mbar_wait(&mbar[s], (uint32_t)((q / NSLOT) & 1))) atomicOr(&s_fault, 1);
+
+    // drift this plane in place: phi* = phi + c pi (re-centred in the split form)
+    T cur_ph[NF][VX], cur_pi[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T ph[VX], pv[VX];
+      vload<T, VX>(&stage[s][0][f][ly + 1][lane * VX], ph);
+      vload<T, VX>(&stage[s][1][f][ly + 1][lane * VX], pv);
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        if constexpr (PREC == PREC_SPLIT) { ph[j] -= cx.mu_phi[f]; pv[j] -= cx.mu_pi[f]; }
+        cur_pi[f][j] = pv[j];
+        cur_ph[f][j] = madd(cx.cdrift, pv[j], ph[j]);
+      }
+      vstore<T, VX>(&stage[s][0][f][ly + 1][lane * VX], cur_ph[f]);
+    }
+    if (tid < 64) {  // the two halo rows
+      const int r = tid < 32 ? 0 : ROWS - 1;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        T ph[VX], pv[VX];
+        vload<T, VX>(&stage[s][0][f][r][lane * VX], ph);
+        vload<T, VX>(&stage[s][1][f][r][lane * VX], pv);
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+          if constexpr (PREC == PREC_SPLIT) { ph[j] -= cx.mu_phi[f]; pv[j] -= cx.mu_pi[f]; }
+          ph[j] = madd(cx.cdrift, pv[j], ph[j]);
+        }
+        vstore<T, VX>(&stage[s][0][f][r][lane * VX], ph);
+      }
+    } else if (hcol) {  // the two halo columns
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        T ph = sp[f], pv = sq[f];
+        if constexpr (PREC == PREC_SPLIT) { ph -= cx.mu_phi[f]; pv -= cx.mu_pi[f]; }
+        colb[s][f][hc_side][hc_row] = madd(cx.cdrift, pv, ph);
+      }
+      if (q + 1 < Q) load_col(p + 1);
+    }
+    __syncthreads();
+    if (s_fault) break;
+    if (tid == 0 && q + 2 < Q) {
+      fence_proxy_async();   // generic writes to the recycled slot before the async copy
+      issue(q + 2);
+    }
+
+    T so_new[NF][VX], smid_new[NF][VX];   // S_off(p), S_mid(p)
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T dn[VX], up[VX];
+      vload<T, VX>(&stage[s][0][f][ly][lane * VX], dn);
+      vload<T, VX>(&stage[s][0][f][ly + 2][lane * VX], up);
+      T left = __shfl_up_sync(0xffffffffu, cur_ph[f][VX - 1], 1);
+      T right = __shfl_down_sync(0xffffffffu, cur_ph[f][0], 1);
+      if (lane == 0) left = colb[s][f][0][ly + 1];
+      if (lane == 31) right = colb[s][f][1][ly + 1];
+      T dl = 0, dr = 0, ul = 0, ur = 0;
+      if constexpr (CORNERS) {
+        dl = __shfl_up_sync(0xffffffffu, dn[VX - 1], 1);
+        dr = __shfl_down_sync(0xffffffffu, dn[0], 1);
+        ul = __shfl_up_sync(0xffffffffu, up[VX - 1], 1);
+        ur = __shfl_down_sync(0xffffffffu, up[0], 1);
+        if (lane == 0) { dl = colb[s][f][0][ly]; ul = colb[s][f][0][ly + 2]; }
+        if (lane == 31) { dr = colb[s][f][1][ly]; ur = colb[s][f][1][ly + 2]; }
+      }
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        const T ctr = cur_ph[f][j];
+        const T L = j > 0 ? cur_ph[f][j - 1] : left;
+        const T R = j < VX - 1 ? cur_ph[f][j + 1] : right;
+        const T faces = (dn[j] + up[j]) + (L + R);
+        if constexpr (CORNERS) {
+          const T DL = j > 0 ? dn[j - 1] : dl;
+          const T DR = j < VX - 1 ? dn[j + 1] : dr;
+          const T UL = j > 0 ? up[j - 1] : ul;
+          const T UR = j < VX - 1 ? up[j + 1] : ur;
+          const T corners = (DL + DR) + (UL + UR);
+          smid_new[f][j] = madd(c2, corners, madd(c1, faces, c0 * ctr));
+          so_new[f][j] = madd(c3, corners, madd(c2, faces, c1 * ctr));
+        } else {
+          smid_new[f][j] = madd(c0, ctr, faces);
+          so_new[f][j] = ctr;
+        }
+      }
+    }
+    if (q >= 2) {  // output plane z = p - 1
+      const size_t o = (size_t)(p - 1) * nn + (size_t)gy * n + gx;
+      // float: per-plane partials then Kahan; double: straight into the accumulators
+      T ps_local[NQ];
+      T* ps = ps_local;
+      if constexpr (PREC == PREC_FP64) {
+        ps = accd_s;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) ps_local[i] = (T)0;
+      }
+      T pin[NF][VX];
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        T phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          phj[f] = ph_m[f][j];
+          Dj[f] = part_m[f][j] + so_new[f][j];
+          pmj[f] = pi_m[f][j];
+        }
+        cx.site(mode, phj, Dj, pmj, pnj, ps);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) pin[f][j] = pnj[f];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        vstore<T, VX>(phi_out + f * S + o, ph_m[f]);
+        if (mode == MODE_SWEEP) vstore<T, VX>(pi_out + f * S + o, pin[f]);
+      }
+      if constexpr (PREC == PREC_SPLIT) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i].add(ps_local[i]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        part_m[f][j] = (CORNERS ? so_m[f][j] : ph_m[f][j]) + smid_new[f][j];
+        if constexpr (CORNERS) so_m[f][j] = so_new[f][j];
+        ph_m[f][j] = cur_ph[f][j];
+        pi_m[f][j] = cur_pi[f][j];
+      }
+  }
+
+  if (s_fault) {
+    // a TMA copy never completed: record it, drain what is in flight (bounded), stop
+    if (tid == 0) {
+      atomicOr(d.fault, 1);
+      for (int r = q; r < Q && r < q + 2; ++r)
+        mbar_wait(&mbar[r % NSLOT], (uint32_t)((r / NSLOT) & 1));
+    }
+    return;
+  }
+  block_partials<PREC, NQ, T>(acc, accd_s, sred, sout);
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sred, sout, &s_last);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Split-FP32 sweep (n % 32 == 0), barrier-free warp pipeline.
+//
+// The float32 form is bound by HBM, so its sweep avoids block-wide barriers in
+// the z loop.  Thread 0 keeps LEAD planes of TMA copies in flight in a
+// NSLOT-deep ring ("full" mbarriers, transaction counted).  Each warp owns one
+// tile row: it waits for the plane, drifts the three rows it needs (its own and
+// the two neighbours, re-centred and drifted on the fly, never written back),
+// releases the slot (one arrival per warp on the slot's "empty" mbarrier, on
+// which thread 0 waits before recycling it), then does the stencil, kick and
+// sums from registers.  Lanes 0 and 31 fetch the halo columns themselves, one
+// plane ahead.  Warps drift apart by up to NSLOT - LEAD planes.
+// ---------------------------------------------------------------------------
+template <int MODEL, int STENCIL, int VX>
+__global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTable tab) {
+  constexpr int PREC = PREC_SPLIT;
+  using C = Ctx<MODEL, PREC>;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int TY = kMaxTY;
+  constexpr int TX = 32 * VX;
+  constexpr int ROWS = TY + 2;
+  constexpr int NSLOT = 4, LEAD = 2;
+  constexpr int CR = CORNERS ? 3 : 1;           // halo-column rows a lane needs
+  constexpr uint32_t kPlaneBytes = 2u * NF * ROWS * TX * sizeof(float);
+
+  __shared__ __align__(128) float stage[NSLOT][2][NF][ROWS][TX];
+  __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT];
+  __shared__ double sred[(kThreads / 32) * NQ];
+  __shared__ double sout[NQ];
+  __shared__ int s_last, s_fault;
+  __shared__ C s_ctx;
+
+  const int mem = member_of(tab, blockIdx.x);
+  const SimDesc& d = *tab.desc[mem];
+  const int cta = blockIdx.x - tab.cta_offset[mem];
+  const Background& bgr = *d.bg;
+  const int mode = bgr.mode;
+  if (mode == MODE_IDLE) return;
+
+  const int n = d.n;
+  const int tile = cta % (d.tiles_x * d.tiles_y);
+  const int zch = cta / (d.tiles_x * d.tiles_y);
+  const int x0 = (tile % d.tiles_x) * TX;
+  const int y0 = (tile / d.tiles_x) * TY;
+  const int z0 = zch * d.zc;
+  const int zend = min(n, z0 + d.zc);
+  const int Q = zend - z0 + 2;                 // planes z0-1 .. zend
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, ly = tid >> 5;
+  const int gx = x0 + lane * VX, gy = y0 + ly;
+  const size_t S = (size_t)d.S;
+  const size_t nn = (size_t)n * n;
+  const int ib = bgr.cur;
+  const float* __restrict__ phi_in = (const float*)d.phi[ib & 1];
+  float* __restrict__ phi_out = (float*)d.phi[(ib & 1) ^ 1];
+  const float* __restrict__ pi_in = (const float*)d.pi[(ib >> 1) & 1];
+  float* __restrict__ pi_out = (float*)d.pi[((ib >> 1) & 1) ^ 1];
+  const CUtensorMap* tphi_main = &d.tmap[ib & 1][0];
+  const CUtensorMap* tphi_row = &d.tmap[ib & 1][1];
+  const CUtensorMap* tpi_main = &d.tmap[2 + ((ib >> 1) & 1)][0];
+  const CUtensorMap* tpi_row = &d.tmap[2 + ((ib >> 1) & 1)][1];
+  const int yl = wrapi(y0 - 1, n), yh = wrapi(y0 + TY, n);
+
+  if (tid == 0) {
+    s_ctx.init(bgr, d, mode);
+    for (int s = 0; s < NSLOT; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kThreads / 32);
+    }
+    fence_mbar_init();
+    tensormap_acquire(tphi_main);
+    tensormap_acquire(tphi_row);
+    tensormap_acquire(tpi_main);
+    tensormap_acquire(tpi_row);
+    s_fault = 0;
+  }
+  __syncthreads();
+  const C cx = s_ctx;
+  // re-centring folded into the drift: phi* = phi + c pi - (mu_phi + c mu_pi)
+  float Mf[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Mf[f] = madd(cx.cdrift, cx.mu_pi[f], cx.mu_phi[f]);
+  const float c0 = CORNERS ? (float)(-128.0 / 30.0) : -6.0f;
+  const float c1 = CORNERS ? (float)(14.0 / 30.0) : 1.0f;
+  const float c2 = CORNERS ? (float)(3.0 / 30.0) : 0.0f;
+  const float c3 = CORNERS ? (float)(1.0 / 30.0) : 0.0f;
+
+  int issued = 0;   // planes whose copies thread 0 has issued
+  auto issue = [&](int q) {
+    const int s = q % NSLOT;
+    const int zw = wrapi(z0 - 1 + q, n);
+    mbar_expect_tx(&full[s], kPlaneBytes);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int zz = f * n + zw;
+      tma_load_3d(&stage[s][0][f][1][0], tphi_main, x0, y0, zz, &full[s]);
+      tma_load_3d(&stage[s][0][f][0][0], tphi_row, x0, yl, zz, &full[s]);
+      tma_load_3d(&stage[s][0][f][ROWS - 1][0], tphi_row, x0, yh, zz, &full[s]);
+      tma_load_3d(&stage[s][1][f][1][0], tpi_main, x0, y0, zz, &full[s]);
+      tma_load_3d(&stage[s][1][f][0][0], tpi_row, x0, yl, zz, &full[s]);
+      tma_load_3d(&stage[s][1][f][ROWS - 1][0], tpi_row, x0, yh, zz, &full[s]);
+    }
+  };
+  if (tid == 0) {
+    for (; issued < LEAD && issued < Q; ++issued) issue(issued);
+  }
+
+  // halo columns: lane 0 the left one (x0 - 1), lane 31 the right one (x0 + TX)
+  const bool edge = (lane == 0) || (lane == 31);
+  const int ex = lane == 0 ? wrapi(x0 - 1, n) : wrapi(x0 + TX, n);
+  size_t eoff[CR];
+#pragma unroll
+  for (int r = 0; r < CR; ++r) eoff[r] = (size_t)wrapi(gy + r - (CR - 1) / 2, n) * n + ex;
+  float ep[NF][CR], eq[NF][CR];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int r = 0; r < CR; ++r) { ep[f][r] = 0.f; eq[f][r] = 0.f; }
+  auto load_edge = [&](int p) {
+    if (edge) {
+      const size_t zoff = (size_t)wrapi(p, n) * nn;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int r = 0; r < CR; ++r) {
+          ep[f][r] = phi_in[f * S + zoff + eoff[r]];
+          eq[f][r] = pi_in[f * S + zoff + eoff[r]];
+        }
+    }
+  };
+  load_edge(z0 - 1);
+
+  Acc<float> acc[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) acc[i].zero();
+  float part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int j = 0; j < VX; ++j) part_m[f][j] = so_m[f][j] = ph_m[f][j] = pi_m[f][j] = 0.f;
+
+  int q = 0;
+  for (; q < Q; ++q) {
+    // every exit decision is taken by the whole warp (shuffles and __syncwarp follow)
+    if (__any_sync(0xffffffffu, s_fault != 0)) break;
+    const int s = q % NSLOT;
+    const int p = z0 - 1 + q;
+    // producer: recycle the slot of plane q + LEAD - NSLOT once every warp released it
+    if (tid == 0 && issued < Q && issued == q + LEAD) {
+      const int r = issued - NSLOT;
+      if (r >= 0 && !mbar_wait(&empty[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) {
+        atomicOr(&s_fault, 1);
+      } else {
+        issue(issued);
+        ++issued;
+      }
+    }
+    const bool ready = mbar_wait(&full[s], (uint32_t)((q / NSLOT) & 1));
+    if (!__all_sync(0xffffffffu, ready)) {
+      if (lane == 0) atomicOr(&s_fault, 1);
+      break;
+    }
+    // the three rows of this warp, drifted in registers
+    float cur_ph[NF][VX], cur_pi[NF][VX], dn[NF][VX], up[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      float a[VX], b[VX];
+      vload<float, VX>(&stage[s][0][f][ly + 1][lane * VX], a);
+      vload<float, VX>(&stage[s][1][f][ly + 1][lane * VX], b);
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        cur_pi[f][j] = b[j] - cx.mu_pi[f];
+        cur_ph[f][j] = madd(cx.cdrift, b[j], a[j]) - Mf[f];
+      }
+      vload<float, VX>(&stage[s][0][f][ly][lane * VX], a);
+      vload<float, VX>(&stage[s][1][f][ly][lane * VX], b);
+#pragma unroll
+      for (int j = 0; j < VX; ++j) dn[f][j] = madd(cx.cdrift, b[j], a[j]) - Mf[f];
+      vload<float, VX>(&stage[s][0][f][ly + 2][lane * VX], a);
+      vload<float, VX>(&stage[s][1][f][ly + 2][lane * VX], b);
+#pragma unroll
+      for (int j = 0; j < VX; ++j) up[f][j] = madd(cx.cdrift, b[j], a[j]) - Mf[f];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with the slot
+    float el[NF][CR];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int r = 0; r < CR; ++r) el[f][r] = madd(cx.cdrift, eq[f][r], ep[f][r]) - Mf[f];
+    if (q + 1 < Q) load_edge(p + 1);
+
+    float so_new[NF][VX], smid_new[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      float left = __shfl_up_sync(0xffffffffu, cur_ph[f][VX - 1], 1);
+      float right = __shfl_down_sync(0xffffffffu, cur_ph[f][0], 1);
+      if (lane == 0) left = el[f][(CR - 1) / 2];
+      if (lane == 31) right = el[f][(CR - 1) / 2];
+      float dl = 0.f, dr = 0.f, ul = 0.f, ur = 0.f;
+      if constexpr (CORNERS) {
+        dl = __shfl_up_sync(0xffffffffu, dn[f][VX - 1], 1);
+        dr = __shfl_down_sync(0xffffffffu, dn[f][0], 1);
+        ul = __shfl_up_sync(0xffffffffu, up[f][VX - 1], 1);
+        ur = __shfl_down_sync(0xffffffffu, up[f][0], 1);
+        if (lane == 0) { dl = el[f][0]; ul = el[f][CR - 1]; }
+        if (lane == 31) { dr = el[f][0]; ur = el[f][CR - 1]; }
+      }
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        const float ctr = cur_ph[f][j];
+        const float L = j > 0 ? cur_ph[f][j - 1] : left;
+        const float R = j < VX - 1 ? cur_ph[f][j + 1] : right;
+        const float faces = (dn[f][j] + up[f][j]) + (L + R);
+        if constexpr (CORNERS) {
+          const float DL = j > 0 ? dn[f][j - 1] : dl;
+          const float DR = j < VX - 1 ? dn[f][j + 1] : dr;
+          const float UL = j > 0 ? up[f][j - 1] : ul;
+          const float UR = j < VX - 1 ? up[f][j + 1] : ur;
+          const float corners = (DL + DR) + (UL + UR);
+          smid_new[f][j] = madd(c2, corners, madd(c1, faces, c0 * ctr));
+          so_new[f][j] = madd(c3, corners, madd(c2, faces, c1 * ctr));
+        } else {
+          smid_new[f][j] = madd(c0, ctr, faces);
+          so_new[f][j] = ctr;
+        }
+      }
+    }
+    if (q >= 2) {  // output plane z = p - 1
+      const size_t o = (size_t)(p - 1) * nn + (size_t)gy * n + gx;
+      float ps[NQ];
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) ps[i] = 0.f;
+      float pin[NF][VX];
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        float phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          phj[f] = ph_m[f][j];
+          Dj[f] = part_m[f][j] + so_new[f][j];
+          pmj[f] = pi_m[f][j];
+        }
+        cx.site(mode, phj, Dj, pmj, pnj, ps);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) pin[f][j] = pnj[f];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        vstore<float, VX>(phi_out + f * S + o, ph_m[f]);
+        if (mode == MODE_SWEEP) vstore<float, VX>(pi_out + f * S + o, pin[f]);
+      }
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) acc[i].add(ps[i]);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int j = 0; j < VX; ++j) {
+        part_m[f][j] = (CORNERS ? so_m[f][j] : ph_m[f][j]) + smid_new[f][j];
+        if constexpr (CORNERS) so_m[f][j] = so_new[f][j];
+        ph_m[f][j] = cur_ph[f][j];
+        pi_m[f][j] = cur_pi[f][j];
+      }
+  }
+
+  block_partials<PREC, NQ, float>(acc, nullptr, sred, sout);
+  if (s_fault) {
+    // a copy or a release never completed: record it, drain issued copies (bounded), stop
+    if (tid == 0) {
+      atomicOr(d.fault, 1);
+      for (int r = q; r < issued; ++r) mbar_wait(&full[r % NSLOT], (uint32_t)((r / NSLOT) & 1));
+    }
+    return;
+  }
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sred, sout, &s_last);
+}
+
+// ---------------------------------------------------------------------------
+// Plain-load sweep (any n): one site per thread, modular indices, ragged tiles.
+// ---------------------------------------------------------------------------
+template <int MODEL, int STENCIL, int PREC>
+__global__ void __launch_bounds__(kThreads, 2) sweep_plain(const LaunchTable tab) {
+  using C = Ctx<MODEL, PREC>;
+  using T = typename C::T;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+
+  __shared__ T sm[2][NF][kMaxTY + 2][kMaxTXT + 2];
+  __shared__ double sred[(kThreads / 32) * NQ];
+  __shared__ double sout[NQ];
+  __shared__ int s_last;
+
+  const int mem = member_of(tab, blockIdx.x);
+  const SimDesc& d = *tab.desc[mem];
+  const int cta = blockIdx.x - tab.cta_offset[mem];
+  const Background& bgr = *d.bg;
+  const int mode = bgr.mode;
+  if (mode == MODE_IDLE) return;
+
+  const int n = d.n;
+  const int TX = d.txt, TY = d.ty;
+  const int tile = cta % (d.tiles_x * d.tiles_y);
+  const int zch = cta / (d.tiles_x * d.tiles_y);
+  const int x0 = (tile % d.tiles_x) * TX;
+  const int y0 = (tile / d.tiles_x) * TY;
+  const int z0 = zch * d.zc;
+  const int zend = min(n, z0 + d.zc);
+  const int tid = threadIdx.x;
+  const bool active = tid < TX * TY;
+  const int lx = active ? tid % TX : 0;
+  const int ly = active ? tid / TX : 0;
+  const int gx = x0 + lx, gy = y0 + ly;
+  const bool valid = active && gx < n && gy < n;
+  const size_t own_off = (size_t)wrapi(gy, n) * n + wrapi(gx, n);
+  const size_t S = (size_t)d.S;
+  const size_t nn = (size_t)n * n;
+
+  __shared__ C s_ctx;   // scalar context: computed once, by one thread (FP64 pipe is scarce)
+  if (threadIdx.x == 0) s_ctx.init(bgr, d, mode);
+  __syncthreads();
+  const C cx = s_ctx;
+  const int ib = bgr.cur;
+  const T* __restrict__ phi_in = (const T*)d.phi[ib & 1];
+  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
+  const T* __restrict__ pi_in = (const T*)d.pi[(ib >> 1) & 1];
+  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
+
+  const T c0 = CORNERS ? (T)(-128.0 / 30.0) : (T)(-6.0);
+  const T c1 = CORNERS ? (T)(14.0 / 30.0) : (T)1.0;
+  const T c2 = CORNERS ? (T)(3.0 / 30.0) : (T)0.0;
+  const T c3 = CORNERS ? (T)(1.0 / 30.0) : (T)0.0;
+
+  // halo ring: (TX+2) cells below, (TX+2) above, TY left, TY right
+  const int nhalo = 2 * (TX + 2) + 2 * TY;
+  int hx = 0, hy = 0;
+  if (tid < nhalo) {
+    int t = tid;
+    if (t < TX + 2) { hx = t - 1; hy = -1; }
+    else if ((t -= TX + 2) < TX + 2) { hx = t - 1; hy = TY; }
+    else if ((t -= TX + 2) < TY) { hx = -1; hy = t; }
+    else { t -= TY; hx = TX; hy = t; }
+  }
+  const size_t halo_off = (size_t)wrapi(y0 + hy, n) * n + wrapi(x0 + hx, n);
+
+  T rp[NF], rq[NF], hp[NF], hq[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) { rp[f] = rq[f] = hp[f] = hq[f] = 0; }
+  auto load_raw = [&](int p) {
+    const size_t zoff = (size_t)wrapi(p, n) * nn;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (active) { rp[f] = phi_in[f * S + zoff + own_off]; rq[f] = pi_in[f * S + zoff + own_off]; }
+      if (tid < nhalo) { hp[f] = phi_in[f * S + zoff + halo_off]; hq[f] = pi_in[f * S + zoff + halo_off]; }
+    }
+  };
+
+  Acc<T> acc[NQ];
+  T accd_s[NQ];   // float64 path: plain per-thread sums
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { acc[q].zero(); accd_s[q] = (T)0; }
+  T part_m[NF], so_m[NF], ph_m[NF], pi_m[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) part_m[f] = so_m[f] = ph_m[f] = pi_m[f] = (T)0;
+
+  load_raw(z0 - 1);
+  for (int p = z0 - 1; p <= zend; ++p) {
+    const int buf = (p - z0 + 1) & 1;
+    T cur_ph[NF], cur_pi[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T ph = rp[f], pv = rq[f];
+      if constexpr (PREC == PREC_SPLIT) { ph -= cx.mu_phi[f]; pv -= cx.mu_pi[f]; }
+      cur_pi[f] = pv;
+      cur_ph[f] = madd(cx.cdrift, pv, ph);
+      if (active) sm[buf][f][ly + 1][lx + 1] = cur_ph[f];
+      if (tid < nhalo) {
+        T h1 = hp[f], h2 = hq[f];
+        if constexpr (PREC == PREC_SPLIT) { h1 -= cx.mu_phi[f]; h2 -= cx.mu_pi[f]; }
+        sm[buf][f][hy + 1][hx + 1] = madd(cx.cdrift, h2, h1);
+      }
+    }
+    if (p < zend) load_raw(p + 1);
+    __syncthreads();
+    T so_new[NF], smid_new[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T ctr = sm[buf][f][ly + 1][lx + 1];
+      const T faces = (sm[buf][f][ly][lx + 1] + sm[buf][f][ly + 2][lx + 1]) +
+                      (sm[buf][f][ly + 1][lx] + sm[buf][f][ly + 1][lx + 2]);
+      if constexpr (CORNERS) {
+        const T corners = (sm[buf][f][ly][lx] + sm[buf][f][ly][lx + 2]) +
+                          (sm[buf][f][ly + 2][lx] + sm[buf][f][ly + 2][lx + 2]);
+        smid_new[f] = madd(c2, corners, madd(c1, faces, c0 * ctr));
+        so_new[f] = madd(c3, corners, madd(c2, faces, c1 * ctr));
+      } else {
+        smid_new[f] = madd(c0, ctr, faces);
+        so_new[f] = ctr;
+      }
+    }
+    if (p >= z0 + 1 && valid) {
+      const size_t o = (size_t)(p - 1) * nn + (size_t)gy * n + gx;
+      T ps_local[NQ];
+      T* ps = ps_local;
+      if constexpr (PREC == PREC_FP64) {
+        ps = accd_s;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) ps_local[i] = (T)0;
+      }
+      T Dj[NF], pnj[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) Dj[f] = part_m[f] + so_new[f];
+      cx.site(mode, ph_m, Dj, pi_m, pnj, ps);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        phi_out[f * S + o] = ph_m[f];
+        if (mode == MODE_SWEEP) pi_out[f * S + o] = pnj[f];
+      }
+      if constexpr (PREC == PREC_SPLIT) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i].add(ps_local[i]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      part_m[f] = (CORNERS ? so_m[f] : ph_m[f]) + smid_new[f];
+      if constexpr (CORNERS) so_m[f] = so_new[f];
+      ph_m[f] = cur_ph[f];
+      pi_m[f] = cur_pi[f];
+    }
+  }
+  block_partials<PREC, NQ, T>(acc, accd_s, sred, sout);
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sred, sout, &s_last);
+}
+
+// Launch helper: dispatch (model, stencil, path/vx) at runtime to an instance.
 template <int PREC>
-cudaError_t launch_sweep_impl(int model, int stencil, const LaunchTable& t, int grid,
-                              cudaStream_t s) {
+cudaError_t launch_sweep_impl(int model, int stencil, int vx, int tma, const LaunchTable& t,
+                              int grid, cudaStream_t s) {
   const dim3 g(grid), b(kThreads);
-#define PYCOOL_CASE(M, ST)                                               \
-  if (model == M && stencil == ST) {                                     \
-    sweep_kernel<M, ST, PREC><<<g, b, 0, s>>>(t);                        \
+#define PYCOOL_PLAIN(M, ST)                                              \
+  if (!tma && model == M && stencil == ST) {                             \
+    sweep_plain<M, ST, PREC><<<g, b, 0, s>>>(t);                         \
     return cudaGetLastError();                                           \
   }
-  PYCOOL_CASE(M_FREE, 7) PYCOOL_CASE(M_FREE, 27)
-  PYCOOL_CASE(M_CHAOTIC2, 7) PYCOOL_CASE(M_CHAOTIC2, 27)
-  PYCOOL_CASE(M_OSCILLON, 7) PYCOOL_CASE(M_OSCILLON, 27)
-  PYCOOL_CASE(M_QBALL, 7) PYCOOL_CASE(M_QBALL, 27)
-#undef PYCOOL_CASE
+#define PYCOOL_TMA(M, ST, V)                                             \
+  if constexpr (V * Pot<M>::NF * (PREC == PREC_FP64 ? 8 : 4) <= 16) {    \
+    if (tma && model == M && stencil == ST && vx == V) {                 \
+      if constexpr (PREC == PREC_SPLIT)                                  \
+        sweep_split_pipe<M, ST, V><<<g, b, 0, s>>>(t);                   \
+      else                                                               \
+        sweep_tma<M, ST, PREC, V><<<g, b, 0, s>>>(t);                    \
+      return cudaGetLastError();                                         \
+    }                                                                    \
+  }
+#define PYCOOL_FOR_MODELS(X, V)                                          \
+  X(M_FREE, 7 V) X(M_FREE, 27 V) X(M_CHAOTIC2, 7 V) X(M_CHAOTIC2, 27 V)  \
+  X(M_OSCILLON, 7 V) X(M_OSCILLON, 27 V) X(M_QBALL, 7 V) X(M_QBALL, 27 V)
+#define PYCOOL_NOV
+#define PYCOOL_V1 , 1
+#define PYCOOL_V2 , 2
+#define PYCOOL_V4 , 4
+  PYCOOL_FOR_MODELS(PYCOOL_PLAIN, PYCOOL_NOV)
+  PYCOOL_FOR_MODELS(PYCOOL_TMA, PYCOOL_V1)
+  PYCOOL_FOR_MODELS(PYCOOL_TMA, PYCOOL_V2)
+  if constexpr (PREC == PREC_SPLIT) { PYCOOL_FOR_MODELS(PYCOOL_TMA, PYCOOL_V4) }
+#undef PYCOOL_V4
+#undef PYCOOL_V2
+#undef PYCOOL_V1
+#undef PYCOOL_NOV
+#undef PYCOOL_FOR_MODELS
+#undef PYCOOL_TMA
+#undef PYCOOL_PLAIN
   return cudaErrorInvalidValue;
 }
 

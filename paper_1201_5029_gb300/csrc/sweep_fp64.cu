@@ -2,8 +2,8 @@
 #include "sweep.cuh"
 
 namespace pycool {
-cudaError_t launch_sweep_fp64(int model, int stencil, const LaunchTable& t, int grid,
+cudaError_t launch_sweep_fp64(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
                               cudaStream_t s) {
-  return launch_sweep_impl<PREC_FP64>(model, stencil, t, grid, s);
+  return launch_sweep_impl<PREC_FP64>(model, stencil, vx, tma, t, grid, s);
 }
 }  // namespace pycool

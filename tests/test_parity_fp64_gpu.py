@@ -190,3 +190,18 @@ def test_invalid_configs_rejected():
     with pytest.raises(P.PycoolError) as ei:
         P.Simulation(G.gpu_cfg(P, w, dt=1.0))
     assert ei.value.status == P.E_UNSTABLE_DT
+
+
+@pytest.mark.parametrize("name,n,order,steps", [
+    ("oscillon256", 64, 6, 3),    # TMA kernel, 2 sites per lane (double2)
+    ("preheat128", 64, 4, 4),     # TMA kernel, 1 site per lane, 2 fields
+    ("qball256", 64, 8, 2),
+    ("oscillon256", 96, 2, 5),    # TMA kernel, 96 = 3 x 32
+])
+@pytest.mark.parametrize("stencil", ["7pt", "iso27"])
+def test_tma_kernel_sizes(name, n, order, steps, stencil):
+    w = I.workload(name)
+    phi, pi = I.initial_fields(w, n=n)
+    gphi, gpi, ge = G.run_gpu(P, G.gpu_cfg(P, w, n=n, order=order, stencil=stencil), phi, pi, steps)
+    st, oe = G.run_oracle(G.oracle_cfg(w, n=n, order=order, stencil=stencil), phi, pi, steps)
+    _check(gphi, gpi, ge, st, oe)

@@ -19,6 +19,9 @@ import gpu_helpers as G  # noqa: E402
     ("preheat128", 4, 24, 20),
     ("oscillon256", 6, 20, 10),
     ("qball256", 8, 16, 6),
+    ("oscillon256", 6, 128, 2),   # TMA kernel, 4 sites per lane (float4)
+    ("preheat128", 4, 64, 5),     # TMA kernel, 2 sites per lane, 2 fields
+    ("qball256", 8, 96, 1),       # TMA kernel, 1 site per lane
 ])
 @pytest.mark.parametrize("stencil", ["7pt", "iso27"])
 def test_split_errors_against_oracle(name, order, n, steps, stencil):
