@@ -199,6 +199,60 @@ void pycool_destroy(pycool_sim* sim);
 
 /* Static description of a status code. */
 const char* pycool_strerror(pycool_status status);
+/* ---- allocation-free stage sweep ---------------------------------------------
+ * The paper has no counterpart to this call; it is a deployment convenience.
+ *
+ * For callers that cannot call cudaMalloc: code whose device memory belongs to
+ * another allocator (a framework's caching allocator, a pre-reserved arena
+ * that leaves nothing for cudaMalloc) and host loops that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.  The caller owns
+ * the field arrays; every other byte the sweep needs (background record,
+ * launch descriptor, per-block partial sums, ticket) lives in one file-scope
+ * device array of PYCOOL_NOALLOC_SCRATCH_BYTES, which every GPU that loads the
+ * library holds until the process exits.  No call here allocates.
+ *
+ * One call = one launch of the FP64 stage sweep of pycool_evolve:
+ *   flush == 0 : the fused sweep of stage `state->stage` (drift merged with the
+ *                pending half-stage, Laplacian, kick); reads phi_in, pi_in,
+ *                writes phi_out and pi_out.  The result is staggered
+ *                (state->h_prev != 0), as between the sweeps of pycool_evolve.
+ *   flush != 0 : the synchronising drift; reads phi_in, pi_in, writes phi_out
+ *                (pi is unchanged: use pi_in as the momentum; pi_out unused)
+ *                and fills state->obs.  With h_prev == 0 it only reduces
+ *                (phi_out becomes a copy of phi_in): start every run with such
+ *                a call, state->init_pa = 1 sets p_a from H = 0.
+ * A time step of order 2, 4, 6, 8 is 1, 3, 7, 15 non-flush calls; the caller
+ * swaps its two buffer pairs between calls.  Arrays: float64 device memory,
+ * [field][z][y][x], 16-byte aligned; config precision must be PYCOOL_FP64.
+ *
+ * Errors: E_INVALID for a bad config, bad pointers, or a lattice whose sweep
+ * needs more than pycool_noalloc_max_blocks() blocks (about n <= 512 for two
+ * fields); E_NONFINITE if a sum overflowed; E_CUDA / E_TIMEOUT as elsewhere.
+ * The call synchronises the stream (it reads the background record back).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array and it keeps the last call's contents (the call clears
+ * what must start at zero): calls whose work overlaps on the GPU, from two
+ * streams or two threads, race and must not be issued. */
+#define PYCOOL_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+typedef struct {
+  double a, pa, eta;      /* scale factor, its momentum, conformal time             */
+  double h_prev;          /* pending half-stage step (0 = synchronised)             */
+  double sum_pi2;         /* sum of pi^2 of the current momentum                    */
+  int64_t stage;          /* stage-table index of the next sweep                    */
+  int64_t steps_done;     /* completed time steps                                   */
+  int32_t init_pa;        /* in: 1 = the next flush sets p_a from H = 0             */
+  int32_t error;          /* out: 1 = a lattice sum was not finite                  */
+  pycool_observables obs; /* out, flush calls: observables of the synchronised state */
+} pycool_stage_state;
+
+/* Largest number of blocks (lattice tiles x z-chunks) a sweep may use here. */
+size_t pycool_noalloc_max_blocks(void);
+
+pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const double* phi_in,
+                                   const double* pi_in, double* phi_out, double* pi_out,
+                                   int32_t flush, pycool_stage_state* state, void* cuda_stream);
 
 #ifdef __cplusplus
 }

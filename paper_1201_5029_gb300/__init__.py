@@ -64,6 +64,14 @@ class pycool_energies_t(C.Structure):
                     steps_done=self.steps_done, sweeps_done=self.sweeps_done)
 
 
+class pycool_stage_state(C.Structure):
+    """Background record of the allocation-free sweep (pycool_sweep_noalloc)."""
+    _fields_ = [("a", C.c_double), ("pa", C.c_double), ("eta", C.c_double),
+                ("h_prev", C.c_double), ("sum_pi2", C.c_double), ("stage", C.c_int64),
+                ("steps_done", C.c_int64), ("init_pa", C.c_int32), ("error", C.c_int32),
+                ("obs", pycool_energies_t)]
+
+
 class pycool_ic(C.Structure):
     _fields_ = [("background", C.c_double * MAX_FIELDS), ("momentum", C.c_double * MAX_FIELDS),
                 ("noise", C.c_double), ("a0", C.c_double)]
@@ -108,6 +116,9 @@ def _load():
         "pycool_server_stats": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "pycool_server_destroy": (None, [P]),
+        "pycool_noalloc_max_blocks": (C.c_size_t, []),
+        "pycool_sweep_noalloc": (S, [C.POINTER(pycool_config), P, P, P, P, C.c_int32,
+                                     C.POINTER(pycool_stage_state), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name, None)
@@ -283,6 +294,20 @@ def pycool_kernel_launches(sim) -> int:
 
 def pycool_destroy(sim) -> None:
     lib.pycool_destroy(sim)
+
+
+def pycool_noalloc_max_blocks() -> int:
+    return int(lib.pycool_noalloc_max_blocks())
+
+
+def pycool_sweep_noalloc(cfg: pycool_config, phi_in, pi_in, phi_out, pi_out, flush: bool,
+                         state: pycool_stage_state, stream=None) -> int:
+    """One stage sweep (flush=False) or synchronising flush (flush=True) with no
+    device allocation; arrays are CUDA tensors.  Returns the status code."""
+    ptr = lambda t: None if t is None else C.c_void_p(int(t.data_ptr()))  # noqa: E731
+    return lib.pycool_sweep_noalloc(C.byref(cfg), ptr(phi_in), ptr(pi_in), ptr(phi_out),
+                                    ptr(pi_out), 1 if flush else 0, C.byref(state),
+                                    _stream_ptr(stream))
 
 
 # ---------------------------------------------------------------- convenience wrapper

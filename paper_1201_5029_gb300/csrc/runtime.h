@@ -24,6 +24,7 @@ Layout layout_for(const pycool_config& c);
 pycool_status validate(const pycool_config* c);
 void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state, char* ws);
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s);
+cudaError_t encode_tensor_maps(SimDesc& d);
 cudaError_t launch_arm(Background* bg, long long nsweeps, cudaStream_t s);
 void observables(const Background& b, const SimDesc& d, double mpl, double rho_r0,
                  double rho_m0, pycool_observables* out);
