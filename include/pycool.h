@@ -199,6 +199,59 @@ void pycool_destroy(pycool_sim* sim);
 
 /* Static description of a status code. */
 const char* pycool_strerror(pycool_status status);
+/* ---- serving: many simulations resident on one GPU ---------------------------
+ * The paper's multi-simulation use (Sec. 2.4: Delta-N from many runs with
+ * different initial values; Sec. 4: many lattices evolved simultaneously) as
+ * a continuous-batching server.  A server thread admits queued requests while
+ * the HBM budget and slot count allow, generates their initial fields on the
+ * device, and advances every resident simulation that shares a kernel instance
+ * with one launch per stage (CUDA graphs of several stages, rebuilt when the
+ * membership changes).  A request's result is bit-identical whether it ran
+ * alone or with others. */
+
+/* Initial-condition recipes generated on the device.  WHITE:
+ *   phi_i = background_i + noise N(0,1),  pi_i = momentum_i + noise N(0,1),
+ * with the normals from Philox4x32-10 (Salmon et al., SC'11), key = seed,
+ * counter = (e/4, array, 0, 0) for element e of array phi_1..phi_N, pi_1..pi_N,
+ * and Box-Muller on the uniforms (x + 1/2) 2^-32 (component e mod 4). */
+typedef enum { PYCOOL_IC_WHITE = 0 } pycool_ic_kind;
+
+typedef struct {
+  double background[PYCOOL_MAX_FIELDS];
+  double momentum[PYCOOL_MAX_FIELDS];
+  double noise;     /* rms of the white noise, >= 0                        */
+  double a0;        /* initial scale factor (<= 0 means 1)                 */
+} pycool_ic;
+
+/* Start a server that keeps up to max_slots simulations resident and reserves
+ * hbm_budget bytes of device memory for them (one arena, allocated here).
+ * The server owns one host thread and its own CUDA streams on the device that
+ * is current at this call.  E_NOMEM if the arena cannot be reserved. */
+pycool_status pycool_server_create(size_t hbm_budget, int32_t max_slots, pycool_server** out);
+
+/* Queue a simulation (cfg, initial-condition recipe, RNG seed, time steps);
+ * *ticket identifies it.  E_INVALID / E_UNSTABLE_DT for a bad config, E_NOMEM if
+ * it could never fit the budget.  Thread-safe; never blocks on the GPU. */
+pycool_status pycool_server_submit(pycool_server* srv, const pycool_config* cfg,
+                                   const pycool_ic* ic, uint64_t seed, int64_t steps,
+                                   uint64_t* ticket);
+
+/* Wait (at most timeout_s seconds; < 0 = no limit) for a ticket's result: the
+ * observables of its final, synchronised state.  Returns the run's status
+ * (OK, E_NONFINITE, ...), E_TIMEOUT if not finished in time (the ticket stays
+ * valid), E_NOT_FOUND for an unknown or already collected ticket.  Thread-safe. */
+pycool_status pycool_server_wait(pycool_server* srv, uint64_t ticket, double timeout_s,
+                                 pycool_observables* out);
+
+/* Latency percentiles (submission to result, seconds) of the completed
+ * requests, the aggregate site-updates per second between the first admission
+ * and the last completion, and the number of completed requests. */
+pycool_status pycool_server_stats(pycool_server* srv, double* p50_s, double* p99_s,
+                                  double* site_updates_per_s, int64_t* completed);
+
+/* Stop the server thread and release every resident simulation and the arena. */
+void pycool_server_destroy(pycool_server* srv);
+
 /* ---- allocation-free stage sweep ---------------------------------------------
  * The paper has no counterpart to this call; it is a deployment convenience.
  *

@@ -296,6 +296,50 @@ def pycool_destroy(sim) -> None:
     lib.pycool_destroy(sim)
 
 
+def make_ic(background: Sequence[float], momentum: Sequence[float], noise: float,
+            a0: float = 1.0) -> pycool_ic:
+    ic = pycool_ic()
+    for i, v in enumerate(background):
+        ic.background[i] = float(v)
+    for i, v in enumerate(momentum):
+        ic.momentum[i] = float(v)
+    ic.noise, ic.a0 = float(noise), float(a0)
+    return ic
+
+
+def pycool_server_create(hbm_budget: int, max_slots: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib.pycool_server_create(int(hbm_budget), int(max_slots), C.byref(h)),
+           "pycool_server_create")
+    return h
+
+
+def pycool_server_submit(srv, cfg: pycool_config, ic: pycool_ic, seed: int, steps: int) -> int:
+    t = C.c_uint64()
+    _check(lib.pycool_server_submit(srv, C.byref(cfg), C.byref(ic), int(seed), int(steps),
+                                    C.byref(t)), "pycool_server_submit")
+    return t.value
+
+
+def pycool_server_wait(srv, ticket: int, timeout_s: float = -1.0):
+    """Returns (status, observables dict); does not raise on a run's status."""
+    e = pycool_energies_t()
+    st = lib.pycool_server_wait(srv, int(ticket), float(timeout_s), C.byref(e))
+    return st, e
+
+
+def pycool_server_stats(srv) -> dict:
+    p50, p99, sus, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+    _check(lib.pycool_server_stats(srv, C.byref(p50), C.byref(p99), C.byref(sus), C.byref(n)),
+           "pycool_server_stats")
+    return dict(p50_s=p50.value, p99_s=p99.value, site_updates_per_s=sus.value,
+                completed=n.value)
+
+
+def pycool_server_destroy(srv) -> None:
+    lib.pycool_server_destroy(srv)
+
+
 def pycool_noalloc_max_blocks() -> int:
     return int(lib.pycool_noalloc_max_blocks())
 

@@ -148,6 +148,59 @@ def plane_wave(n: int, mode: Tuple[int, int, int], amplitude: float = 1.0,
     return amplitude * np.cos(arg)
 
 
+def philox4x32_10(c0, c1, c2, c3, k0: int, k1: int):
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) on numpy arrays of
+    32-bit counters held in uint64: ten rounds of
+      (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+    with the key advanced by (W0, W1) before every round but the first."""
+    M0, M1, W0, W1 = 0xD2511F53, 0xCD9E8D57, 0x9E3779B9, 0xBB67AE85
+    mask = np.uint64(0xFFFFFFFF)
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & mask for c in (c0, c1, c2, c3))
+    ka, kb = np.uint64(k0 & 0xFFFFFFFF), np.uint64(k1 & 0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            ka = np.uint64((int(ka) + W0) & 0xFFFFFFFF)
+            kb = np.uint64((int(kb) + W1) & 0xFFFFFFFF)
+        p0 = np.uint64(M0) * c0
+        p1 = np.uint64(M1) * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c0, c1, c2, c3 = hi1 ^ c1 ^ ka, lo1, hi0 ^ c3 ^ kb, lo0
+    return c0, c1, c2, c3
+
+
+def philox_normals(seed: int, arr: int, count: int) -> np.ndarray:
+    """Standard normals z_e, e = 0..count-1, of array `arr`: element e is
+    component e mod 4 of counter block e // 4 = (e//4, arr, 0, 0), key = seed;
+    uniforms u = (x + 1/2) 2^-32, Box-Muller on (u0, u1) and (u2, u3)."""
+    e = np.arange(count, dtype=np.uint64)
+    blk = e >> np.uint64(2)
+    comp = (e & np.uint64(3)).astype(np.int64)
+    r0, r1, r2, r3 = philox4x32_10(blk, np.full_like(blk, arr), np.zeros_like(blk),
+                                   np.zeros_like(blk), seed & 0xFFFFFFFF, seed >> 32)
+    a = np.where(comp < 2, r0, r2).astype(np.float64)
+    b = np.where(comp < 2, r1, r3).astype(np.float64)
+    s = 2.0 ** -32
+    u1, u2 = (a + 0.5) * s, (b + 0.5) * s
+    rad = np.sqrt(-2.0 * np.log(u1))
+    th = 2.0 * np.pi * u2
+    return np.where(comp & 1, rad * np.sin(th), rad * np.cos(th))
+
+
+def philox_white_ics(n: int, background, momentum, noise: float, seed: int
+                     ) -> Tuple[np.ndarray, np.ndarray]:
+    """The white-noise initial conditions a serving request generates on the
+    device: phi_i = bg_i + noise z (array i), pi_i = mom_i + noise z (array N+i)."""
+    nf = len(background)
+    S = n ** 3
+    phi = np.empty((nf, n, n, n), dtype=np.float64)
+    pi = np.empty((nf, n, n, n), dtype=np.float64)
+    for i in range(nf):
+        phi[i] = (background[i] + noise * philox_normals(seed, i, S)).reshape(n, n, n)
+        pi[i] = (momentum[i] + noise * philox_normals(seed, nf + i, S)).reshape(n, n, n)
+    return phi, pi
+
+
 def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson stream with the given rate."""
     rng = np.random.default_rng(seed)
