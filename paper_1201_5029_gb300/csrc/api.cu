@@ -128,8 +128,7 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.tma = L.geo.tma; d.vx = L.geo.vx; d.txt = L.geo.txt;
   d.tx = L.geo.tx; d.ty = L.geo.ty; d.zc = L.geo.zc;
   d.tiles_x = L.geo.tiles_x; d.tiles_y = L.geo.tiles_y;
-  d.zchunks = L.geo.zchunks; d.ncta = L.geo.ncta;
-  d.S = (int64_t)c.n * c.n * c.n;
+  d.zchunks = L.geo.zchunks; d.ncta = L.geo.ncta;  d.S = (int64_t)c.n * c.n * c.n;
   d.dt = c.dt;
   const double dx = c.L / c.n;
   d.dx2inv = 1.0 / (dx * dx);
@@ -399,6 +398,13 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
   sim->table.cta_offset[0] = 0;
   sim->table.cta_offset[1] = sim->L.geo.ncta;
   sim->table.desc[0] = sim->d_desc;
+  // set the kernel's shared-memory attribute now, not inside the graph capture
+  e = launch_sweep(sim->hdesc, sim->table, 0, sim->stream);
+  if (e != cudaSuccess) {
+    cuda_fail(sim, e, "kernel attributes");
+    pycool_destroy(sim);
+    return PYCOOL_E_CUDA;
+  }
   st = build_graph(sim);
   if (st != PYCOOL_OK) {
     pycool_destroy(sim);

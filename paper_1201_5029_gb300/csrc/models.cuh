@@ -92,32 +92,37 @@ template <> struct Pot<M_OSCILLON> {
     dV[0] = f[0] * fma(x2, fma(k.g, x2, -k.lam), k.m2);   // m2 x - lam x^3 + g x^5
     V = x2 * fma(x2, fma(k.sg, x2, -k.qlam), k.hm2);      // m2/2 x^2 - lam/4 x^4 + g/6 x^6
   }
-  // (x0 + d)^n - x0^n = d * sum_{j=0}^{n-1} C(n, j+1) x0^{n-1-j} d^j  (Horner in d)
-  struct SplitK { float m2, lam, g, hm2, qlam, sg, c2, c3[2], c4[3], c5[4], c6[5]; };
+  // V' and V are polynomials, so their differences are exact Taylor polynomials
+  // in d around x0 whose coefficients (computed in float64) are
+  //   dV'(d) = d (c1 + d (c2 + d (c3 + d (c4 + d c5))))
+  //     c1 = m2 - 3 lam x0^2 + 5 g x0^4,  c2 = -3 lam x0 + 10 g x0^3,
+  //     c3 = -lam + 10 g x0^2,  c4 = 5 g x0,  c5 = g
+  //   dV(d)  = d (e1 + d (e2 + d (e3 + d (e4 + d (e5 + d e6)))))
+  //     e1 = m2 x0 - lam x0^3 + g x0^5,  e2 = m2/2 - 3 lam/2 x0^2 + 5 g/2 x0^4,
+  //     e3 = -lam x0 + 10 g/3 x0^3,  e4 = -lam/4 + 5 g/2 x0^2,  e5 = g x0,  e6 = g/6
+  struct SplitK { float c[5], e[6]; };
   __device__ static SplitK split_prep(const double* p, const double* b) {
+    const double m2 = p[0], lam = p[1], g = p[2];
     const double x = b[0], x2 = x * x, x3 = x2 * x, x4 = x3 * x, x5 = x4 * x;
     SplitK k;
-    k.m2 = (float)p[0]; k.lam = (float)p[1]; k.g = (float)p[2];
-    k.hm2 = (float)(0.5 * p[0]); k.qlam = (float)(0.25 * p[1]); k.sg = (float)(p[2] / 6.0);
-    k.c2 = (float)(2 * x);
-    k.c3[0] = (float)(3 * x2); k.c3[1] = (float)(3 * x);
-    k.c4[0] = (float)(4 * x3); k.c4[1] = (float)(6 * x2); k.c4[2] = (float)(4 * x);
-    k.c5[0] = (float)(5 * x4); k.c5[1] = (float)(10 * x3); k.c5[2] = (float)(10 * x2);
-    k.c5[3] = (float)(5 * x);
-    k.c6[0] = (float)(6 * x5); k.c6[1] = (float)(15 * x4); k.c6[2] = (float)(20 * x3);
-    k.c6[3] = (float)(15 * x2); k.c6[4] = (float)(6 * x);
+    k.c[0] = (float)(m2 - 3.0 * lam * x2 + 5.0 * g * x4);
+    k.c[1] = (float)(-3.0 * lam * x + 10.0 * g * x3);
+    k.c[2] = (float)(-lam + 10.0 * g * x2);
+    k.c[3] = (float)(5.0 * g * x);
+    k.c[4] = (float)g;
+    k.e[0] = (float)(m2 * x - lam * x3 + g * x5);
+    k.e[1] = (float)(0.5 * m2 - 1.5 * lam * x2 + 2.5 * g * x4);
+    k.e[2] = (float)(-lam * x + (10.0 / 3.0) * g * x3);
+    k.e[3] = (float)(-0.25 * lam + 2.5 * g * x2);
+    k.e[4] = (float)(g * x);
+    k.e[5] = (float)(g / 6.0);
     return k;
   }
   __device__ static void diff(const SplitK& k, const float* dd, float* dVd, float& dVv) {
     const float d = dd[0];
-    const float D2 = d * (k.c2 + d);
-    const float D3 = d * fmaf(d, k.c3[1] + d, k.c3[0]);
-    const float D4 = d * fmaf(d, fmaf(d, k.c4[2] + d, k.c4[1]), k.c4[0]);
-    const float D5 = d * fmaf(d, fmaf(d, fmaf(d, k.c5[3] + d, k.c5[2]), k.c5[1]), k.c5[0]);
-    const float D6 =
-        d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, k.c6[4] + d, k.c6[3]), k.c6[2]), k.c6[1]), k.c6[0]);
-    dVd[0] = fmaf(k.m2, d, fmaf(k.g, D5, -k.lam * D3));
-    dVv = fmaf(k.hm2, D2, fmaf(k.sg, D6, -k.qlam * D4));
+    dVd[0] = d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, k.c[4], k.c[3]), k.c[2]), k.c[1]), k.c[0]);
+    dVv = d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, fmaf(d, k.e[5], k.e[4]), k.e[3]), k.e[2]), k.e[1]),
+                   k.e[0]);
   }
 };
 

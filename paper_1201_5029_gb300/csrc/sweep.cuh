@@ -265,7 +265,8 @@ struct Ctx {
         ps[SL::DPI2 + f] = madd(pin[f], pin[f], ps[SL::DPI2 + f]);
         ps[SL::PHID + f] = madd(phj[f], D[f], ps[SL::PHID + f]);
         ps[SL::DPHI + f] += phj[f];
-        ps[SL::DPHI2 + f] = madd(phj[f], phj[f], ps[SL::DPHI2 + f]);
+        if (mode != MODE_SWEEP)   // the variance is only reported at synchronised states
+          ps[SL::DPHI2 + f] = madd(phj[f], phj[f], ps[SL::DPHI2 + f]);
       }
       ps[SL::V] += dVv;
     }
@@ -812,19 +813,46 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tma(const LaunchTable tab) 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// 4-byte asynchronous global -> shared copy.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+// Arrive on `bar` once this thread's earlier cp.async copies have landed; the
+// arrival counts toward the barrier's expected count (.noinc).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// halo-column rows a lane needs: its own row (7-point) or three rows (iso-27)
+#define CR_OF(corners) ((corners) ? 3 : 1)
+
+// Depth of the split sweep's TMA ring: kPipeSlots slots, kPipeLead planes in
+// flight ahead of the plane being computed (the slot being recycled was
+// released kPipeSlots - kPipeLead planes earlier).
+constexpr int kPipeSlots = 6;
+constexpr int kPipeLead = 4;
+
+template <int NF, int VX>
+constexpr size_t pipe_smem_bytes() {
+  return sizeof(float) * (size_t)kPipeSlots * 2 * NF * (kMaxTY + 2) * 32 * VX;
+}
 
 // ---------------------------------------------------------------------------
-// Split-FP32 sweep (n % 32 == 0), barrier-free warp pipeline.
+// Split-FP32 sweep (n % 32 == 0): barrier-free warp pipeline.
 //
-// The float32 form is bound by HBM, so its sweep avoids block-wide barriers in
-// the z loop.  Thread 0 keeps LEAD planes of TMA copies in flight in a
-// NSLOT-deep ring ("full" mbarriers, transaction counted).  Each warp owns one
-// tile row: it waits for the plane, drifts the three rows it needs (its own and
-// the two neighbours, re-centred and drifted on the fly, never written back),
-// releases the slot (one arrival per warp on the slot's "empty" mbarrier, on
-// which thread 0 waits before recycling it), then does the stencil, kick and
-// sums from registers.  Lanes 0 and 31 fetch the halo columns themselves, one
-// plane ahead.  Warps drift apart by up to NSLOT - LEAD planes.
+// The float32 form is bound by HBM, so its sweep keeps every SM streaming:
+//   - block b owns tile b mod T and z-chunk b / T, so blocks that run together
+//     are neighbouring tiles at the same z and the halo rows they read hit L2
+//     (a plane-balanced persistent grid with unaligned z-ranges was measured
+//     to re-read ~60% more from DRAM);
+//   - thread 0 keeps LEAD planes of TMA copies in flight in an NSLOT-deep ring
+//     ("full" mbarriers, transaction-counted); each warp owns one tile row,
+//     drifts the three rows it needs in registers (never written back),
+//     releases the slot (one arrival per warp on the slot's "empty" mbarrier,
+//     which thread 0 waits on before recycling it), and does the stencil, kick
+//     and sums from registers; no block barrier in the z loop;
+//   - lanes 0 and 31 fetch the two halo columns themselves, two planes ahead.
 // ---------------------------------------------------------------------------
 template <int MODEL, int STENCIL, int VX>
 __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTable tab) {
@@ -837,13 +865,17 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
   constexpr int TY = kMaxTY;
   constexpr int TX = 32 * VX;
   constexpr int ROWS = TY + 2;
-  constexpr int NSLOT = 4, LEAD = 2;
-  constexpr int CR = CORNERS ? 3 : 1;           // halo-column rows a lane needs
+  constexpr int NWARP = kThreads / 32;
+  constexpr int NSLOT = kPipeSlots, LEAD = kPipeLead;
+  constexpr int NCOL = 2 * NF * 2 * ROWS;       // halo-column values per plane
   constexpr uint32_t kPlaneBytes = 2u * NF * ROWS * TX * sizeof(float);
 
-  __shared__ __align__(128) float stage[NSLOT][2][NF][ROWS][TX];
+  // the ring lives in dynamic shared memory (pipe_smem_bytes(), above the 48 KB static limit)
+  extern __shared__ __align__(128) unsigned char pipe_smem[];
+  auto& stage = *reinterpret_cast<float (*)[NSLOT][2][NF][ROWS][TX]>(pipe_smem);
+  __shared__ float colb[NSLOT][2][NF][2][ROWS];   // [slot][phi/pi][f][left/right][row]
   __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT];
-  __shared__ double sred[(kThreads / 32) * NQ];
+  __shared__ double sred[NWARP * NQ];
   __shared__ double sout[NQ];
   __shared__ int s_last, s_fault;
   __shared__ C s_ctx;
@@ -856,16 +888,9 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
   if (mode == MODE_IDLE) return;
 
   const int n = d.n;
-  const int tile = cta % (d.tiles_x * d.tiles_y);
-  const int zch = cta / (d.tiles_x * d.tiles_y);
-  const int x0 = (tile % d.tiles_x) * TX;
-  const int y0 = (tile / d.tiles_x) * TY;
-  const int z0 = zch * d.zc;
-  const int zend = min(n, z0 + d.zc);
-  const int Q = zend - z0 + 2;                 // planes z0-1 .. zend
+  const int tiles_x = d.tiles_x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, ly = tid >> 5;
-  const int gx = x0 + lane * VX, gy = y0 + ly;
   const size_t S = (size_t)d.S;
   const size_t nn = (size_t)n * n;
   const int ib = bgr.cur;
@@ -877,24 +902,37 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
   const CUtensorMap* tphi_row = &d.tmap[ib & 1][1];
   const CUtensorMap* tpi_main = &d.tmap[2 + ((ib >> 1) & 1)][0];
   const CUtensorMap* tpi_row = &d.tmap[2 + ((ib >> 1) & 1)][1];
+
+  // this block's tile and z-chunk: consecutive blocks are neighbouring tiles at
+  // the same z, so the halo rows one block reads were just read by another (L2)
+  const int tile = cta % (tiles_x * d.tiles_y);
+  const int zch = cta / (tiles_x * d.tiles_y);
+  const int x0 = (tile % tiles_x) * TX;
+  const int y0 = (tile / tiles_x) * TY;
+  const int z0 = zch * d.zc;
+  const int Q = min(n, z0 + d.zc) - z0 + 2;   // planes z0 - 1 .. z1
   const int yl = wrapi(y0 - 1, n), yh = wrapi(y0 + TY, n);
+  const int xl = wrapi(x0 - 1, n), xr = wrapi(x0 + TX, n);
 
   if (tid == 0) {
     s_ctx.init(bgr, d, mode);
     for (int s = 0; s < NSLOT; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kThreads / 32);
+      mbar_init(&full[s], 1 + 32);        // the TMA transaction + one warp of cp.async
+      mbar_init(&empty[s], NWARP);
     }
     fence_mbar_init();
+    s_fault = 0;
+  }
+  if (lane == 0) {
     tensormap_acquire(tphi_main);
     tensormap_acquire(tphi_row);
     tensormap_acquire(tpi_main);
     tensormap_acquire(tpi_row);
-    s_fault = 0;
   }
   __syncthreads();
   const C cx = s_ctx;
-  // re-centring folded into the drift: phi* = phi + c pi - (mu_phi + c mu_pi)
+  // re-centring of the output: phi* = phi + c pi - (mu_phi + c mu_pi); the
+  // stencil works on phi + c pi (D of a constant is zero)
   float Mf[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) Mf[f] = madd(cx.cdrift, cx.mu_pi[f], cx.mu_phi[f]);
@@ -903,54 +941,44 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
   const float c2 = CORNERS ? (float)(3.0 / 30.0) : 0.0f;
   const float c3 = CORNERS ? (float)(1.0 / 30.0) : 0.0f;
 
-  int issued = 0;   // planes whose copies thread 0 has issued
-  auto issue = [&](int q) {
+  // Producer of plane q, run by every lane of warp q mod NWARP: lane 0 issues
+  // the TMA copies of the tile and its two halo rows, all lanes copy the two
+  // halo columns with cp.async; both complete on full[q mod NSLOT].
+  auto produce = [&](int q) {
     const int s = q % NSLOT;
     const int zw = wrapi(z0 - 1 + q, n);
-    mbar_expect_tx(&full[s], kPlaneBytes);
+    const size_t zoff = (size_t)zw * nn;
+    if (lane == 0) {
+      mbar_expect_tx(&full[s], kPlaneBytes);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int zz = f * n + zw;
-      tma_load_3d(&stage[s][0][f][1][0], tphi_main, x0, y0, zz, &full[s]);
-      tma_load_3d(&stage[s][0][f][0][0], tphi_row, x0, yl, zz, &full[s]);
-      tma_load_3d(&stage[s][0][f][ROWS - 1][0], tphi_row, x0, yh, zz, &full[s]);
-      tma_load_3d(&stage[s][1][f][1][0], tpi_main, x0, y0, zz, &full[s]);
-      tma_load_3d(&stage[s][1][f][0][0], tpi_row, x0, yl, zz, &full[s]);
-      tma_load_3d(&stage[s][1][f][ROWS - 1][0], tpi_row, x0, yh, zz, &full[s]);
+      for (int f = 0; f < NF; ++f) {
+        const int zz = f * n + zw;
+        tma_load_3d(&stage[s][0][f][1][0], tphi_main, x0, y0, zz, &full[s]);
+        tma_load_3d(&stage[s][0][f][0][0], tphi_row, x0, yl, zz, &full[s]);
+        tma_load_3d(&stage[s][0][f][ROWS - 1][0], tphi_row, x0, yh, zz, &full[s]);
+        tma_load_3d(&stage[s][1][f][1][0], tpi_main, x0, y0, zz, &full[s]);
+        tma_load_3d(&stage[s][1][f][0][0], tpi_row, x0, yl, zz, &full[s]);
+        tma_load_3d(&stage[s][1][f][ROWS - 1][0], tpi_row, x0, yh, zz, &full[s]);
+      }
     }
-  };
-  if (tid == 0) {
-    for (; issued < LEAD && issued < Q; ++issued) issue(issued);
-  }
-
-  // halo columns: lane 0 the left one (x0 - 1), lane 31 the right one (x0 + TX)
-  const bool edge = (lane == 0) || (lane == 31);
-  const int ex = lane == 0 ? wrapi(x0 - 1, n) : wrapi(x0 + TX, n);
-  size_t eoff[CR];
-#pragma unroll
-  for (int r = 0; r < CR; ++r) eoff[r] = (size_t)wrapi(gy + r - (CR - 1) / 2, n) * n + ex;
-  float ep[NF][CR], eq[NF][CR];
-#pragma unroll
-  for (int f = 0; f < NF; ++f)
-#pragma unroll
-    for (int r = 0; r < CR; ++r) { ep[f][r] = 0.f; eq[f][r] = 0.f; }
-  auto load_edge = [&](int p) {
-    if (edge) {
-      const size_t zoff = (size_t)wrapi(p, n) * nn;
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int r = 0; r < CR; ++r) {
-          ep[f][r] = phi_in[f * S + zoff + eoff[r]];
-          eq[f][r] = pi_in[f * S + zoff + eoff[r]];
-        }
+    for (int i = lane; i < NCOL; i += 32) {
+      const int row = i % ROWS;
+      const int side = (i / ROWS) & 1;
+      const int f = (i / (2 * ROWS)) % NF;
+      const int arr = i / (2 * ROWS * NF);
+      const size_t off = zoff + (size_t)wrapi(y0 - 1 + row, n) * n + (side ? xr : xl);
+      cp_async4(&colb[s][arr][f][side][row], (arr ? pi_in : phi_in) + f * S + off);
     }
+    cp_async_arrive_noinc(&full[s]);
   };
-  load_edge(z0 - 1);
+  for (int q = ly; q < LEAD && q < Q; q += NWARP) produce(q);
 
   Acc<float> acc[NQ];
 #pragma unroll
   for (int i = 0; i < NQ; ++i) acc[i].zero();
+  // rotating registers: part_m = S_off(z-1) + S_mid(z) of the plane z = p - 1
+  // awaiting output; so_m = S_off(p - 1) (iso27); ph_m / pi_m = drifted field
+  // (not re-centred) and re-centred momentum of plane p - 1
   float part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
 #pragma unroll
   for (int f = 0; f < NF; ++f)
@@ -959,26 +987,24 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
 
   int q = 0;
   for (; q < Q; ++q) {
-    // every exit decision is taken by the whole warp (shuffles and __syncwarp follow)
-    if (__any_sync(0xffffffffu, s_fault != 0)) break;
     const int s = q % NSLOT;
     const int p = z0 - 1 + q;
-    // producer: recycle the slot of plane q + LEAD - NSLOT once every warp released it
-    if (tid == 0 && issued < Q && issued == q + LEAD) {
-      const int r = issued - NSLOT;
-      if (r >= 0 && !mbar_wait(&empty[r % NSLOT], (uint32_t)((r / NSLOT) & 1))) {
-        atomicOr(&s_fault, 1);
-      } else {
-        issue(issued);
-        ++issued;
-      }
+    // the producer role rotates over the warps: plane q + LEAD, once every warp
+    // has released the slot's previous plane (q + LEAD - NSLOT)
+    const int qn = q + LEAD;
+    bool ok = true;
+    if (qn < Q && qn % NWARP == ly) {
+      const int rr = qn - NSLOT;
+      if (rr >= 0) ok = mbar_wait(&empty[rr % NSLOT], (uint32_t)((rr / NSLOT) & 1));
+      if (__all_sync(0xffffffffu, ok)) produce(qn);
     }
-    const bool ready = mbar_wait(&full[s], (uint32_t)((q / NSLOT) & 1));
-    if (!__all_sync(0xffffffffu, ready)) {
+    ok = ok && mbar_wait(&full[s], (uint32_t)((q / NSLOT) & 1));
+    // every exit decision is taken by the whole warp (shuffles and __syncwarp follow)
+    if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicOr(&s_fault, 1);
       break;
     }
-    // the three rows of this warp, drifted in registers
+    // the three rows this warp needs, drifted in registers (not written back)
     float cur_ph[NF][VX], cur_pi[NF][VX], dn[NF][VX], up[NF][VX];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -988,29 +1014,36 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
 #pragma unroll
       for (int j = 0; j < VX; ++j) {
         cur_pi[f][j] = b[j] - cx.mu_pi[f];
-        cur_ph[f][j] = madd(cx.cdrift, b[j], a[j]) - Mf[f];
+        cur_ph[f][j] = madd(cx.cdrift, b[j], a[j]);
       }
       vload<float, VX>(&stage[s][0][f][ly][lane * VX], a);
       vload<float, VX>(&stage[s][1][f][ly][lane * VX], b);
 #pragma unroll
-      for (int j = 0; j < VX; ++j) dn[f][j] = madd(cx.cdrift, b[j], a[j]) - Mf[f];
+      for (int j = 0; j < VX; ++j) dn[f][j] = madd(cx.cdrift, b[j], a[j]);
       vload<float, VX>(&stage[s][0][f][ly + 2][lane * VX], a);
       vload<float, VX>(&stage[s][1][f][ly + 2][lane * VX], b);
 #pragma unroll
-      for (int j = 0; j < VX; ++j) up[f][j] = madd(cx.cdrift, b[j], a[j]) - Mf[f];
+      for (int j = 0; j < VX; ++j) up[f][j] = madd(cx.cdrift, b[j], a[j]);
+    }
+    // halo columns (lane 0: left, lane 31: right), rows ly .. ly + 2 of the slot
+    float el[NF][CR_OF(CORNERS)];
+    {
+      const int side = lane == 31 ? 1 : 0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int rr = 0; rr < CR_OF(CORNERS); ++rr) {
+          const int row = ly + 1 + rr - (CR_OF(CORNERS) - 1) / 2;
+          el[f][rr] = madd(cx.cdrift, colb[s][1][f][side][row], colb[s][0][f][side][row]);
+        }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with the slot
-    float el[NF][CR];
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-      for (int r = 0; r < CR; ++r) el[f][r] = madd(cx.cdrift, eq[f][r], ep[f][r]) - Mf[f];
-    if (q + 1 < Q) load_edge(p + 1);
 
     float so_new[NF][VX], smid_new[NF][VX];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
+      constexpr int CR = CR_OF(CORNERS);
       float left = __shfl_up_sync(0xffffffffu, cur_ph[f][VX - 1], 1);
       float right = __shfl_down_sync(0xffffffffu, cur_ph[f][0], 1);
       if (lane == 0) left = el[f][(CR - 1) / 2];
@@ -1045,17 +1078,18 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
       }
     }
     if (q >= 2) {  // output plane z = p - 1
-      const size_t o = (size_t)(p - 1) * nn + (size_t)gy * n + gx;
+      const size_t o = (size_t)(p - 1) * nn + (size_t)(y0 + ly) * n + x0 + lane * VX;
       float ps[NQ];
 #pragma unroll
       for (int i = 0; i < NQ; ++i) ps[i] = 0.f;
-      float pin[NF][VX];
+      float pin[NF][VX], phs[NF][VX];
 #pragma unroll
       for (int j = 0; j < VX; ++j) {
         float phj[NF], Dj[NF], pmj[NF], pnj[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          phj[f] = ph_m[f][j];
+          phs[f][j] = ph_m[f][j] - Mf[f];   // the re-centred drifted field
+          phj[f] = phs[f][j];
           Dj[f] = part_m[f][j] + so_new[f][j];
           pmj[f] = pi_m[f][j];
         }
@@ -1065,11 +1099,12 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        vstore<float, VX>(phi_out + f * S + o, ph_m[f]);
+        vstore<float, VX>(phi_out + f * S + o, phs[f]);
         if (mode == MODE_SWEEP) vstore<float, VX>(pi_out + f * S + o, pin[f]);
       }
 #pragma unroll
-      for (int i = 0; i < NQ; ++i) acc[i].add(ps[i]);
+      for (int i = 0; i < NQ; ++i)
+        if (mode != MODE_SWEEP || i < SL::DPHI2 || i >= SL::DPHI2 + NF) acc[i].add(ps[i]);
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f)
@@ -1084,10 +1119,11 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
 
   block_partials<PREC, NQ, float>(acc, nullptr, sred, sout);
   if (s_fault) {
-    // a copy or a release never completed: record it, drain issued copies (bounded), stop
+    // a copy or a release never completed: record it, drain what may be in flight (bounded)
     if (tid == 0) {
       atomicOr(d.fault, 1);
-      for (int r = q; r < issued; ++r) mbar_wait(&full[r % NSLOT], (uint32_t)((r / NSLOT) & 1));
+      for (int rr = q; rr < Q && rr < q + LEAD; ++rr)
+        mbar_wait(&full[rr % NSLOT], (uint32_t)((rr / NSLOT) & 1));
     }
     return;
   }
@@ -1255,22 +1291,32 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_plain(const LaunchTable tab
 }
 
 // Launch helper: dispatch (model, stencil, path/vx) at runtime to an instance.
+// grid == 0 only prepares the instance (its shared-memory attribute), so that
+// callers can do it before a stream capture.
 template <int PREC>
 cudaError_t launch_sweep_impl(int model, int stencil, int vx, int tma, const LaunchTable& t,
                               int grid, cudaStream_t s) {
   const dim3 g(grid), b(kThreads);
 #define PYCOOL_PLAIN(M, ST)                                              \
   if (!tma && model == M && stencil == ST) {                             \
+    if (grid == 0) return cudaSuccess;                                   \
     sweep_plain<M, ST, PREC><<<g, b, 0, s>>>(t);                         \
     return cudaGetLastError();                                           \
   }
 #define PYCOOL_TMA(M, ST, V)                                             \
   if constexpr (V * Pot<M>::NF * (PREC == PREC_FP64 ? 8 : 4) <= 16) {    \
     if (tma && model == M && stencil == ST && vx == V) {                 \
-      if constexpr (PREC == PREC_SPLIT)                                  \
-        sweep_split_pipe<M, ST, V><<<g, b, 0, s>>>(t);                   \
-      else                                                               \
+      if constexpr (PREC == PREC_SPLIT) {                                \
+        constexpr size_t smem = pipe_smem_bytes<Pot<M>::NF, V>();        \
+        static const cudaError_t attr = cudaFuncSetAttribute(            \
+            sweep_split_pipe<M, ST, V>,                                  \
+            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        if (attr != cudaSuccess || grid == 0) return attr;               \
+        sweep_split_pipe<M, ST, V><<<g, b, smem, s>>>(t);                \
+      } else {                                                           \
+        if (grid == 0) return cudaSuccess;                               \
         sweep_tma<M, ST, PREC, V><<<g, b, 0, s>>>(t);                    \
+      }                                                                  \
       return cudaGetLastError();                                         \
     }                                                                    \
   }
