@@ -160,6 +160,59 @@ def e2e_form(P, torch, w, precision, steps, phi_pin, pi_pin, out_phi, out_pi, st
     return dt
 
 
+def _serving_configs(P, I, reqs, prec):
+    mix = I.SERVING_MIX
+    out = []
+    for r in reqs:
+        w = I.workload(r["workload"])
+        cfg = P.make_config(r["n"], mix["L"][w["model"]], w["model"], w["params"],
+                            mix["dt"][w["model"]], order=r["order"], precision=prec, mpl=w["mpl"])
+        out.append((cfg, P.make_ic(w["background"], w["momentum"], w["noise"]), r))
+    return out
+
+
+def _serve(P, items, arrivals, slots=64, budget=96 << 30):
+    """Submit each request at its arrival time (None: all at once), wait for all.
+    Returns the server's latency percentiles and the aggregate rate."""
+    srv = P.pycool_server_create(budget, slots)
+    t0 = time.perf_counter()
+    tickets, work = [], 0
+    for i, (cfg, ic, r) in enumerate(items):
+        if arrivals is not None:
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+        tickets.append(P.pycool_server_submit(srv, cfg, ic, r["seed"], r["steps"]))
+        work += r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])
+    bad = sum(P.pycool_server_wait(srv, t, 600.0)[0] != P.OK for t in tickets)
+    wall = time.perf_counter() - t0
+    s = P.pycool_server_stats(srv)
+    P.pycool_server_destroy(srv)
+    return dict(p50_s=s["p50_s"], p99_s=s["p99_s"], site_updates_per_s=work / wall,
+                completed=s["completed"], failed=int(bad), wall_s=wall)
+
+
+def serving_leg(P, I, count, steps_scale, load):
+    """Serving mix (sizes 32..384^3, three models, orders 2..8): a closed-loop
+    calibration of the FP64 form's capacity, then the same Poisson arrival
+    stream at `load` x that capacity for each form."""
+    reqs = I.serving_requests(count=count, steps_scale=steps_scale)
+    mean_work = sum(r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])
+                    for r in reqs) / len(reqs)
+    items64 = _serving_configs(P, I, reqs, "fp64")
+    calib = _serve(P, items64, None)
+    capacity = calib["site_updates_per_s"] / mean_work          # requests/s
+    rate = load * capacity
+    arr = I.poisson_arrivals(rate, len(reqs), I.SERVING_MIX["arrival_seed"])
+    out = {"requests": len(reqs), "steps_scale": steps_scale, "offered_load": load,
+           "arrival_rate_per_s": rate, "capacity_fp64_req_per_s": capacity,
+           "mean_site_stages_per_request": mean_work,
+           "latency": "submit (Poisson arrival) -> observables read back on the host"}
+    for prec, items in (("fp64", items64), ("split_fp32", _serving_configs(P, I, reqs, "split_fp32"))):
+        out[prec] = _serve(P, items, arr)
+    return out
+
+
 def cpu_baseline(w, phi, pi, budget_s=15.0):
     """The oracle as it stands, on the host cores: whole time steps of the workload."""
     from oracle import pycool_oracle as O
@@ -240,6 +293,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=60)
+    ap.add_argument("--serving-steps-scale", type=float, default=0.02)
+    ap.add_argument("--serving-load", type=float, default=0.7)
     ap.add_argument("--forms", default="fp64,split_fp32",
                     help="comma list of forms to time (profiling a single kernel)")
     args = ap.parse_args()
@@ -343,6 +400,11 @@ def main():
                "form": "fp64", "steps": k,
                "note": "set_initial(host) + evolve(1) + get_fields(host) per step"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_leg(P, I, args.serving_requests, args.serving_steps_scale,
+                              args.serving_load)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -366,6 +428,7 @@ def main():
             },
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serving,
             "gpu_launches": int(l64 + l32),
             "clocks": clocks,
         }

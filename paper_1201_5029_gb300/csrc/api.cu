@@ -82,10 +82,17 @@ Layout layout_for(const pycool_config& c) {
   L.off_desc = align256(sizeof(Background));
   L.off_fields = L.off_desc + align256(sizeof(SimDesc));
   L.state_bytes = L.off_fields + 4 * L.field_bytes;
-  L.off_ticket = 0;
-  L.off_partials = 256;
-  L.ws_bytes = L.off_partials + align256((size_t)L.geo.ncta * kNQ * sizeof(double));
+  workspace_layout(L.geo.ncta, L);
   return L;
+}
+
+void workspace_layout(int ncta, Layout& L) {
+  const size_t ngroups = ((size_t)ncta + kGroup - 1) / kGroup;
+  L.off_ticket = 0;
+  L.off_gticket = 256;
+  L.off_partials = L.off_gticket + align256(ngroups * sizeof(unsigned int));
+  L.off_gpartials = L.off_partials + align256((size_t)ncta * kNQ * sizeof(double));
+  L.ws_bytes = L.off_gpartials + align256(ngroups * kNQ * sizeof(double));
 }
 
 pycool_status validate(const pycool_config* c) {
@@ -139,6 +146,8 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.rho_r0 = c.rho_rad0;
   d.rho_m0 = c.rho_mat0;
   for (int i = 0; i < 8; ++i) d.params[i] = c.params[i];
+  d.invS = 1.0 / (double)d.S;
+  if (c.model == PYCOOL_MODEL_QBALL) d.derived[0] = std::log(c.params[2] * c.params[2]);
   char* f = state + L.off_fields;
   d.phi[0] = f;
   d.phi[1] = f + L.field_bytes;
@@ -148,6 +157,9 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.ticket = (unsigned int*)(ws + L.off_ticket);
   d.fault = (int32_t*)(ws + L.off_ticket + 128);
   d.partials = (double*)(ws + L.off_partials);
+  d.gticket = (unsigned int*)(ws + L.off_gticket);
+  d.gpartials = (double*)(ws + L.off_gpartials);
+  d.ngroups = (L.geo.ncta + kGroup - 1) / kGroup;
 }
 
 // TMA descriptors for the four field buffers (see SimDesc::tmap).  The driver
@@ -487,7 +499,7 @@ PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, 
     CK(cudaMemcpy(sim->hdesc.pi[0], dpi.data(), count * sizeof(float), cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
-  CK(cudaMemsetAsync(sim->hdesc.ticket, 0, sizeof(unsigned int), sim->stream));
+  CK(cudaMemsetAsync(sim->ws, 0, sim->L.off_partials, sim->stream));
   pycool_status st = launch_one(sim);
   if (st != PYCOOL_OK) return st;
   CK(cudaEventRecord(sim->done, sim->stream));
@@ -657,7 +669,7 @@ PYCOOL_API pycool_status pycool_checkpoint_load(pycool_sim* sim, const void* buf
   CK(cudaMemcpy(sim->hdesc.phi[b.cur & 1], p + sizeof(b), fb, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(sim->hdesc.pi[(b.cur >> 1) & 1], p + sizeof(b) + fb, fb, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice));
-  CK(cudaMemset(sim->hdesc.ticket, 0, sizeof(unsigned int)));
+  CK(cudaMemset(sim->ws, 0, sim->L.off_partials));
   CK(cudaEventRecord(sim->done, sim->stream));
   sim->initialised = true;
   return PYCOOL_OK;

@@ -23,6 +23,7 @@ constexpr int kMaxTXT = 32;        // threads per tile row (x, contiguous)
 constexpr int kMaxTY = 8;          // tile height (y)
 constexpr int kNQ = 12;            // reduction slots per block
 constexpr int kMaxMembers = 64;    // simulations per batched launch
+constexpr int kGroup = 32;         // blocks per first-level fold group
 
 enum Mode : int32_t { MODE_IDLE = 0, MODE_SWEEP = 1, MODE_FLUSH = 2 };
 enum Prec : int32_t { PREC_FP64 = 0, PREC_SPLIT = 1 };
@@ -66,12 +67,17 @@ struct alignas(64) SimDesc {
   int32_t tx, ty, zc, tiles_x, tiles_y, zchunks, ncta;
   int64_t S;                  // n^3
   double dt, dx2inv, VL, inv6VLm2, mpl2, rho_r0, rho_m0;
+  double invS;                // 1 / n^3
   double params[8];
+  double derived[4];          // host-computed model constants (Q-ball: ln M^2)
   double w[kMaxStages];
   void* phi[2];
   void* pi[2];
-  double* partials;           // ncta * kNQ
-  unsigned int* ticket;
+  double* partials;           // ncta * kNQ: one row per block
+  double* gpartials;          // ngroups * kNQ: one row per group of kGroup blocks
+  unsigned int* ticket;       // groups folded so far
+  unsigned int* gticket;      // per group: blocks finished so far
+  int32_t ngroups;
   int32_t* fault;             // set when a device-side wait gave up
   Background* bg;
 };

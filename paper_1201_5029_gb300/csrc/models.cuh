@@ -7,7 +7,11 @@
 //   QBALL    V = m2 u (1 + K ln(u/M^2)), u = |Phi|^2 = (phi1^2 + phi2^2)/2
 //                                                    (Sec. 3.3)  p = {m2, K, M}
 //
-// Pot<M>::eval gives V and dV/dphi_i in float64.  Pot<M>::SplitK / diff give,
+// Pot<M>::eval gives V and dV/dphi_i in float64.  Pot<M>::split_prep gives,
+// at the float64 background phi0, V(phi0), V'(phi0) and the float32 constants
+// of the difference forms (one call per block: it runs in a single thread, so
+// each model computes its transcendental functions there only once).
+// Pot<M>::SplitK / diff give,
 // in float32, the differences dV'_i = V'_i(phi0 + d) - V'_i(phi0) and
 // dV = V(phi0 + d) - V(phi0) around a float64 background phi0, written so that
 // every term carries at least one factor of d (no cancellation for small d):
@@ -27,13 +31,15 @@ template <int M> struct Pot;
 template <> struct Pot<M_FREE> {
   static constexpr int NF = 1;
   struct K { double m2, hm2; };
-  __device__ static K prep(const double* p) { return K{p[0], 0.5 * p[0]}; }
+  __device__ static K prep(const double* p, const double*) { return K{p[0], 0.5 * p[0]}; }
   __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
     dV[0] = k.m2 * f[0];
     V = k.hm2 * f[0] * f[0];
   }
   struct SplitK { float m2, hm2, p0, two_p0; };
-  __device__ static SplitK split_prep(const double* p, const double* phi0) {
+  __device__ static SplitK split_prep(const K& pk, const double* p, const double*,
+                                      const double* phi0, double* dV0, double& V0) {
+    eval(pk, phi0, dV0, V0);
     return SplitK{(float)p[0], (float)(0.5 * p[0]), (float)phi0[0], (float)(2.0 * phi0[0])};
   }
   __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {
@@ -46,7 +52,7 @@ template <> struct Pot<M_FREE> {
 template <> struct Pot<M_CHAOTIC2> {
   static constexpr int NF = 2;
   struct K { double m2, g2; };
-  __device__ static K prep(const double* p) { return K{p[0], p[1]}; }
+  __device__ static K prep(const double* p, const double*) { return K{p[0], p[1]}; }
   __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
     const double ph2 = f[0] * f[0];
     const double t = fma(k.g2, f[1] * f[1], k.m2);       // m2 + g2 chi^2
@@ -55,7 +61,9 @@ template <> struct Pot<M_CHAOTIC2> {
     V = ph2 * (0.5 * t);                                // phi^2 (m2 + g2 chi^2) / 2
   }
   struct SplitK { float m2, g2, hm2, hg2, p0, c0, two_p0, two_c0, p0sq, c0sq; };
-  __device__ static SplitK split_prep(const double* p, const double* b) {
+  __device__ static SplitK split_prep(const K& pk, const double* p, const double*,
+                                      const double* b, double* dV0, double& V0) {
+    eval(pk, b, dV0, V0);
     SplitK k;
     k.m2 = (float)p[0]; k.g2 = (float)p[1];
     k.hm2 = (float)(0.5 * p[0]); k.hg2 = (float)(0.5 * p[1]);
@@ -84,8 +92,8 @@ template <> struct Pot<M_CHAOTIC2> {
 template <> struct Pot<M_OSCILLON> {
   static constexpr int NF = 1;
   struct K { double m2, lam, g, hm2, qlam, sg; };
-  __device__ static K prep(const double* p) {
-    return K{p[0], p[1], p[2], 0.5 * p[0], 0.25 * p[1], p[2] / 6.0};
+  __device__ static K prep(const double* p, const double*) {
+    return K{p[0], p[1], p[2], 0.5 * p[0], 0.25 * p[1], p[2] * (1.0 / 6.0)};
   }
   __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
     const double x2 = f[0] * f[0];
@@ -101,7 +109,9 @@ template <> struct Pot<M_OSCILLON> {
   //     e1 = m2 x0 - lam x0^3 + g x0^5,  e2 = m2/2 - 3 lam/2 x0^2 + 5 g/2 x0^4,
   //     e3 = -lam x0 + 10 g/3 x0^3,  e4 = -lam/4 + 5 g/2 x0^2,  e5 = g x0,  e6 = g/6
   struct SplitK { float c[5], e[6]; };
-  __device__ static SplitK split_prep(const double* p, const double* b) {
+  __device__ static SplitK split_prep(const K& pk, const double* p, const double*,
+                                      const double* b, double* dV0, double& V0) {
+    eval(pk, b, dV0, V0);
     const double m2 = p[0], lam = p[1], g = p[2];
     const double x = b[0], x2 = x * x, x3 = x2 * x, x4 = x3 * x, x5 = x4 * x;
     SplitK k;
@@ -130,8 +140,9 @@ template <> struct Pot<M_OSCILLON> {
 template <> struct Pot<M_QBALL> {
   static constexpr int NF = 2;
   struct K { double m2, K1, mK, lnM2; };
-  __device__ static K prep(const double* p) {
-    return K{p[0], 1.0 + p[1], p[0] * p[1], log(p[2] * p[2])};
+  // dv[0] = ln(M^2), computed once on the host
+  __device__ static K prep(const double* p, const double* dv) {
+    return K{p[0], 1.0 + p[1], p[0] * p[1], dv[0]};
   }
   // u = (f1^2 + f2^2)/2 ; V' = m2 (1 + K + K ln(u/M^2)) f_i ; V = m2 u (1 + K ln(u/M^2))
   __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
@@ -151,18 +162,30 @@ template <> struct Pot<M_QBALL> {
   //   dV'_i = m2 [ A d_i + K l (p_i + d_i) ],  A = 1 + K + K L0
   //   dV    = m2 [ B du + K l (u0 + du) ],      B = 1 + K L0,  L0 = ln(u0/M^2)
   struct SplitK { float m2, K, A, B, p1, p2, u0, inv_u0; int direct; float lnM2; };
-  __device__ static SplitK split_prep(const double* p, const double* b) {
+  // one logarithm for V(phi0), V'(phi0) and the constants (dv[0] = ln M^2)
+  __device__ static SplitK split_prep(const K& pk, const double* p, const double* dv,
+                                      const double* b, double* dV0, double& V0) {
     SplitK k;
-    const double u0 = 0.5 * (b[0] * b[0] + b[1] * b[1]);
+    const double u0 = 0.5 * fma(b[0], b[0], b[1] * b[1]);
     k.m2 = (float)p[0]; k.K = (float)p[1];
     k.p1 = (float)b[0]; k.p2 = (float)b[1];
-    k.lnM2 = (float)log(p[2] * p[2]);
+    k.lnM2 = (float)dv[0];
     k.direct = !(u0 > 1e-30);
-    const double L0 = k.direct ? 0.0 : log(u0) - log(p[2] * p[2]);
+    const double L = u0 > 0.0 ? log(u0) - dv[0] : 0.0;   // ln(u0 / M^2)
+    const double L0 = k.direct ? 0.0 : L;
     k.A = (float)(1.0 + p[1] + p[1] * L0);
     k.B = (float)(1.0 + p[1] * L0);
     k.u0 = (float)u0;
-    k.inv_u0 = k.direct ? 0.f : (float)(1.0 / u0);
+    k.inv_u0 = k.direct ? 0.f : (float)__drcp_rn(u0);
+    if (u0 > 0.0) {  // as eval(), with the logarithm above
+      const double kl = pk.mK * L;
+      const double fac = fma(pk.m2, pk.K1, kl);
+      dV0[0] = fac * b[0];
+      dV0[1] = fac * b[1];
+      V0 = u0 * (pk.m2 + kl);
+    } else {
+      dV0[0] = 0.0; dV0[1] = 0.0; V0 = 0.0;
+    }
     return k;
   }
   __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {

@@ -24,13 +24,14 @@ using namespace pycool;
 namespace {
 
 // The shared scratch.  Every GPU that loads this library holds it until the
-// process exits.  Layout: [Background][SimDesc][ticket, fault][partials].
+// process exits.  Layout: [Background][SimDesc][workspace: tickets, fault word,
+// partial sums (the simulation workspace layout)].
 constexpr size_t kOffBg = 0;
 constexpr size_t kOffDesc = 1024;
-constexpr size_t kOffTicket = 4096;
-constexpr size_t kOffPartials = 4352;
+constexpr size_t kOffWs = 4096;
+constexpr size_t kWsAvail = PYCOOL_NOALLOC_SCRATCH_BYTES - kOffWs;
 static_assert(sizeof(Background) <= kOffDesc - kOffBg, "background record does not fit");
-static_assert(sizeof(SimDesc) <= kOffTicket - kOffDesc, "descriptor does not fit");
+static_assert(sizeof(SimDesc) <= kOffWs - kOffDesc, "descriptor does not fit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PYCOOL_NOALLOC_SCRATCH_BYTES];
 
@@ -61,7 +62,15 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 }  // namespace
 
 PYCOOL_API size_t pycool_noalloc_max_blocks(void) {
-  return (PYCOOL_NOALLOC_SCRATCH_BYTES - kOffPartials) / (kNQ * sizeof(double));
+  // the workspace grows with the block count: largest count that fits
+  int lo = 0, hi = (int)(kWsAvail / (kNQ * sizeof(double)));
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    Layout L;
+    workspace_layout(mid, L);
+    if (L.ws_bytes <= kWsAvail) lo = mid; else hi = mid - 1;
+  }
+  return (size_t)lo;
 }
 
 PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const double* phi_in,
@@ -77,7 +86,7 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
     return PYCOOL_E_INVALID;
   if (!(state->a > 0.0) || !std::isfinite(state->a)) return PYCOOL_E_INVALID;
   const Layout L = layout_for(*cfg);
-  if ((size_t)L.geo.ncta > pycool_noalloc_max_blocks()) return PYCOOL_E_INVALID;  // too large
+  if (L.ws_bytes > kWsAvail) return PYCOOL_E_INVALID;  // too large for the scratch
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   char* base = nullptr;
   cudaError_t e = scratch_base(&base);
@@ -85,15 +94,11 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
 
   // descriptor: the caller's arrays are buffer 0 (read) and buffer 1 (written)
   SimDesc d;
-  fill_desc(d, *cfg, L, base + kOffBg, base + kOffTicket);
+  fill_desc(d, *cfg, L, base + kOffBg, base + kOffWs);
   d.phi[0] = const_cast<double*>(phi_in);
   d.phi[1] = phi_out;
   d.pi[0] = const_cast<double*>(pi_in);
   d.pi[1] = flush ? const_cast<double*>(pi_in) : pi_out;  // a flush leaves pi unchanged
-  d.bg = (Background*)(base + kOffBg);
-  d.ticket = (unsigned int*)(base + kOffTicket);
-  d.fault = (int32_t*)(base + kOffTicket + 128);
-  d.partials = (double*)(base + kOffPartials);
   if (encode_tensor_maps(d) != cudaSuccess) return PYCOOL_E_CUDA;
 
   Background b;
@@ -119,12 +124,12 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
     if (cudaStreamSynchronize(stream) != cudaSuccess) return PYCOOL_E_CUDA;
   }
 
-  // the shared scratch keeps the last call's contents: ticket and fault must start at 0
+  // the shared scratch keeps the last call's contents: tickets and fault must start at 0
   if (cudaMemcpyAsync(base + kOffDesc, &d, sizeof(d), cudaMemcpyHostToDevice, stream) !=
           cudaSuccess ||
       cudaMemcpyAsync(base + kOffBg, &b, sizeof(b), cudaMemcpyHostToDevice, stream) !=
           cudaSuccess ||
-      cudaMemsetAsync(base + kOffTicket, 0, kOffPartials - kOffTicket, stream) != cudaSuccess)
+      cudaMemsetAsync(base + kOffWs, 0, L.off_partials, stream) != cudaSuccess)
     return PYCOOL_E_CUDA;
   LaunchTable t;
   std::memset(&t, 0, sizeof(t));
@@ -137,7 +142,7 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
   int32_t fault = 0;
   if (cudaMemcpyAsync(&r, base + kOffBg, sizeof(r), cudaMemcpyDeviceToHost, stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(&fault, base + kOffTicket + 128, sizeof(fault), cudaMemcpyDeviceToHost,
+      cudaMemcpyAsync(&fault, base + kOffWs + 128, sizeof(fault), cudaMemcpyDeviceToHost,
                       stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess)
     return PYCOOL_E_CUDA;

@@ -10,13 +10,18 @@ namespace pycool {
 
 // Device memory layout of one simulation.
 //   state     : [Background][SimDesc][phi buf 0][phi buf 1][pi buf 0][pi buf 1]
-//   workspace : [ticket (256 B)][partials: ncta * kNQ doubles]
+//   workspace : [ticket, fault word (256 B)][group tickets][block partials: ncta * kNQ
+//               doubles][group partials: ngroups * kNQ doubles]; the counters
+//               [0, off_partials) must be zero before a launch.
 struct Layout {
   Geometry geo;
   size_t field_bytes;
   size_t off_bg, off_desc, off_fields, state_bytes;
-  size_t off_ticket, off_partials, ws_bytes;
+  size_t off_ticket, off_gticket, off_partials, off_gpartials, ws_bytes;
 };
+
+// Workspace layout of a launch of `ncta` blocks (fills the off_* / ws_bytes fields).
+void workspace_layout(int ncta, Layout& L);
 
 int stage_table(int order, double* w);
 int model_nfields(int model);

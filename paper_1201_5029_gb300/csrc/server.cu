@@ -280,7 +280,7 @@ pycool_status admit(pycool_server* s, const Request& r, int slot) {
   cudaStream_t st = s->setup;
   SCK(cudaMemcpyAsync(m->state + m->L.off_desc, &m->hdesc, sizeof(SimDesc), cudaMemcpyHostToDevice, st));
   SCK(cudaMemcpyAsync(m->state + m->L.off_bg, &b, sizeof(b), cudaMemcpyHostToDevice, st));
-  SCK(cudaMemsetAsync(m->ws, 0, 256, st));
+  SCK(cudaMemsetAsync(m->ws, 0, m->L.off_partials, st));
   ic_white_kernel<<<2048, 256, 0, st>>>(d.phi[0], d.pi[0], (long long)d.S, d.nf, split ? 1 : 0,
                                         r.ic.background[0], r.ic.background[1], r.ic.momentum[0],
                                         r.ic.momentum[1], r.ic.noise, (unsigned long long)r.seed);

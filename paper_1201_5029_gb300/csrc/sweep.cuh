@@ -71,9 +71,13 @@ __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, 
   double a = b.a;
   double pa = b.pa;
   const double s2 = b.sum_pi2;
+  const double VLrm = d.VL * d.rho_m0;
+  // one reciprocal per value of a instead of divisions: an FP64 division costs
+  // ~450 cycles of a single thread on GB300, and this runs at every block start
+  double ia = __drcp_rn(a), ia2 = ia * ia;
   // trailing Phi_H2(h_prev/2) of the previous stage: p_a += [sum pi^2/a^3 - V_L rho_m] h_prev/2
-  pa = pa + (s2 / (a * a * a) - d.VL * d.rho_m0) * (0.5 * hp);
-  double c = 0.5 * hp / (a * a);
+  pa = pa + (s2 * (ia2 * ia) - VLrm) * (0.5 * hp);
+  double c = (0.5 * hp) * ia2;
   if (mode != MODE_SWEEP) {
     // trailing Phi_H1(h_prev/2): a -= p_a h_prev / (12 V_L m^2)
     a = a - pa * d.inv6VLm2 * (0.5 * hp);
@@ -82,9 +86,11 @@ __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, 
   }
   // Phi_H1(h_prev/2) Phi_H1(h/2) merged (p_a is constant under H1)
   a = a - pa * d.inv6VLm2 * (0.5 * (hp + h));
+  ia = __drcp_rn(a);
+  ia2 = ia * ia;
   // leading Phi_H2(h/2)
-  pa = pa + (s2 / (a * a * a) - d.VL * d.rho_m0) * (0.5 * h);
-  c = c + 0.5 * h / (a * a);
+  pa = pa + (s2 * (ia2 * ia) - VLrm) * (0.5 * h);
+  c = c + (0.5 * h) * ia2;
   k.c = c;
   k.kD = a * a * h * d.dx2inv;
   k.kV = (a * a) * (a * a) * h;
@@ -203,7 +209,7 @@ struct Ctx {
 
   __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode) {
     k = prestage(bg, d, mode);
-    pk = P::prep(d.params);
+    pk = P::prep(d.params, d.derived);
     V0 = 0.0;
     if constexpr (PREC == PREC_SPLIT) {
       cdrift = (T)k.c; kD = (T)k.kD; kV = (T)k.kV;
@@ -218,11 +224,10 @@ struct Ctx {
         phi0s[f] = fma(k.c, pi0p[f], phi0p[f]);   // background drift
         shiftK[f] = 0;
       }
-      P::eval(pk, phi0s, dV0, V0);
+      sk = P::split_prep(pk, d.params, d.derived, phi0s, dV0, V0);
 #pragma unroll
       for (int f = 0; f < NF; ++f)  // background kick (D[phi0] = 0)
         pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], pi0p[f]) : pi0p[f];
-      sk = P::split_prep(d.params, phi0s);
     } else {
       cdrift = k.c; kD = k.kD; kV = k.kV;
 #pragma unroll
@@ -328,41 +333,84 @@ __device__ __forceinline__ void block_partials(const Acc<T>* acc, const T* accd_
 }
 
 // ---------------------------------------------------------------------------
-// Block finish: partials, ticket, and (last block) the background update.
-// sout holds this block's NQ sums on entry.
+// Fixed-order fold of P rows of NQ doubles (row r at src[r * kNQ + q]) into
+// out[0..NQ) (shared), by the whole block.  Warp w folds quantities w and
+// w + 8: lane k sums rows k, k + 32, k + 64, ... in that order, then a
+// shuffle tree adds lane k + h into k for h = 16, 8, 4, 2, 1.  The order
+// depends on P alone.  No shared-memory levels or block barriers: on GB300 a
+// dependent FP64 add costs ~60 cycles, so the fold is latency-bound.
+// ---------------------------------------------------------------------------
+template <int NQ>
+__device__ __forceinline__ void fold_rows(const double* src, int P, double* out) {
+  static_assert(NQ <= 2 * (kThreads / 32), "two quantities per warp at most");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q0 = warp, q1 = warp + kThreads / 32;
+  double s0 = 0.0, s1 = 0.0;
+  for (int r = lane; r < P; r += 32) {
+    if (q0 < NQ) s0 += __ldcg(&src[(size_t)r * kNQ + q0]);
+    if (q1 < NQ) s1 += __ldcg(&src[(size_t)r * kNQ + q1]);
+  }
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, h);
+    s1 += __shfl_down_sync(0xffffffffu, s1, h);
+  }
+  if (lane == 0) {
+    if (q0 < NQ) out[q0] = s0;
+    if (q1 < NQ) out[q1] = s1;
+  }
+  __syncthreads();
+}
+
+// Ticket increment with acquire-release semantics at GPU scope: it publishes
+// the caller's earlier stores (the row it wrote) and, for the block that takes
+// the last ticket, makes every other block's row visible.
+__device__ __forceinline__ unsigned int ticket_add(unsigned int* p) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
+// ---------------------------------------------------------------------------
+// Block finish: partials, tickets, and (last block) the background update.
+// sout holds this block's NQ sums on entry.  Two levels, so that almost all
+// of the fold overlaps the sweep: the last block of each group of kGroup
+// consecutive blocks folds the group's rows into one group row; the last group
+// to finish folds the group rows and advances the background.  Thread 0 writes
+// each row and takes the ticket; the block barrier after it orders the other
+// threads' reads of the rows.
 // ---------------------------------------------------------------------------
 template <int MODEL, int PREC, typename C>
 __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int mode, int cta,
-                                             double* sred, double* sout, int* s_last) {
+                                             double* sout, int* s_last) {
   using SL = typename C::SL;
   constexpr int NF = C::NF;
   constexpr int NQ = SL::NQ;
   const int tid = threadIdx.x;
-  if (tid < NQ) d.partials[(size_t)cta * kNQ + tid] = sout[tid];
-  __threadfence();
-  __syncthreads();
+  const int g = cta / kGroup;
+  const int g0 = g * kGroup;
+  const int gn = min(kGroup, d.ncta - g0);
   if (tid == 0) {
-    const unsigned int t = atomicAdd(d.ticket, 1u);
-    *s_last = (t == (unsigned int)(d.ncta - 1));
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) d.partials[(size_t)cta * kNQ + q] = sout[q];
+    *s_last = (ticket_add(&d.gticket[g]) == (unsigned int)(gn - 1));
   }
   __syncthreads();
   if (!*s_last) return;
-  __threadfence();
 
-  // ---- last block: fixed-order fold of the partials ------------------------
-  double tot[NQ];
+  // ---- last block of group g: fold the group's rows ------------------------
+  fold_rows<NQ>(d.partials + (size_t)g0 * kNQ, gn, sout);
+  if (tid == 0) {
+    d.gticket[g] = 0u;  // every block of the group has counted
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double s = 0.0, comp = 0.0;  // Neumaier
-    for (int c = tid; c < d.ncta; c += kThreads) {
-      const double x = __ldcg(&d.partials[(size_t)c * kNQ + q]);
-      const double t = s + x;
-      comp += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-      s = t;
-    }
-    tot[q] = s + comp;
+    for (int q = 0; q < NQ; ++q) d.gpartials[(size_t)g * kNQ + q] = sout[q];
+    *s_last = (ticket_add(d.ticket) == (unsigned int)(d.ngroups - 1));
   }
-  block_sum<NQ>(tot, sred, sout);
+  __syncthreads();
+  if (!*s_last) return;
+
+  // ---- last group: fold the group rows, then the background update ---------
+  fold_rows<NQ>(d.gpartials, d.ngroups, sout);
   if (tid != 0) return;
 
   Background* bgp = d.bg;
@@ -427,9 +475,9 @@ __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int 
       nb.s_phiD[f] = fphiD[f];
       // shifted-data mean and variance: K = shift (FP64) or phi0 (split)
       const double K = (PREC == PREC_FP64) ? bg.shift[f] : cx.phi0s[f];
-      const double m1 = fdphi[f] / Sd;
+      const double m1 = fdphi[f] * d.invS;
       nb.mean[f] = K + m1;
-      nb.var[f] = fdphi2[f] / Sd - m1 * m1;
+      nb.var[f] = fma(fdphi2[f], d.invS, -m1 * m1);
       ok = ok && is_fin(fdphi[f]) && is_fin(fdphi2[f]);
       // the next flush shifts by the mean just measured (keeps the variance well-conditioned)
       if (PREC == PREC_FP64) nb.shift[f] = nb.mean[f];
@@ -443,10 +491,10 @@ __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int 
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       nb.phi0[f] = cx.phi0s[f];
-      nb.mu_phi[f] = fdphi[f] / Sd;
+      nb.mu_phi[f] = fdphi[f] * d.invS;
       if (mode == MODE_SWEEP) {
         nb.pi0[f] = cx.pi0s[f];
-        nb.mu_pi[f] = sout[SL::DPI + f] / Sd;
+        nb.mu_pi[f] = sout[SL::DPI + f] * d.invS;
       }
       ok = ok && is_fin(cx.phi0s[f]) && is_fin(cx.pi0s[f]);
     }
@@ -456,9 +504,8 @@ __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int 
     nb.error = 1;
     nb.mode = MODE_IDLE;
   }
-  *bgp = nb;
+  *bgp = nb;  // published to the next launch by the kernel boundary
   *d.ticket = 0u;
-  __threadfence();
 }
 
 __device__ __forceinline__ int member_of(const LaunchTable& tab, int b) {
@@ -574,9 +621,6 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tma(const LaunchTable tab) 
   const size_t nn = (size_t)n * n;
 
   __shared__ C s_ctx;   // scalar context: computed once, by one thread (FP64 pipe is scarce)
-  if (threadIdx.x == 0) s_ctx.init(bgr, d, mode);
-  __syncthreads();
-  const C cx = s_ctx;
   const int ib = bgr.cur;  // bit0: phi buffer, bit1: pi buffer
   const T* __restrict__ phi_in = (const T*)d.phi[ib & 1];
   T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
@@ -645,8 +689,12 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tma(const LaunchTable tab) 
   if (tid == 0) {
     issue(0);
     if (Q > 1) issue(1);
+  } else if (tid == 32) {
+    s_ctx.init(bgr, d, mode);  // while the first planes are in flight
   }
   load_col(z0 - 1);
+  __syncthreads();
+  const C cx = s_ctx;
 
   Acc<T> acc[NQ];
   T accd_s[NQ];   // float64 path: plain per-thread sums
@@ -807,7 +855,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tma(const LaunchTable tab) 
     return;
   }
   block_partials<PREC, NQ, T>(acc, accd_s, sred, sout);
-  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sred, sout, &s_last);
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sout, &s_last);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -875,7 +923,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
   auto& stage = *reinterpret_cast<float (*)[NSLOT][2][NF][ROWS][TX]>(pipe_smem);
   __shared__ float colb[NSLOT][2][NF][2][ROWS];   // [slot][phi/pi][f][left/right][row]
   __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT];
-  __shared__ double sred[NWARP * NQ];
+  __shared__ double sred[(kThreads / 32) * NQ];
   __shared__ double sout[NQ];
   __shared__ int s_last, s_fault;
   __shared__ C s_ctx;
@@ -915,7 +963,6 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
   const int xl = wrapi(x0 - 1, n), xr = wrapi(x0 + TX, n);
 
   if (tid == 0) {
-    s_ctx.init(bgr, d, mode);
     for (int s = 0; s < NSLOT; ++s) {
       mbar_init(&full[s], 1 + 32);        // the TMA transaction + one warp of cp.async
       mbar_init(&empty[s], NWARP);
@@ -930,12 +977,6 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
     tensormap_acquire(tpi_row);
   }
   __syncthreads();
-  const C cx = s_ctx;
-  // re-centring of the output: phi* = phi + c pi - (mu_phi + c mu_pi); the
-  // stencil works on phi + c pi (D of a constant is zero)
-  float Mf[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) Mf[f] = madd(cx.cdrift, cx.mu_pi[f], cx.mu_phi[f]);
   const float c0 = CORNERS ? (float)(-128.0 / 30.0) : -6.0f;
   const float c1 = CORNERS ? (float)(14.0 / 30.0) : 1.0f;
   const float c2 = CORNERS ? (float)(3.0 / 30.0) : 0.0f;
@@ -971,7 +1012,16 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
     }
     cp_async_arrive_noinc(&full[s]);
   };
+  static_assert(LEAD < NWARP, "the last warp must not produce the first planes");
   for (int q = ly; q < LEAD && q < Q; q += NWARP) produce(q);
+  if (tid == kThreads - 32) s_ctx.init(bgr, d, mode);  // while the first planes are in flight
+  __syncthreads();
+  const C cx = s_ctx;
+  // re-centring of the output: phi* = phi + c pi - (mu_phi + c mu_pi); the
+  // stencil works on phi + c pi (D of a constant is zero)
+  float Mf[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Mf[f] = madd(cx.cdrift, cx.mu_pi[f], cx.mu_phi[f]);
 
   Acc<float> acc[NQ];
 #pragma unroll
@@ -1127,7 +1177,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
     }
     return;
   }
-  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sred, sout, &s_last);
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sout, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -1287,7 +1337,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_plain(const LaunchTable tab
     }
   }
   block_partials<PREC, NQ, T>(acc, accd_s, sred, sout);
-  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sred, sout, &s_last);
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sout, &s_last);
 }
 
 // Launch helper: dispatch (model, stencil, path/vx) at runtime to an instance.
