@@ -21,7 +21,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpycool.so")
-SOURCES = ("api.cu", "sweep_fp64.cu", "sweep_split.cu", "server.cu", "noalloc.cu")
+SOURCES = ("api.cu", "sweep_fp64.cu", "sweep_split.cu", "persist_fp64.cu", "persist_split.cu",
+           "server.cu", "noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

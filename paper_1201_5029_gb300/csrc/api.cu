@@ -2,6 +2,7 @@
 // layout, CUDA-graph replay of the sweep chain, observables, checkpoints.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -83,7 +84,53 @@ Layout layout_for(const pycool_config& c) {
   L.off_fields = L.off_desc + align256(sizeof(SimDesc));
   L.state_bytes = L.off_fields + 4 * L.field_bytes;
   workspace_layout(L.geo.ncta, L);
+  L.off_prows = 0;
   return L;
+}
+
+Layout sim_layout(const pycool_config& c) {
+  Layout L = layout_for(c);
+  if (L.geo.tma) {
+    L.off_prows = align256(L.ws_bytes);
+    L.ws_bytes = L.off_prows + align256((size_t)2 * kMaxPBlocks * kNQ * sizeof(double));
+  }
+  return L;
+}
+
+// Persistent geometry.  Tiles are 32 vx x 16 sites (vx sites per lane along
+// x, vx * N_f * word <= 16 bytes); the z-axis of every tile is cut into R
+// ranges (units = tiles x R, range-major).  R minimises the planes on the
+// busiest block, counting each unit's two z-halo planes at a fraction h of a
+// plane (FP64: only their drift is recomputed; split: their loads cost about
+// as much as the compute).
+PGeo choose_pgeo(int n, int word, int nf, int prec, int sms) {
+  PGeo g;
+  std::memset(&g, 0, sizeof(g));
+  g.n = n;
+  g.vx = 1;
+  for (int v = 4; v >= 1; v /= 2)
+    if (v * nf * word <= 16 && n % (32 * v) == 0) { g.vx = v; break; }
+  g.tx = 32 * g.vx;
+  g.tiles_x = n / g.tx;
+  g.ntiles = g.tiles_x * (n / 16);
+  const double h = prec == PREC_FP64 ? 0.1 : 0.5;
+  const int cap = std::min(sms, kMaxPBlocks);
+  double best = 1e300;
+  for (int R = 1; R <= n; ++R) {
+    const long long U = (long long)g.ntiles * R;
+    const long long G = std::min<long long>(U, cap);
+    const long long per = (U + G - 1) / G;
+    if (per > kMaxPUnits) continue;
+    const int zr = (n + R - 1) / R;
+    const double cost = (double)per * (zr + 2.0 * h);
+    if (cost < best - 1e-9) {
+      best = cost;
+      g.nranges = R;
+      g.nunits = (int)U;
+      g.G = (int)G;
+    }
+  }
+  return g;
 }
 
 void workspace_layout(int ncta, Layout& L) {
@@ -148,6 +195,9 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   for (int i = 0; i < 8; ++i) d.params[i] = c.params[i];
   d.invS = 1.0 / (double)d.S;
   if (c.model == PYCOOL_MODEL_QBALL) d.derived[0] = std::log(c.params[2] * c.params[2]);
+  for (int i = 0; i < 4; ++i) d.fparams[i] = (float)c.params[i];
+  d.fparams[4] = (float)(0.5 * c.params[0]);
+  d.fparams[5] = (float)(0.5 * c.params[1]);
   char* f = state + L.off_fields;
   d.phi[0] = f;
   d.phi[1] = f + L.field_bytes;
@@ -169,8 +219,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-cudaError_t encode_tensor_maps(SimDesc& d) {
-  if (!d.tma) return cudaSuccess;
+static cudaError_t encode_fn(EncodeTiledFn* out) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -181,24 +230,73 @@ cudaError_t encode_tensor_maps(SimDesc& d) {
     if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
     fn = (EncodeTiledFn)p;
   }
+  *out = fn;
+  return cudaSuccess;
+}
+
+// One 3-D map of a field buffer viewed as x: n, y: n, z: N_f n (fields stacked in z).
+static cudaError_t encode_box(EncodeTiledFn fn, CUtensorMap* m, const SimDesc& d, void* buf,
+                              int bx, int by) {
   const size_t word = d.prec == PREC_SPLIT ? 4 : 8;
   const CUtensorMapDataType dt =
       d.prec == PREC_SPLIT ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
   const cuuint64_t dims[3] = {(cuuint64_t)d.n, (cuuint64_t)d.n, (cuuint64_t)d.n * d.nf};
   const cuuint64_t strides[2] = {(cuuint64_t)d.n * word, (cuuint64_t)d.n * d.n * word};
-  const cuuint32_t box_tile[3] = {(cuuint32_t)d.tx, (cuuint32_t)d.ty, 1};
-  const cuuint32_t box_row[3] = {(cuuint32_t)d.tx, 1, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(m, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_tensor_maps(SimDesc& d) {
+  if (!d.tma) return cudaSuccess;
+  EncodeTiledFn fn = nullptr;
+  cudaError_t e = encode_fn(&fn);
+  if (e != cudaSuccess) return e;
   void* bufs[4] = {d.phi[0], d.phi[1], d.pi[0], d.pi[1]};
   for (int b = 0; b < 4; ++b) {
-    for (int k = 0; k < 2; ++k) {
-      const CUresult r = fn(&d.tmap[b][k], dt, 3, bufs[b], dims, strides, k == 0 ? box_tile : box_row,
-                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
+    if ((e = encode_box(fn, &d.tmap[b][0], d, bufs[b], d.tx, d.ty)) != cudaSuccess) return e;
+    if ((e = encode_box(fn, &d.tmap[b][1], d, bufs[b], d.tx, 1)) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// The persistent kernel's boxes over the four field buffers viewed as one 5-D
+// tensor (x: n, y: n, z: n, field: N_f, buffer: 4); see PParams::tm.
+cudaError_t encode_persist_maps(const SimDesc& d, const PGeo& g, PParams& p) {
+  EncodeTiledFn fn = nullptr;
+  cudaError_t e = encode_fn(&fn);
+  if (e != cudaSuccess) return e;
+  const size_t word = d.prec == PREC_SPLIT ? 4 : 8;
+  const cuuint64_t n = (cuuint64_t)d.n;
+  const cuuint64_t bstride = (cuuint64_t)((const char*)d.phi[1] - (const char*)d.phi[0]);
+  if ((const char*)d.pi[0] - (const char*)d.phi[0] != (ptrdiff_t)(2 * bstride) ||
+      (const char*)d.pi[1] - (const char*)d.phi[0] != (ptrdiff_t)(3 * bstride) || bstride % 16)
+    return cudaErrorInvalidValue;
+  const CUtensorMapDataType dt =
+      d.prec == PREC_SPLIT ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t dims[5] = {n, n, n, (cuuint64_t)d.nf, 4};
+  const cuuint64_t strides[4] = {n * word, n * n * word, n * n * n * word, bstride};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const int cw = (int)(16 / word);
+  const int shapes[6][3] = {{g.tx, 18, d.nf}, {cw, 18, d.nf}, {g.tx, 16, 1},
+                            {g.tx, 1, 1},     {cw, 16, 1},    {cw, 1, 1}};
+  for (int k = 0; k < 6; ++k) {
+    const cuuint32_t box[5] = {(cuuint32_t)shapes[k][0], (cuuint32_t)shapes[k][1], 1,
+                               (cuuint32_t)shapes[k][2], 1};
+    const CUresult r = fn(&p.tm[k], dt, 5, d.phi[0], dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_persist(const SimDesc& d, const PParams& p, int grid, cudaStream_t s, int* bps) {
+  if (d.prec == PREC_SPLIT) return launch_persist_split(d.model, d.stencil, p.g.vx, p, grid, s, bps);
+  return launch_persist_fp64(d.model, d.stencil, p.g.vx, p, grid, s, bps);
 }
 
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s) {
@@ -283,6 +381,10 @@ struct pycool_sim {
   bool initialised = false;
   bool poisoned = false;
   int64_t launches = 0;
+  // persistent evolve kernel (n a multiple of 32): one cooperative launch per
+  // evolve(); otherwise a chain of per-stage launches replayed as a graph
+  bool persist = false;
+  PParams pp{};
 };
 
 static constexpr int kGraphLen = 16;
@@ -316,7 +418,7 @@ PYCOOL_API pycool_status pycool_query_bytes(const pycool_config* cfg, size_t* st
                                             size_t* workspace_bytes) {
   const pycool_status st = validate(cfg);
   if (st != PYCOOL_OK) return st;
-  const Layout L = layout_for(*cfg);
+  const Layout L = sim_layout(*cfg);
   if (state_bytes) *state_bytes = L.state_bytes;
   if (workspace_bytes) *workspace_bytes = L.ws_bytes;
   return PYCOOL_OK;
@@ -338,6 +440,40 @@ static pycool_status build_graph(pycool_sim* sim) {
   return PYCOOL_OK;
 }
 
+// Persistent path: geometry for this device, tensor maps, occupancy check.
+// Leaves sim->persist false (per-stage launches) if one block per SM does not fit.
+static pycool_status setup_persist(pycool_sim* sim) {
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
+  const int word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  PGeo g = choose_pgeo(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms);
+  PParams& p = sim->pp;
+  std::memset(&p, 0, sizeof(p));
+  p.g = g;
+  CK(encode_persist_maps(sim->hdesc, g, p));
+  p.d = sim->d_desc;
+  p.bg = sim->d_bg;
+  p.bar = (unsigned long long*)(sim->ws + sim->L.off_ticket + 64);
+  p.bar_base = 0;
+  p.rows = sim->ws + sim->L.off_prows;
+  p.fault = sim->hdesc.fault;
+  int bps = 0;
+  CK(launch_persist(sim->hdesc, p, 0, sim->stream, &bps));
+  sim->persist = bps >= 1 && g.G <= bps * sms;
+  return PYCOOL_OK;
+}
+
+// One cooperative launch: nsweeps stage sweeps and the flush.  The grid
+// barrier counter is monotonic (zeroed with the workspace counters); the host
+// tracks how many arrivals earlier launches made.
+static pycool_status launch_persist_sweeps(pycool_sim* sim, long long nsweeps) {
+  sim->pp.nsweeps = nsweeps;
+  CK(launch_persist(sim->hdesc, sim->pp, sim->pp.g.G, sim->stream, nullptr));
+  sim->pp.bar_base += (unsigned long long)(nsweeps + 1) * (unsigned long long)sim->pp.g.G;
+  sim->launches += 1;
+  return PYCOOL_OK;
+}
+
 PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state,
                                        void* dev_workspace, void* cuda_stream,
                                        pycool_sim** out) {
@@ -349,7 +485,7 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
   pycool_sim* sim = new (std::nothrow) pycool_sim();
   if (!sim) return PYCOOL_E_NOMEM;
   sim->cfg = *cfg;
-  sim->L = layout_for(*cfg);
+  sim->L = sim_layout(*cfg);
   sim->nf = model_nfields(cfg->model);
   sim->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&sim->device);
@@ -417,10 +553,19 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
     pycool_destroy(sim);
     return PYCOOL_E_CUDA;
   }
-  st = build_graph(sim);
-  if (st != PYCOOL_OK) {
-    pycool_destroy(sim);
-    return st;
+  if (sim->L.off_prows) {
+    st = setup_persist(sim);
+    if (st != PYCOOL_OK) {
+      pycool_destroy(sim);
+      return st;
+    }
+  }
+  if (!sim->persist) {
+    st = build_graph(sim);
+    if (st != PYCOOL_OK) {
+      pycool_destroy(sim);
+      return st;
+    }
   }
   *out = sim;
   return PYCOOL_OK;
@@ -500,7 +645,9 @@ PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, 
   }
   CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
   CK(cudaMemsetAsync(sim->ws, 0, sim->L.off_partials, sim->stream));
-  pycool_status st = launch_one(sim);
+  sim->pp.bar_base = 0;
+  // the reducing flush: sums of the initial state (and p_a from H = 0)
+  pycool_status st = sim->persist ? launch_persist_sweeps(sim, 0) : launch_one(sim);
   if (st != PYCOOL_OK) return st;
   CK(cudaEventRecord(sim->done, sim->stream));
   CK(cudaStreamSynchronize(sim->stream));
@@ -514,6 +661,12 @@ PYCOOL_API pycool_status pycool_evolve(pycool_sim* sim, int64_t steps) {
   if (!sim->initialised) return PYCOOL_E_STATE;
   if (steps == 0) return PYCOOL_OK;
   const long long nsweeps = (long long)steps * sim->nstages;
+  if (sim->persist) {
+    pycool_status st = launch_persist_sweeps(sim, nsweeps);
+    if (st != PYCOOL_OK) return st;
+    CK(cudaEventRecord(sim->done, sim->stream));
+    return PYCOOL_OK;
+  }
   CK(launch_arm(sim->d_bg, nsweeps, sim->stream));
   sim->launches += 1;
   long long left = nsweeps + 1;  // + the synchronising flush
@@ -670,6 +823,7 @@ PYCOOL_API pycool_status pycool_checkpoint_load(pycool_sim* sim, const void* buf
   CK(cudaMemcpy(sim->hdesc.pi[(b.cur >> 1) & 1], p + sizeof(b) + fb, fb, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice));
   CK(cudaMemset(sim->ws, 0, sim->L.off_partials));
+  sim->pp.bar_base = 0;
   CK(cudaEventRecord(sim->done, sim->stream));
   sim->initialised = true;
   return PYCOOL_OK;

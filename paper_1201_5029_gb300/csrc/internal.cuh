@@ -70,6 +70,7 @@ struct alignas(64) SimDesc {
   double invS;                // 1 / n^3
   double params[8];
   double derived[4];          // host-computed model constants (Q-ball: ln M^2)
+  float fparams[8];           // params[] and, from slot 4 on, half of params 0 and 1, in float32
   double w[kMaxStages];
   void* phi[2];
   void* pi[2];
@@ -126,10 +127,55 @@ inline Geometry choose_geometry(int n, int word, int nf) {
   return g;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent evolve kernel (persist.cuh): one cooperative launch per evolve()
+// call, one 512-thread block per SM, tiles of 32 vx x 16 sites.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPBlocks = 1024;          // partial-sum rows reserved in the workspace
+constexpr int kMaxPUnits = 64;             // work units per block
+
+// Geometry, chosen on the host (a function of n, word, N_f and the SM count).
+//   units = tiles x z-ranges, ordered range-major; block b owns units
+//   b, b + G, b + 2G, ...
+struct PGeo {
+  int n, vx, tx, tiles_x, ntiles, nranges, nunits, G;
+};
+
+// Kernel parameters, passed as one __grid_constant__ struct (the tensor maps
+// live in parameter space, as TMA wants them).
+struct PParams {
+  // [box]: the four field buffers (phi0, phi1, pi0, pi1: equally spaced in the
+  // state block) viewed as ONE 5-D tensor (x: n, y: n, z: n, field: N_f,
+  // buffer: 4), so that a stage switch uses the same six descriptors;
+  // cw = 16 bytes / word; every box spans one buffer and one z-plane:
+  //   0: tx x 18 x N_f  tile with both halo rows, every field (y0 > 0, y0 + 16 < n)
+  //   1: cw x 18 x N_f  halo column with its corner cells, every field (same tiles)
+  //   2: tx x 16 x 1    tile rows of one field        (tiles at the y wrap)
+  //   3: tx x 1 x 1     one halo row of one field
+  //   4: cw x 16 x 1    halo column of one field
+  //   5: cw x 1 x 1     one corner cell of one field
+  CUtensorMap tm[6];
+  const SimDesc* d;
+  Background* bg;
+  unsigned long long* bar;       // grid barrier: arrivals so far (monotonic)
+  unsigned long long bar_base;   // arrivals before this launch
+  void* rows;              // [2][G][kNQ] doubles (FP64) or float pairs (split)
+  int32_t* fault;
+  PGeo g;
+  long long nsweeps;       // stage sweeps of this launch (then one flush)
+};
+
+PGeo choose_pgeo(int n, int word, int nf, int prec, int sms);
+
 // Launchers (one translation unit per precision).
 cudaError_t launch_sweep_fp64(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
                               cudaStream_t s);
 cudaError_t launch_sweep_split(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
                                cudaStream_t s);
+// grid == 0: set the kernel attributes and report blocks per SM in *bps.
+cudaError_t launch_persist_fp64(int model, int stencil, int vx, const PParams& p, int grid,
+                                cudaStream_t s, int* bps);
+cudaError_t launch_persist_split(int model, int stencil, int vx, const PParams& p, int grid,
+                                 cudaStream_t s, int* bps);
 
 }  // namespace pycool

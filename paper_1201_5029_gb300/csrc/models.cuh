@@ -9,8 +9,10 @@
 //
 // Pot<M>::eval gives V and dV/dphi_i in float64.  Pot<M>::split_prep gives,
 // at the float64 background phi0, V(phi0), V'(phi0) and the float32 constants
-// of the difference forms (one call per block: it runs in a single thread, so
-// each model computes its transcendental functions there only once).
+// of the difference forms.  It runs in one thread per stage, where every
+// float64 instruction is ~70 cycles of latency on GB300, so constants that are
+// only used in float32 are formed in float32 (fp: the parameters in float32;
+// slots 4 and 5 hold m2/2 and params[1]/2) wherever that costs at most an ulp.
 // Pot<M>::SplitK / diff give,
 // in float32, the differences dV'_i = V'_i(phi0 + d) - V'_i(phi0) and
 // dV = V(phi0 + d) - V(phi0) around a float64 background phi0, written so that
@@ -37,10 +39,11 @@ template <> struct Pot<M_FREE> {
     V = k.hm2 * f[0] * f[0];
   }
   struct SplitK { float m2, hm2, p0, two_p0; };
-  __device__ static SplitK split_prep(const K& pk, const double* p, const double*,
+  __device__ static SplitK split_prep(const K& pk, const double*, const double*, const float* fp,
                                       const double* phi0, double* dV0, double& V0) {
     eval(pk, phi0, dV0, V0);
-    return SplitK{(float)p[0], (float)(0.5 * p[0]), (float)phi0[0], (float)(2.0 * phi0[0])};
+    const float p0 = (float)phi0[0];
+    return SplitK{fp[0], fp[4], p0, 2.f * p0};
   }
   __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {
     dVd[0] = k.m2 * d[0];
@@ -61,15 +64,15 @@ template <> struct Pot<M_CHAOTIC2> {
     V = ph2 * (0.5 * t);                                // phi^2 (m2 + g2 chi^2) / 2
   }
   struct SplitK { float m2, g2, hm2, hg2, p0, c0, two_p0, two_c0, p0sq, c0sq; };
-  __device__ static SplitK split_prep(const K& pk, const double* p, const double*,
+  __device__ static SplitK split_prep(const K& pk, const double*, const double*, const float* fp,
                                       const double* b, double* dV0, double& V0) {
     eval(pk, b, dV0, V0);
     SplitK k;
-    k.m2 = (float)p[0]; k.g2 = (float)p[1];
-    k.hm2 = (float)(0.5 * p[0]); k.hg2 = (float)(0.5 * p[1]);
+    k.m2 = fp[0]; k.g2 = fp[1];
+    k.hm2 = fp[4]; k.hg2 = fp[5];
     k.p0 = (float)b[0]; k.c0 = (float)b[1];
-    k.two_p0 = (float)(2.0 * b[0]); k.two_c0 = (float)(2.0 * b[1]);
-    k.p0sq = (float)(b[0] * b[0]); k.c0sq = (float)(b[1] * b[1]);
+    k.two_p0 = 2.f * k.p0; k.two_c0 = 2.f * k.c0;   // exact
+    k.p0sq = k.p0 * k.p0; k.c0sq = k.c0 * k.c0;     // within an ulp of the float64 square
     return k;
   }
   // P = phi^2, Q = chi^2:  dP = d_phi (2 phi0 + d_phi),  dQ = d_chi (2 chi0 + d_chi)
@@ -101,7 +104,7 @@ template <> struct Pot<M_OSCILLON> {
     V = x2 * fma(x2, fma(k.sg, x2, -k.qlam), k.hm2);      // m2/2 x^2 - lam/4 x^4 + g/6 x^6
   }
   // V' and V are polynomials, so their differences are exact Taylor polynomials
-  // in d around x0 whose coefficients (computed in float64) are
+  // in d around x0 whose coefficients are
   //   dV'(d) = d (c1 + d (c2 + d (c3 + d (c4 + d c5))))
   //     c1 = m2 - 3 lam x0^2 + 5 g x0^4,  c2 = -3 lam x0 + 10 g x0^3,
   //     c3 = -lam + 10 g x0^2,  c4 = 5 g x0,  c5 = g
@@ -109,23 +112,28 @@ template <> struct Pot<M_OSCILLON> {
   //     e1 = m2 x0 - lam x0^3 + g x0^5,  e2 = m2/2 - 3 lam/2 x0^2 + 5 g/2 x0^4,
   //     e3 = -lam x0 + 10 g/3 x0^3,  e4 = -lam/4 + 5 g/2 x0^2,  e5 = g x0,  e6 = g/6
   struct SplitK { float c[5], e[6]; };
-  __device__ static SplitK split_prep(const K& pk, const double* p, const double*,
+  // The leading coefficients c1 = V''(x0) and e1 = V'(x0) are formed in float64
+  // (they may be small differences of larger terms); the higher-order ones
+  // multiply at least d^2 and are formed in float32.
+  __device__ static SplitK split_prep(const K& pk, const double* p, const double*, const float* fp,
                                       const double* b, double* dV0, double& V0) {
     eval(pk, b, dV0, V0);
     const double m2 = p[0], lam = p[1], g = p[2];
-    const double x = b[0], x2 = x * x, x3 = x2 * x, x4 = x3 * x, x5 = x4 * x;
+    const double x = b[0], x2 = x * x, x4 = x2 * x2;
     SplitK k;
-    k.c[0] = (float)(m2 - 3.0 * lam * x2 + 5.0 * g * x4);
-    k.c[1] = (float)(-3.0 * lam * x + 10.0 * g * x3);
-    k.c[2] = (float)(-lam + 10.0 * g * x2);
-    k.c[3] = (float)(5.0 * g * x);
-    k.c[4] = (float)g;
-    k.e[0] = (float)(m2 * x - lam * x3 + g * x5);
-    k.e[1] = (float)(0.5 * m2 - 1.5 * lam * x2 + 2.5 * g * x4);
-    k.e[2] = (float)(-lam * x + (10.0 / 3.0) * g * x3);
-    k.e[3] = (float)(-0.25 * lam + 2.5 * g * x2);
-    k.e[4] = (float)(g * x);
-    k.e[5] = (float)(g / 6.0);
+    k.c[0] = (float)fma(x4, 5.0 * g, fma(x2, -3.0 * lam, m2));   // V''(x0)
+    k.e[0] = (float)dV0[0];                                      // V'(x0)
+    const float mf = fp[0], lf = fp[1], gf = fp[2];
+    const float xf = (float)x, xf2 = xf * xf, xf3 = xf2 * xf, xf4 = xf2 * xf2;
+    k.c[1] = fmaf(10.f * gf, xf3, -3.f * lf * xf);
+    k.c[2] = fmaf(10.f * gf, xf2, -lf);
+    k.c[3] = 5.f * gf * xf;
+    k.c[4] = gf;
+    k.e[1] = fmaf(2.5f * gf, xf4, fmaf(-1.5f * lf, xf2, 0.5f * mf));
+    k.e[2] = fmaf((10.f / 3.f) * gf, xf3, -lf * xf);
+    k.e[3] = fmaf(2.5f * gf, xf2, -0.25f * lf);
+    k.e[4] = gf * xf;
+    k.e[5] = gf * (1.f / 6.f);
     return k;
   }
   __device__ static void diff(const SplitK& k, const float* dd, float* dVd, float& dVv) {
@@ -163,7 +171,7 @@ template <> struct Pot<M_QBALL> {
   //   dV    = m2 [ B du + K l (u0 + du) ],      B = 1 + K L0,  L0 = ln(u0/M^2)
   struct SplitK { float m2, K, A, B, p1, p2, u0, inv_u0; int direct; float lnM2; };
   // one logarithm for V(phi0), V'(phi0) and the constants (dv[0] = ln M^2)
-  __device__ static SplitK split_prep(const K& pk, const double* p, const double* dv,
+  __device__ static SplitK split_prep(const K& pk, const double* p, const double* dv, const float*,
                                       const double* b, double* dV0, double& V0) {
     SplitK k;
     const double u0 = 0.5 * fma(b[0], b[0], b[1] * b[1]);

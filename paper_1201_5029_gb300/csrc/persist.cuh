@@ -1,0 +1,955 @@
+// The persistent evolve kernel: one cooperative launch advances a lattice
+// through every stage of an evolve() call -- `nsweeps` fused stage sweeps
+// (Sec. 2.3, one per second-order stage Phi1(h/2) Phi2(h/2) Phi3(h) Phi2(h/2)
+// Phi1(h/2), drift merged across stage boundaries exactly as in sweep.cuh)
+// and the synchronising flush -- with one resident block per SM.
+//
+// Why: a stage is a global dependency (the drift coefficient of stage i+1
+// needs a and p_a after Phi_H3 of stage i, i.e. lattice-wide sums of stage i),
+// so a per-stage launch pays the launch ramp, the tail of its last block and a
+// re-derivation of the scalar coefficients in every block, every stage.  Here:
+//   - each block owns a fixed list of work units (tile x z-range), ordered
+//     range-major so that blocks running together are neighbouring tiles at
+//     the same z (their halo rows and columns hit L2);
+//   - all loads are TMA (tile, two halo rows, two 16-byte halo-column boxes,
+//     and for the 27-point stencil four corner cells) into an mbarrier ring;
+//   - at the end of a stage every block writes one row of partial sums; a
+//     grid barrier (atomic arrival counter + generation word, bounded spin)
+//     separates stages; every block then folds all rows in the same fixed
+//     order, so every block derives bit-identical sums, background and
+//     coefficients without another launch, and block 0 alone writes the final
+//     Background back.
+// The per-site arithmetic (drift, Eq. D, kick, sums) is that of sweep.cuh
+// (Ctx<>::site, the same potentials and difference forms), so the FP64 and
+// split-FP32 forms compute what the per-launch kernels compute, in a different
+// (fixed) summation order.
+//
+// FP64 form: a plane is drifted once into a shared-memory buffer (one block
+// barrier per plane), since FP64 arithmetic is the binding resource on GB300.
+// Split-FP32 form: barrier-free warp pipeline (each warp drifts the three rows
+// it needs in registers; "empty" mbarriers release slots; the producer role
+// rotates over the warps), since that form is bound by memory traffic.
+#pragma once
+
+#include "sweep.cuh"
+
+namespace pycool {
+
+constexpr int kPThreads = 512;               // one block per SM
+constexpr int kPWarps = kPThreads / 32;
+constexpr int kPTY = kPWarps;                // tile rows: one per warp
+constexpr int kColFieldBytes = 512;          // halo column of one field (y-wrap layout)
+constexpr int kPSmemBudget = 200 * 1024;     // dynamic shared memory per block
+static_assert(kPTY * 16 == 256, "column box layout assumes 16 rows of 16 bytes");
+static_assert((kPTY + 2) * 16 <= kColFieldBytes, "a dense 18-row column fits a field's slot");
+
+// Slot layout (elements of WORD bytes), every TMA destination 128-byte aligned:
+//   main[arr][f][TY+2][TX]      rows 0 and TY+1 are the halo rows
+//   col[arr][side][...]         the x-1 / x+TX halo columns of all fields, in one
+//                               of two layouts: tiles clear of the y wrap get one
+//                               dense box [f][TY+2][CW]; tiles at the wrap get per
+//                               field [f][512 B: low cell | TY rows | high cell]
+template <int NF, int VX, int WORD>
+struct PLayout {
+  static constexpr int TX = 32 * VX;
+  static constexpr int CW = 16 / WORD;                                // column box width
+  static constexpr int MAIN = (kPTY + 2) * TX;                        // elements per (array, field)
+  static constexpr int COLF = kColFieldBytes / WORD;                  // elements per field column
+  static constexpr int SLOT = 2 * NF * (MAIN + 2 * COLF);             // elements per slot
+  static constexpr int SLOT_BYTES = SLOT * WORD;
+  __device__ static constexpr int main_off(int arr, int f) { return (arr * NF + f) * MAIN; }
+  __device__ static constexpr int col_base(int arr, int side) {
+    return 2 * NF * MAIN + (arr * 2 + side) * NF * COLF;
+  }
+  // element offset of field f, column row r (0 = y0-1, 1..TY = tile rows, TY+1 = y0+TY)
+  __device__ static constexpr int col_dense(int f, int r) { return (f * (kPTY + 2) + r) * CW; }
+  __device__ static constexpr int col_wrap(int f, int r) {
+    return f * COLF + (r == 0 ? 0 : (128 + (r - 1) * 16) / WORD);
+  }
+};
+
+// TMA ring of a form: NSLOT slots, LEAD planes in flight ahead of the plane
+// being computed.  FP64 (ALU-bound): three slots.  Split (memory-bound): as
+// many slots as fit beside the per-thread compensated sums (NQ float pairs per
+// thread), at most eight.
+//   FP64 extra: two drifted-plane buffers [NF][TY+2][TX] (one per plane parity)
+//               and the block-reduction scratch [NQ][threads].
+//   split extra: the per-thread compensated sums [NQ][threads] float pairs.
+template <int PREC, int NF, int VX, int NQ>
+struct PRing {
+  using LY = PLayout<NF, VX, PREC == PREC_FP64 ? 8 : 4>;
+  static constexpr int DRIFT_ELEMS = NF * (kPTY + 2) * LY::TX;
+  static constexpr int EXTRA_BYTES =
+      PREC == PREC_FP64 ? 2 * DRIFT_ELEMS * 8 + NQ * kPThreads * 8 : NQ * kPThreads * 8;
+  static constexpr int FIT = (kPSmemBudget - EXTRA_BYTES) / LY::SLOT_BYTES;
+  static constexpr int NSLOT = PREC == PREC_FP64 ? 3 : (FIT < 8 ? FIT : 8);
+  // planes ahead: the slots less two, and at most the warps that do not fold
+  // the block sums (each issues one of a stage's first planes)
+  static constexpr int LEAD = PREC == PREC_FP64 ? 2
+                              : (NSLOT - 2 < kPWarps - NQ ? NSLOT - 2 : kPWarps - NQ);
+  static constexpr int RING_BYTES = NSLOT * LY::SLOT_BYTES;
+  static constexpr int SMEM_BYTES = RING_BYTES + EXTRA_BYTES;
+  static_assert(NSLOT >= 4 || PREC == PREC_FP64, "split ring too shallow");
+};
+
+template <int MODEL, int PREC, int VX>
+constexpr size_t persist_smem_bytes() {
+  return (size_t)PRing<PREC, Pot<MODEL>::NF, VX, Slots<Pot<MODEL>::NF, PREC>::NQ>::SMEM_BYTES;
+}
+
+// Shared-memory state of a block, passed to the stage functions.
+struct PShared {
+  const SimDesc* d;       // shared-memory copy of the simulation descriptor
+  unsigned char* ring;
+  float2* kahan;          // split: [NQ][kPThreads] compensated sums (s, c)
+  double* drift;          // FP64: two drifted planes [parity][NF][TY+2][TX]
+  double* red;            // FP64: block-reduction scratch [NQ][kPThreads]
+  uint64_t* full;
+  uint64_t* empty;
+  const int4* units;      // (x0, y0, z0, Q): tile origin, first output plane, planes incl. halos
+  int nunits;
+  uint32_t* issued;       // per slot: 1 + ring index of the last plane issued
+};
+
+// Advance a (unit, plane) position by one plane.
+__device__ __forceinline__ void padvance(const PShared& sm, int& ui, int& uq) {
+  if (ui < sm.nunits && ++uq == sm.units[ui].w) { ++ui; uq = 0; }
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid barrier of the cooperative launch: a monotonic arrival counter.
+// Thread 0 adds its arrival with release semantics (publishing the block's
+// global writes, ordered before it by the block barrier) and polls the
+// counter with acquire loads until every block of this barrier has arrived
+// (target = arrivals before it + G).  The poll is bounded by ~2^31 clocks
+// (about a second); on timeout it reports false instead of waiting on.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long target) {
+  bool ok = true;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red_release_add_u64(count, 1ull);
+    if (ld_acquire_u64(count) < target) {
+      const long long t0 = clock64();
+      for (uint32_t i = 1; ld_acquire_u64(count) < target; ++i)
+        if ((i & 63u) == 0u && clock64() - t0 > (1ll << 31)) { ok = false; break; }
+    }
+  }
+  return ok;
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            int f, int buf, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(buf),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Does unit u's tile (rows y0-1 .. y0+TY) stay clear of the periodic y wrap?
+__device__ __forceinline__ bool yclear(int4 u, int n) { return u.y > 0 && u.y + kPTY < n; }
+
+// Issue the TMA copies of plane q of unit u into `slot` (one thread): tile,
+// halo rows, halo columns (and, 27-point stencil, corner cells) of phi and pi
+// of every field.  A tile clear of the y wrap takes 3 boxes per array (tile
+// with both halo rows, two columns, all fields at once); a tile at the wrap
+// takes its rows and cells one field at a time.  Every box is in bounds: x0
+// and the column x are multiples of 16 bytes, wrapped rows are separate boxes.
+template <int NF, int VX, int WORD, bool CORNERS>
+__device__ __forceinline__ void pproduce(const PParams& p, int ib, int4 u, int q,
+                                         unsigned char* slot, uint64_t* bar) {
+  using LY = PLayout<NF, VX, WORD>;
+  constexpr int TX = LY::TX, CW = LY::CW;
+  constexpr uint32_t kClear = 2u * NF * ((kPTY + 2) * TX * WORD + 2 * (kPTY + 2) * 16);
+  constexpr uint32_t kWrap = 2u * NF * ((kPTY + 2) * TX * WORD + 2 * kPTY * 16 + (CORNERS ? 4 * 16 : 0));
+  const int n = p.g.n;
+  const int zw = wrapi(u.z - 1 + q, n);
+  const int xl = (u.x == 0 ? n : u.x) - CW;
+  const int xr = (u.x + TX == n) ? 0 : u.x + TX;
+  const CUtensorMap* m = p.tm;
+  if (yclear(u, n)) {
+    mbar_expect_tx(bar, kClear);
+#pragma unroll
+    for (int arr = 0; arr < 2; ++arr) {
+      const int bi = arr == 0 ? (ib & 1) : 2 + ((ib >> 1) & 1);   // buffer of phi / pi
+      tma_load_5d(slot + (size_t)LY::main_off(arr, 0) * WORD, &m[0], u.x, u.y - 1, zw, 0, bi, bar);
+      tma_load_5d(slot + (size_t)LY::col_base(arr, 0) * WORD, &m[1], xl, u.y - 1, zw, 0, bi, bar);
+      tma_load_5d(slot + (size_t)LY::col_base(arr, 1) * WORD, &m[1], xr, u.y - 1, zw, 0, bi, bar);
+    }
+    return;
+  }
+  const int yl = wrapi(u.y - 1, n), yh = wrapi(u.y + kPTY, n);
+  mbar_expect_tx(bar, kWrap);
+#pragma unroll
+  for (int arr = 0; arr < 2; ++arr) {
+    const int bi = arr == 0 ? (ib & 1) : 2 + ((ib >> 1) & 1);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      unsigned char* mb = slot + (size_t)LY::main_off(arr, f) * WORD;
+      tma_load_5d(mb + (size_t)TX * WORD, &m[2], u.x, u.y, zw, f, bi, bar);
+      tma_load_5d(mb, &m[3], u.x, yl, zw, f, bi, bar);
+      tma_load_5d(mb + (size_t)(kPTY + 1) * TX * WORD, &m[3], u.x, yh, zw, f, bi, bar);
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        unsigned char* cb = slot + (size_t)(LY::col_base(arr, side) + f * LY::COLF) * WORD;
+        const int xc = side ? xr : xl;
+        tma_load_5d(cb + 128, &m[4], xc, u.y, zw, f, bi, bar);
+        if constexpr (CORNERS) {
+          tma_load_5d(cb, &m[5], xc, yl, zw, f, bi, bar);
+          tma_load_5d(cb + 128 + kPTY * 16, &m[5], xc, yh, zw, f, bi, bar);
+        }
+      }
+    }
+  }
+}
+
+// Stencil parts of one plane (Eq. D split by z-offset, as in sweep.cuh):
+//   S_mid = c0 ctr + c1 faces + c2 corners,  S_off = c1 ctr + c2 faces + c3 corners.
+// MID = false computes S_off only (the two z-halo planes of a unit).
+template <typename T, int VX, bool CORNERS, bool MID>
+__device__ __forceinline__ void plane_parts(const T (&ctr)[VX], const T (&dn)[VX], const T (&up)[VX],
+                                            T left, T right, T dl, T dr, T ul, T ur,
+                                            T (&smid)[VX], T (&so)[VX]) {
+  const T c0 = CORNERS ? (T)(-128.0 / 30.0) : (T)(-6.0);
+  const T c1 = CORNERS ? (T)(14.0 / 30.0) : (T)1.0;
+  const T c2 = CORNERS ? (T)(3.0 / 30.0) : (T)0.0;
+  const T c3 = CORNERS ? (T)(1.0 / 30.0) : (T)0.0;
+#pragma unroll
+  for (int j = 0; j < VX; ++j) {
+    if constexpr (!CORNERS) {
+      so[j] = ctr[j];
+      if constexpr (MID) {
+        const T L = j > 0 ? ctr[j - 1] : left;
+        const T R = j < VX - 1 ? ctr[j + 1] : right;
+        smid[j] = madd(c0, ctr[j], (dn[j] + up[j]) + (L + R));
+      }
+    } else {
+      const T L = j > 0 ? ctr[j - 1] : left;
+      const T R = j < VX - 1 ? ctr[j + 1] : right;
+      const T faces = (dn[j] + up[j]) + (L + R);
+      const T DL = j > 0 ? dn[j - 1] : dl;
+      const T DR = j < VX - 1 ? dn[j + 1] : dr;
+      const T UL = j > 0 ? up[j - 1] : ul;
+      const T UR = j < VX - 1 ? up[j + 1] : ur;
+      const T corners = (DL + DR) + (UL + UR);
+      if constexpr (MID) smid[j] = madd(c2, corners, madd(c1, faces, c0 * ctr[j]));
+      so[j] = madd(c3, corners, madd(c2, faces, c1 * ctr[j]));
+    }
+  }
+}
+
+// x-neighbours of a lane's VX sites (shuffles; lanes 0 and 31 take the halo
+// column) and the four diagonal neighbours (27-point stencil), then the parts.
+template <typename T, int VX, bool CORNERS, bool MID, int CR>
+__device__ __forceinline__ void lane_parts(const T (&ctr)[VX], const T (&dn)[VX], const T (&up)[VX],
+                                           const T (&el)[CR], T (&smid)[VX], T (&so)[VX]) {
+  const int lane = threadIdx.x & 31;
+  T left = 0, right = 0, dl = 0, dr = 0, ul = 0, ur = 0;
+  if (MID || CORNERS) {
+    left = __shfl_up_sync(0xffffffffu, ctr[VX - 1], 1);
+    right = __shfl_down_sync(0xffffffffu, ctr[0], 1);
+    if (lane == 0) left = el[(CR - 1) / 2];
+    if (lane == 31) right = el[(CR - 1) / 2];
+  }
+  if constexpr (CORNERS) {
+    dl = __shfl_up_sync(0xffffffffu, dn[VX - 1], 1);
+    dr = __shfl_down_sync(0xffffffffu, dn[0], 1);
+    ul = __shfl_up_sync(0xffffffffu, up[VX - 1], 1);
+    ur = __shfl_down_sync(0xffffffffu, up[0], 1);
+    if (lane == 0) { dl = el[0]; ul = el[CR - 1]; }
+    if (lane == 31) { dr = el[0]; ur = el[CR - 1]; }
+  }
+  plane_parts<T, VX, CORNERS, MID>(ctr, dn, up, left, right, dl, dr, ul, ur, smid, so);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 form.
+// ---------------------------------------------------------------------------
+// One stage of the FP64 form over this block's units: each plane is drifted
+// once into a shared-memory drift buffer, then one block barrier, then the
+// stencil from the drifted plane.  Returns false (in every thread) if a wait gave up.
+// gq: ring planes consumed before this stage.
+template <int MODEL, int STENCIL, int VX, int MODE>
+__device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PREC_FP64>& cx,
+                                           const PShared& sm, uint32_t gq, int ib, double* accd) {
+  using C = Ctx<MODEL, PREC_FP64>;
+  using T = double;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int CR = CORNERS ? 3 : 1;
+  using LY = PLayout<NF, VX, 8>;
+  using RG = PRing<PREC_FP64, NF, VX, SL::NQ>;
+  constexpr int TX = LY::TX, CW = LY::CW;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  const SimDesc& d = *sm.d;
+  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+  const int n = p.g.n;
+  const size_t S = (size_t)d.S, nn = (size_t)n * n;
+  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
+  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
+  const T cd = cx.cdrift;
+  const int side = lane == 31 ? 1 : 0;
+  const int own = (ly + 1) * TX + lane * VX;          // this lane's sites in a slot row
+
+  int pui = 0, puq = 0;                                 // producer position, LEAD ahead
+  for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  uint32_t g = gq;
+  for (int i = 0; i < sm.nunits; ++i) {
+    const int4 u = sm.units[i];
+    const int Q = u.w;
+    const bool clear = yclear(u, n);
+    const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
+    T part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int jj = 0; jj < VX; ++jj) part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = 0.0;
+    for (int q = 0; q < Q; ++q, ++g) {
+      const int s = g % NSLOT;
+      const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
+      T* dp = sm.drift + (g & 1) * RG::DRIFT_ELEMS;   // this plane's drifted phi
+      const bool ok = mbar_wait(&sm.full[s], (g / NSLOT) & 1);
+      // drift the own row and the two halo rows (warps 0 and 1) into the
+      // drift buffer, and the halo-column values this lane needs (registers)
+      T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* mph = sl + LY::main_off(0, f);
+        const T* mpi = sl + LY::main_off(1, f);
+        T* dph = dp + f * (kPTY + 2) * TX;
+        T a[VX], b[VX];
+        vload<T, VX>(&mph[own], a);
+        vload<T, VX>(&mpi[own], b);
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          cur_pi[f][jj] = b[jj];
+          cur_ph[f][jj] = madd(cd, b[jj], a[jj]);
+        }
+        vstore<T, VX>(&dph[own], cur_ph[f]);
+        if (ly < 2) {
+          const int r = (ly == 0 ? 0 : kPTY + 1) * TX + lane * VX;
+          vload<T, VX>(&mph[r], a);
+          vload<T, VX>(&mpi[r], b);
+#pragma unroll
+          for (int jj = 0; jj < VX; ++jj) a[jj] = madd(cd, b[jj], a[jj]);
+          vstore<T, VX>(&dph[r], a);
+        }
+        const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
+        const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
+#pragma unroll
+        for (int rr = 0; rr < CR; ++rr) {
+          const int r = ly + 1 + rr - (CR - 1) / 2;
+          const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+          el[f][rr] = madd(cd, cpi[row], cph[row]);
+        }
+      }
+      if (__syncthreads_or(!ok)) return false;   // one decision for the whole block
+      if (tid == 0 && pui < sm.nunits) {
+        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift
+        const uint32_t gp = g + LEAD;
+        pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
+                                     sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                     &sm.full[gp % NSLOT]);
+        sm.issued[gp % NSLOT] = gp + 1;
+      }
+      padvance(sm, pui, puq);
+
+      const bool mid = q > 0 && q < Q - 1;   // the z-halo planes need S_off only
+      T so_new[NF][VX], smid_new[NF][VX];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* dph = dp + f * (kPTY + 2) * TX;
+        T dn[VX], up[VX];
+        if (mid || CORNERS) {
+          vload<T, VX>(&dph[own - TX], dn);
+          vload<T, VX>(&dph[own + TX], up);
+        }
+        if (mid)
+          lane_parts<T, VX, CORNERS, true, CR>(cur_ph[f], dn, up, el[f], smid_new[f], so_new[f]);
+        else
+          lane_parts<T, VX, CORNERS, false, CR>(cur_ph[f], dn, up, el[f], smid_new[f], so_new[f]);
+      }
+      if (q >= 2) {  // output plane z0 + q - 2
+        const size_t o = o0 + (size_t)(q - 2) * nn;
+        T pin[NF][VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          T phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            phj[f] = ph_m[f][jj];
+            Dj[f] = part_m[f][jj] + so_new[f][jj];
+            pmj[f] = pi_m[f][jj];
+          }
+          cx.site(MODE, phj, Dj, pmj, pnj, accd);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pin[f][jj] = pnj[f];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          vstore<T, VX>(phi_out + f * S + o, ph_m[f]);
+          if (MODE == MODE_SWEEP) vstore<T, VX>(pi_out + f * S + o, pin[f]);
+        }
+      }
+      if (mid) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int jj = 0; jj < VX; ++jj)
+            part_m[f][jj] = (CORNERS ? so_m[f][jj] : ph_m[f][jj]) + smid_new[f][jj];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          if constexpr (CORNERS) so_m[f][jj] = so_new[f][jj];
+          ph_m[f][jj] = cur_ph[f][jj];
+          pi_m[f][jj] = cur_pi[f][jj];
+        }
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Split-FP32 form.
+// ---------------------------------------------------------------------------
+// Producer of ring plane gp (one warp): waits until every warp has released
+// the slot's previous plane, then lane 0 issues the copies.
+template <int NF, int VX, bool CORNERS, int NSLOT>
+__device__ __noinline__ bool produce_split(const PParams& p, const PShared& sm, int ib, uint32_t gp,
+                                           int4 u, int q) {
+  using LY = PLayout<NF, VX, 4>;
+  bool ok = true;
+  if (gp >= (uint32_t)NSLOT) {
+    const uint32_t rr = gp - NSLOT;
+    ok = mbar_wait(&sm.empty[rr % NSLOT], (rr / NSLOT) & 1);
+  }
+  if (!__all_sync(0xffffffffu, ok)) return false;
+  if ((threadIdx.x & 31) == 0) {
+    pproduce<NF, VX, 4, CORNERS>(p, ib, u, q, sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                 &sm.full[gp % NSLOT]);
+    sm.issued[gp % NSLOT] = gp + 1;
+  }
+  return true;
+}
+
+// Add a thread's float partials into its compensated sums (shared memory).
+template <int NQ>
+__device__ __forceinline__ void kahan_flush(float2* kahan, float (&ps)[NQ]) {
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    float2 v = kahan[i * kPThreads + threadIdx.x];
+    const float y = ps[i] - v.y;
+    const float t = v.x + y;
+    v.y = (t - v.x) - y;
+    v.x = t;
+    kahan[i * kPThreads + threadIdx.x] = v;
+    ps[i] = 0.f;
+  }
+}
+
+// One stage of the split-FP32 form: barrier-free warp pipeline.  Ring plane
+// gq + j is produced by warp (gq + j) mod 16; every warp drifts the three rows
+// it needs in registers and releases the slot.  Returns false
+// (warp-uniformly) if a wait gave up.
+template <int MODEL, int STENCIL, int VX, int MODE>
+__device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, PREC_SPLIT>& cx,
+                                            const PShared& sm, uint32_t gq, int ib) {
+  using C = Ctx<MODEL, PREC_SPLIT>;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int CR = CORNERS ? 3 : 1;
+  using LY = PLayout<NF, VX, 4>;
+  using RG = PRing<PREC_SPLIT, NF, VX, NQ>;
+  constexpr int TX = LY::TX, CW = LY::CW;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  constexpr int KGROUP = 8;   // output planes per float partial before a compensated add
+  const SimDesc& d = *sm.d;
+  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+  const int n = p.g.n;
+  const size_t S = (size_t)d.S, nn = (size_t)n * n;
+  float* __restrict__ phi_out = (float*)d.phi[(ib & 1) ^ 1];
+  float* __restrict__ pi_out = (float*)d.pi[((ib >> 1) & 1) ^ 1];
+  const float cd = cx.cdrift;
+  // re-centring: phi* = phi + c pi - (mu_phi + c mu_pi); the stencil works on
+  // phi + c pi (D of a constant is zero)
+  float Mf[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Mf[f] = madd(cd, cx.mu_pi[f], cx.mu_phi[f]);
+  const int side = lane == 31 ? 1 : 0;
+  const int own = (ly + 1) * TX + lane * VX;
+
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) sm.kahan[i * kPThreads + tid] = make_float2(0.f, 0.f);
+  float ps[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) ps[i] = 0.f;
+  int kg = 0;
+
+  int pui = 0, puq = 0;
+  for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  bool ok = true;
+  uint32_t g = gq;
+  for (int i = 0; i < sm.nunits; ++i) {
+    const int4 u = sm.units[i];
+    const int Q = u.w;
+    const bool clear = yclear(u, n);
+    const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
+    float part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int jj = 0; jj < VX; ++jj) part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = 0.f;
+    for (int q = 0; q < Q; ++q, ++g) {
+      const int s = g % NSLOT;
+      if (pui < sm.nunits) {
+        const uint32_t gp = g + LEAD;
+        if ((int)(gp % kPWarps) == ly)
+          ok = produce_split<NF, VX, CORNERS, NSLOT>(p, sm, ib, gp, sm.units[pui], puq) && ok;
+        padvance(sm, pui, puq);
+      }
+      ok = ok && mbar_wait(&sm.full[s], (g / NSLOT) & 1);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      const float* sl = (const float*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
+      // the three rows this warp needs and the halo-column values, drifted in registers
+      float cur_ph[NF][VX], cur_pi[NF][VX], dn[NF][VX], up[NF][VX], el[NF][CR];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const float* mph = sl + LY::main_off(0, f);
+        const float* mpi = sl + LY::main_off(1, f);
+        float a[VX], b[VX];
+        vload<float, VX>(&mph[own], a);
+        vload<float, VX>(&mpi[own], b);
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          cur_pi[f][jj] = b[jj] - cx.mu_pi[f];
+          cur_ph[f][jj] = madd(cd, b[jj], a[jj]);
+        }
+        vload<float, VX>(&mph[own - TX], a);
+        vload<float, VX>(&mpi[own - TX], b);
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) dn[f][jj] = madd(cd, b[jj], a[jj]);
+        vload<float, VX>(&mph[own + TX], a);
+        vload<float, VX>(&mpi[own + TX], b);
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) up[f][jj] = madd(cd, b[jj], a[jj]);
+        const float* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
+        const float* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
+#pragma unroll
+        for (int rr = 0; rr < CR; ++rr) {
+          const int r = ly + 1 + rr - (CR - 1) / 2;
+          const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+          el[f][rr] = madd(cd, cpi[row], cph[row]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the slot
+
+      const bool mid = q > 0 && q < Q - 1;   // the z-halo planes need S_off only
+      float so_new[NF][VX], smid_new[NF][VX];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (mid)
+          lane_parts<float, VX, CORNERS, true, CR>(cur_ph[f], dn[f], up[f], el[f], smid_new[f],
+                                                   so_new[f]);
+        else
+          lane_parts<float, VX, CORNERS, false, CR>(cur_ph[f], dn[f], up[f], el[f], smid_new[f],
+                                                    so_new[f]);
+      }
+      if (q >= 2) {  // output plane z0 + q - 2
+        const size_t o = o0 + (size_t)(q - 2) * nn;
+        float pin[NF][VX], phs[NF][VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          float phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            phs[f][jj] = ph_m[f][jj] - Mf[f];   // the re-centred drifted field
+            phj[f] = phs[f][jj];
+            Dj[f] = part_m[f][jj] + so_new[f][jj];
+            pmj[f] = pi_m[f][jj];
+          }
+          cx.site(MODE, phj, Dj, pmj, pnj, ps);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pin[f][jj] = pnj[f];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          vstore<float, VX>(phi_out + f * S + o, phs[f]);
+          if (MODE == MODE_SWEEP) vstore<float, VX>(pi_out + f * S + o, pin[f]);
+        }
+        if (++kg == KGROUP) {
+          kg = 0;
+          kahan_flush<NQ>(sm.kahan, ps);
+        }
+      }
+      if (mid) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int jj = 0; jj < VX; ++jj)
+            part_m[f][jj] = (CORNERS ? so_m[f][jj] : ph_m[f][jj]) + smid_new[f][jj];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          if constexpr (CORNERS) so_m[f][jj] = so_new[f][jj];
+          ph_m[f][jj] = cur_ph[f][jj];
+          pi_m[f][jj] = cur_pi[f][jj];
+        }
+    }
+  }
+  kahan_flush<NQ>(sm.kahan, ps);
+  return true;
+}
+
+// Plane l (< LEAD) of a stage, issued by lane 0 of the calling warp.  Used at
+// stage starts, one warp per plane.  Every plane of the previous stage has
+// been consumed and released before the block barrier that precedes this
+// call, so the slot needs no wait (the "empty" phases still complete as usual).
+template <int PREC, int NF, int VX, bool CORNERS, int NSLOT>
+__device__ __forceinline__ void prefetch_plane(const PParams& p, const PShared& sm, int ib,
+                                               uint32_t gq, int l) {
+  constexpr int WORD = PREC == PREC_FP64 ? 8 : 4;
+  using LY = PLayout<NF, VX, WORD>;
+  int ui = 0, uq = 0;
+  for (int j = 0; j < l; ++j) padvance(sm, ui, uq);
+  if (ui >= sm.nunits || (threadIdx.x & 31) != 0) return;
+  const uint32_t gp = gq + l;
+  pproduce<NF, VX, WORD, CORNERS>(p, ib, sm.units[ui], uq,
+                                  sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                  &sm.full[gp % NSLOT]);
+  sm.issued[gp % NSLOT] = gp + 1;
+}
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.
+// ---------------------------------------------------------------------------
+template <int MODEL, int STENCIL, int PREC, int VX>
+__global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_constant__ PParams p) {
+  using C = Ctx<MODEL, PREC>;
+  using SL = typename C::SL;
+  constexpr int NQ = SL::NQ;
+  constexpr int NF = C::NF;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  using RG = PRing<PREC, NF, VX, NQ>;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  static_assert(NQ <= kPWarps, "one warp per reduced quantity");
+  static_assert(NQ + LEAD <= kPWarps, "stage-start prefetch: one warp per plane beside the folds");
+
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT];
+  // background and stage coefficients, double-buffered: at a stage boundary
+  // one thread derives the next coefficients while another does the rest of
+  // the background bookkeeping
+  __shared__ __align__(16) Background sbv[2];
+  __shared__ C sctxv[2];
+  __shared__ double s_ia;
+  // the scalar chain between stages reads the descriptor many times; the
+  // ring leaves little L1, so it is kept in shared memory
+  __shared__ __align__(64) SimDesc s_desc;
+  __shared__ double sums[kNQ];
+  __shared__ int4 s_units[kMaxPUnits];
+  __shared__ uint32_t s_issued[NSLOT];
+  __shared__ int s_bad;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SimDesc& d = s_desc;
+  const int G = p.g.G;
+  static_assert(sizeof(SimDesc) % 8 == 0, "descriptor copied as 8-byte words");
+  for (int i = tid; i < (int)(sizeof(SimDesc) / 8); i += kPThreads)
+    reinterpret_cast<unsigned long long*>(&s_desc)[i] =
+        __ldg(reinterpret_cast<const unsigned long long*>(p.d) + i);
+  PShared sm;
+  sm.d = &s_desc;
+  sm.ring = dsm;
+  sm.kahan = reinterpret_cast<float2*>(dsm + RG::RING_BYTES);
+  sm.drift = reinterpret_cast<double*>(dsm + RG::RING_BYTES);
+  sm.red = reinterpret_cast<double*>(dsm + RG::RING_BYTES) + 2 * RG::DRIFT_ELEMS;
+  sm.full = full;
+  sm.empty = empty;
+  sm.units = s_units;
+  sm.issued = s_issued;
+  sm.nunits = ((int)blockIdx.x < p.g.nunits) ? (p.g.nunits - (int)blockIdx.x + G - 1) / G : 0;
+  if (sm.nunits > kMaxPUnits) sm.nunits = kMaxPUnits;   // the host never asks for more
+
+  if (tid == 0) {
+    for (int s = 0; s < NSLOT; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kPWarps);
+    }
+    fence_mbar_init();
+    s_bad = 0;
+  }
+  if (tid < NSLOT) s_issued[tid] = 0;
+  if (tid < 6) {   // bring the tensor maps into the descriptor cache
+    const CUtensorMap* m = &p.tm[tid];
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+  }
+  if (tid < sm.nunits) {   // this block's units: tiles x z-ranges, range-major
+    const int id = (int)blockIdx.x + tid * G;
+    const int t = id % p.g.ntiles, r = id / p.g.ntiles;
+    const int z0 = (int)(((long long)r * p.g.n) / p.g.nranges);
+    const int z1 = (int)(((long long)(r + 1) * p.g.n) / p.g.nranges);
+    s_units[tid] = make_int4((t % p.g.tiles_x) * p.g.tx, (t / p.g.tiles_x) * kPTY, z0, z1 - z0 + 2);
+  }
+  static_assert(sizeof(Background) % 8 == 0, "background copied as 8-byte words");
+  if (tid < (int)(sizeof(Background) / 8))
+    reinterpret_cast<unsigned long long*>(&sbv[0])[tid] =
+        __ldcg(reinterpret_cast<const unsigned long long*>(p.bg) + tid);
+  __syncthreads();
+  if (sbv[0].error) return;   // a stopped simulation stays stopped (same in every block)
+  if (tid == 0) {
+    sbv[0].sweeps_left = p.nsweeps;
+    sbv[0].mode = p.nsweeps > 0 ? MODE_SWEEP : MODE_FLUSH;
+  }
+  int cb = 0;   // current buffer of sbv / sctxv
+  uint32_t np = 0;
+  for (int i = 0; i < sm.nunits; ++i) np += (uint32_t)s_units[i].w;
+  uint32_t gq = 0;
+  const long long K = p.nsweeps;
+  bool fault = false;
+  int ib = sbv[0].cur;
+  // stage 0: its first planes are in flight while one thread derives the
+  // scalar coefficients (the FP64 chain of the merged half-stages)
+  {
+    const int l = kPWarps - 1 - warp;   // warp 15 - l issues plane l
+    if (l < LEAD) prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib, gq, l);
+    if (tid == 0) sctxv[0].init(sbv[0], d, K > 0 ? MODE_SWEEP : MODE_FLUSH);
+    __syncthreads();
+    fault = s_bad != 0;
+  }
+  for (long long k = 0; k <= K && !fault; ++k) {
+    const int mode = (k < K) ? MODE_SWEEP : MODE_FLUSH;
+    const C cx = sctxv[cb];
+    // @stage-start
+
+    // ---- the sweep (per-thread sums) ----
+    bool ok = true;
+    double accd[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) accd[q] = 0.0;
+    if constexpr (PREC == PREC_FP64) {
+      ok = (mode == MODE_SWEEP)
+               ? stage_fp64<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib, accd)
+               : stage_fp64<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib, accd);
+    } else {
+      ok = (mode == MODE_SWEEP) ? stage_split<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib)
+                                : stage_split<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib);
+    }
+    if (!ok) atomicOr(&s_bad, 1);
+    gq += np;
+    // global stores of this stage will be read by TMA (async proxy) next stage
+    fence_proxy_async_global();
+    __syncthreads();
+    // @units-done
+    if (s_bad) { fault = true; break; }
+
+    // ---- block sums: one warp per quantity over the 512 threads' values, fixed order ----
+    if constexpr (PREC == PREC_FP64) {
+      double* red = sm.red;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) red[q * kPThreads + tid] = accd[q];
+      __syncthreads();
+      if (warp < NQ) {
+        // 16 values per lane summed as a pairwise tree (depth 4: FP64 latency is long)
+        double x[kPThreads / 32];
+#pragma unroll
+        for (int r = 0; r < kPThreads / 32; ++r) x[r] = red[warp * kPThreads + lane + 32 * r];
+#pragma unroll
+        for (int w = kPThreads / 64; w >= 1; w >>= 1)
+#pragma unroll
+          for (int r = 0; r < w; ++r) x[r] = x[2 * r] + x[2 * r + 1];
+        double v = x[0];
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) v += __shfl_down_sync(0xffffffffu, v, h);
+        if (lane == 0)
+          reinterpret_cast<double*>(p.rows)[((size_t)(k & 1) * G + blockIdx.x) * kNQ + warp] = v;
+      }
+    } else {
+      if (warp < NQ) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int r = 0; r < kPThreads / 32; ++r) {
+          const float2 v = sm.kahan[warp * kPThreads + lane + 32 * r];
+          pair_add(hi, lo, v.x, -v.y);
+        }
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+          const float bh = __shfl_down_sync(0xffffffffu, hi, h);
+          const float bl = __shfl_down_sync(0xffffffffu, lo, h);
+          pair_add(hi, lo, bh, bl);
+        }
+        if (lane == 0)
+          reinterpret_cast<float2*>(p.rows)[((size_t)(k & 1) * G + blockIdx.x) * kNQ + warp] =
+              make_float2(hi, lo);
+      }
+    }
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned long long)(k + 1) * G)) s_bad = 1;
+    __syncthreads();
+    // @released
+    if (s_bad) { fault = true; break; }
+
+    // ---- after the barrier, on disjoint warps:
+    //   warps 0..NQ-1 fold every block's row (in block order, identically in
+    //     every block); the next stage's copies wait until these latency-
+    //     critical loads have landed (named barrier 1), so that they are not
+    //     queued behind the copies;
+    //   warps 15, 14, ... issue the next stage's first planes, one each (its
+    //     buffers are known: a sweep swaps phi and pi, a flush swaps phi);
+    //   warp 14 also takes 1/a for the next stage's coefficients ----
+    const int ib_next = ib ^ (mode == MODE_SWEEP ? 3 : 1);
+    const bool pre = k < K;
+    constexpr int kPreThreads = (NQ + LEAD) * 32;
+    if (warp < NQ) {
+      using FT = typename std::conditional<PREC == PREC_FP64, double, float2>::type;
+      const FT* rows = reinterpret_cast<const FT*>(p.rows) + (size_t)(k & 1) * G * kNQ;
+      FT x[8];
+      if constexpr (PREC == PREC_FP64) {
+        double v = 0.0;
+        for (int r0 = 0; r0 < G; r0 += 32 * 8) {   // 8 loads in flight, added in row order
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int r = r0 + lane + 32 * j;
+            if (r < G) x[j] = __ldcg(&rows[(size_t)r * kNQ + warp]);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (r0 + lane + 32 * j < G) v += x[j];
+          if (r0 == 0 && pre) named_arrive(1, kPreThreads);   // our loads have landed
+        }
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) v += __shfl_down_sync(0xffffffffu, v, h);
+        if (lane == 0) sums[warp] = v;
+      } else {
+        float hi = 0.f, lo = 0.f;
+        for (int r0 = 0; r0 < G; r0 += 32 * 8) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int r = r0 + lane + 32 * j;
+            if (r < G) x[j] = __ldcg(&rows[(size_t)r * kNQ + warp]);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (r0 + lane + 32 * j < G) pair_add(hi, lo, x[j].x, x[j].y);
+          if (r0 == 0 && pre) named_arrive(1, kPreThreads);   // our loads have landed
+        }
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+          const float bh = __shfl_down_sync(0xffffffffu, hi, h);
+          const float bl = __shfl_down_sync(0xffffffffu, lo, h);
+          pair_add(hi, lo, bh, bl);
+        }
+        if (lane == 0) sums[warp] = (double)hi + (double)lo;
+      }
+      // @sums-written
+    } else {
+      const int l = kPWarps - 1 - warp;
+      if (pre && l < LEAD) {
+        named_sync(1, kPreThreads);
+        prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib_next, gq, l);
+      }
+      // @prefetch-issued
+      if (warp == kPWarps - 2 && lane == 0)
+        s_ia = __drcp_rn(sctxv[cb].k.a);   // the next stage's Background has a = k.a
+    }
+    __syncthreads();
+    // @folded
+    // ---- the next stage's coefficients (warp 14) and the bookkeeping of this
+    //      stage (warp 13), in parallel; identical in every block ----
+    if (tid == kPThreads - 64) {
+      if (k < K) {
+        Background nb = sbv[cb];
+        next_init_fields<MODEL, PREC>(sctxv[cb], d, sums, sbv[cb], nb);
+        sctxv[cb ^ 1].init(nb, d, k + 1 < K ? MODE_SWEEP : MODE_FLUSH, s_ia);
+      }
+    } else if (tid == kPThreads - 96) {
+      post_stage<MODEL, PREC>(sctxv[cb], d, mode, sums, sbv[cb], sbv[cb ^ 1]);
+    }
+    __syncthreads();
+    // @coefficients
+    cb ^= 1;
+    if (s_bad) { fault = true; break; }
+    if (sbv[cb].error) break;   // identical sums in every block: every block stops here
+    ib = ib_next;
+  }
+
+  // copies issued for a stage that will not run (a stop after a non-finite
+  // sum, or a fault) must land before the block exits (bounded waits)
+  __syncthreads();
+  if (tid == 0) {
+    if (fault) atomicOr(p.fault, 1);
+    for (int s = 0; s < NSLOT; ++s)
+      if (s_issued[s]) mbar_wait(&full[s], ((s_issued[s] - 1u) / NSLOT) & 1u);
+  }
+  if (fault) return;   // the state is not trusted any more (the host poisons the simulation)
+  if (blockIdx.x == 0 && tid < (int)(sizeof(Background) / 8))
+    reinterpret_cast<unsigned long long*>(p.bg)[tid] =
+        reinterpret_cast<const unsigned long long*>(&sbv[cb])[tid];
+}
+
+// Launch helper (one translation unit per precision).  grid == 0: only set
+// the kernel's shared-memory attribute and report its occupancy in *bps.
+template <int PREC>
+cudaError_t launch_persist_impl(int model, int stencil, int vx, const PParams& p, int grid,
+                                cudaStream_t s, int* bps) {
+#define PYCOOL_P(M, ST, V)                                                                  \
+  if constexpr (V * Pot<M>::NF * (PREC == PREC_FP64 ? 8 : 4) <= 16) {                       \
+    if (model == M && stencil == ST && vx == V) {                                           \
+      constexpr size_t smem = persist_smem_bytes<M, PREC, V>();                             \
+      auto kern = evolve_persist<M, ST, PREC, V>;                                           \
+      if (grid == 0) {                                                                      \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem);                                    \
+        if (e != cudaSuccess) return e;                                                     \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, kPThreads, smem);   \
+      }                                                                                     \
+      cudaLaunchConfig_t cfg = {};                                                          \
+      cfg.gridDim = dim3(grid);                                                             \
+      cfg.blockDim = dim3(kPThreads);                                                       \
+      cfg.dynamicSmemBytes = smem;                                                          \
+      cfg.stream = s;                                                                       \
+      cudaLaunchAttribute attr[1];                                                          \
+      attr[0].id = cudaLaunchAttributeCooperative;                                          \
+      attr[0].val.cooperative = 1;                                                          \
+      cfg.attrs = attr;                                                                     \
+      cfg.numAttrs = 1;                                                                     \
+      return cudaLaunchKernelEx(&cfg, kern, p);                                             \
+    }                                                                                       \
+  }
+#define PYCOOL_PM(X, V)                                                                     \
+  X(M_FREE, 7, V) X(M_FREE, 27, V) X(M_CHAOTIC2, 7, V) X(M_CHAOTIC2, 27, V)                 \
+  X(M_OSCILLON, 7, V) X(M_OSCILLON, 27, V) X(M_QBALL, 7, V) X(M_QBALL, 27, V)
+  PYCOOL_PM(PYCOOL_P, 1)
+  PYCOOL_PM(PYCOOL_P, 2)
+  if constexpr (PREC == PREC_SPLIT) { PYCOOL_PM(PYCOOL_P, 4) }
+#undef PYCOOL_PM
+#undef PYCOOL_P
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pycool

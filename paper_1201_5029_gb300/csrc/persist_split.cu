@@ -1,0 +1,9 @@
+// Split-FP32 instances of the persistent evolve kernel (every model x stencil).
+#include "persist.cuh"
+
+namespace pycool {
+cudaError_t launch_persist_split(int model, int stencil, int vx, const PParams& p, int grid,
+                                 cudaStream_t s, int* bps) {
+  return launch_persist_impl<PREC_SPLIT>(model, stencil, vx, p, grid, s, bps);
+}
+}  // namespace pycool

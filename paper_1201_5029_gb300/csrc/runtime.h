@@ -18,6 +18,7 @@ struct Layout {
   size_t field_bytes;
   size_t off_bg, off_desc, off_fields, state_bytes;
   size_t off_ticket, off_gticket, off_partials, off_gpartials, ws_bytes;
+  size_t off_prows;   // single-simulation API: rows of the persistent kernel (0 = none)
 };
 
 // Workspace layout of a launch of `ncta` blocks (fills the off_* / ws_bytes fields).
@@ -26,6 +27,11 @@ void workspace_layout(int ncta, Layout& L);
 int stage_table(int order, double* w);
 int model_nfields(int model);
 Layout layout_for(const pycool_config& c);
+// layout_for() plus the persistent kernel's partial-sum rows in the workspace
+// (what pycool_query_bytes reports and pycool_create uses).
+Layout sim_layout(const pycool_config& c);
+cudaError_t encode_persist_maps(const SimDesc& d, const PGeo& g, PParams& p);
+cudaError_t launch_persist(const SimDesc& d, const PParams& p, int grid, cudaStream_t s, int* bps);
 pycool_status validate(const pycool_config* c);
 void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state, char* ws);
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s);

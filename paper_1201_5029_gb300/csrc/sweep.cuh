@@ -64,7 +64,9 @@ struct Coef {
   double h;      // this stage's step (0 for a flush)
 };
 
-__device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, int mode) {
+// ia_a: 1/b.a if the caller already has it (a negative value means "compute it").
+__device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, int mode,
+                                         double ia_a = -1.0) {
   Coef k;
   const double hp = b.h_prev;
   const double h = (mode == MODE_SWEEP) ? d.w[b.stage] * d.dt : 0.0;
@@ -74,7 +76,7 @@ __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, 
   const double VLrm = d.VL * d.rho_m0;
   // one reciprocal per value of a instead of divisions: an FP64 division costs
   // ~450 cycles of a single thread on GB300, and this runs at every block start
-  double ia = __drcp_rn(a), ia2 = ia * ia;
+  double ia = ia_a > 0.0 ? ia_a : __drcp_rn(a), ia2 = ia * ia;
   // trailing Phi_H2(h_prev/2) of the previous stage: p_a += [sum pi^2/a^3 - V_L rho_m] h_prev/2
   pa = pa + (s2 * (ia2 * ia) - VLrm) * (0.5 * hp);
   double c = (0.5 * hp) * ia2;
@@ -202,13 +204,15 @@ struct Ctx {
   Coef k;
   typename P::K pk;
   T cdrift, kD, kV;
+  T nkVg;                          // FP64 chaotic model: -kV g2 (folded into the chi kick)
   T mu_phi[NF], mu_pi[NF];
   T shiftK[NF];
   double phi0s[NF], pi0s[NF], V0;  // split form: background after drift / kick
   typename P::SplitK sk;
 
-  __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode) {
-    k = prestage(bg, d, mode);
+  __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode,
+                                       double ia_a = -1.0) {
+    k = prestage(bg, d, mode, ia_a);
     pk = P::prep(d.params, d.derived);
     V0 = 0.0;
     if constexpr (PREC == PREC_SPLIT) {
@@ -224,12 +228,13 @@ struct Ctx {
         phi0s[f] = fma(k.c, pi0p[f], phi0p[f]);   // background drift
         shiftK[f] = 0;
       }
-      sk = P::split_prep(pk, d.params, d.derived, phi0s, dV0, V0);
+      sk = P::split_prep(pk, d.params, d.derived, d.fparams, phi0s, dV0, V0);
 #pragma unroll
       for (int f = 0; f < NF; ++f)  // background kick (D[phi0] = 0)
         pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], pi0p[f]) : pi0p[f];
     } else {
       cdrift = k.c; kD = k.kD; kV = k.kV;
+      if constexpr (MODEL == M_CHAOTIC2) nkVg = -k.kV * d.params[1];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         mu_phi[f] = 0; mu_pi[f] = 0; phi0s[f] = 0; pi0s[f] = 0;
@@ -242,7 +247,30 @@ struct Ctx {
   //   phj: drifted fields, D: Laplacian, pim: momenta -> pin: new momenta
   __device__ __forceinline__ void site(int mode, const T (&phj)[NF], const T (&D)[NF],
                                        const T (&pim)[NF], T (&pin)[NF], T* ps) const {
-    if constexpr (PREC == PREC_FP64) {
+    if constexpr (PREC == PREC_FP64 && MODEL == M_CHAOTIC2) {
+      // V = phi^2 (m2 + g2 chi^2)/2; the kicks with kV folded into the products,
+      // and 2V accumulated (halved once, in post_stage): 4 DMUL + 6 DFMA
+      const double ph2 = phj[0] * phj[0];
+      const double t = fma(pk.g2, phj[1] * phj[1], pk.m2);      // m2 + g2 chi^2
+      if (mode == MODE_SWEEP) {
+        pin[0] = madd(kD, D[0], madd(-kV * phj[0], t, pim[0]));   // - kV phi (m2 + g2 chi^2)
+        pin[1] = madd(kD, D[1], madd(nkVg * ph2, phj[1], pim[1]));   // - kV g2 phi^2 chi
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (mode == MODE_SWEEP) {
+          ps[SL::PI2 + f] = madd(pin[f], pin[f], ps[SL::PI2 + f]);
+        } else {
+          pin[f] = pim[f];
+          ps[SL::PI2 + f] = madd(pim[f], pim[f], ps[SL::PI2 + f]);
+          const T dd = phj[f] - shiftK[f];
+          ps[SL::DPHI + f] += dd;
+          ps[SL::DPHI2 + f] = madd(dd, dd, ps[SL::DPHI2 + f]);
+        }
+        ps[SL::PHID + f] = madd(phj[f], D[f], ps[SL::PHID + f]);
+      }
+      ps[SL::V] = madd(ph2, t, ps[SL::V]);
+    } else if constexpr (PREC == PREC_FP64) {
       double dV[NF], V;
       P::eval(pk, phj, dV, V);
 #pragma unroll
@@ -362,63 +390,25 @@ __device__ __forceinline__ void fold_rows(const double* src, int P, double* out)
   __syncthreads();
 }
 
-// Ticket increment with acquire-release semantics at GPU scope: it publishes
-// the caller's earlier stores (the row it wrote) and, for the block that takes
-// the last ticket, makes every other block's row visible.
-__device__ __forceinline__ unsigned int ticket_add(unsigned int* p) {
-  unsigned int old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
-  return old;
-}
-
 // ---------------------------------------------------------------------------
-// Block finish: partials, tickets, and (last block) the background update.
-// sout holds this block's NQ sums on entry.  Two levels, so that almost all
-// of the fold overlaps the sweep: the last block of each group of kGroup
-// consecutive blocks folds the group's rows into one group row; the last group
-// to finish folds the group rows and advances the background.  Thread 0 writes
-// each row and takes the ticket; the block barrier after it orders the other
-// threads' reads of the rows.
+// Background update after a stage, from the stage's lattice sums `sout`
+// (NQ doubles, slot layout Slots<NF, PREC>): the p_a kick of Phi_H3 (Eq.
+// split-Phi) and the stage/step counters for a sweep; the H = 0 root (Eq. H2),
+// the synchronised sums and the field statistics for a flush.  Shared by the
+// per-launch kernels (last block) and the persistent kernel (every block).
 // ---------------------------------------------------------------------------
+// Lattice sums of a stage from its reduced slots (NQ doubles, Slots<NF, PREC>):
+// per field sum pi^2, sum phi D, sum (phi - K), sum (phi - K)^2, and sum V.
 template <int MODEL, int PREC, typename C>
-__device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int mode, int cta,
-                                             double* sout, int* s_last) {
+__device__ __forceinline__ void stage_sums(const C& cx, const SimDesc& d, int mode,
+                                           const double* sout, double* fpi2, double* fphiD,
+                                           double* fdphi, double* fdphi2, double& sum_pi2,
+                                           double& sum_phiD, double& sum_V) {
   using SL = typename C::SL;
   constexpr int NF = C::NF;
-  constexpr int NQ = SL::NQ;
-  const int tid = threadIdx.x;
-  const int g = cta / kGroup;
-  const int g0 = g * kGroup;
-  const int gn = min(kGroup, d.ncta - g0);
-  if (tid == 0) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) d.partials[(size_t)cta * kNQ + q] = sout[q];
-    *s_last = (ticket_add(&d.gticket[g]) == (unsigned int)(gn - 1));
-  }
-  __syncthreads();
-  if (!*s_last) return;
-
-  // ---- last block of group g: fold the group's rows ------------------------
-  fold_rows<NQ>(d.partials + (size_t)g0 * kNQ, gn, sout);
-  if (tid == 0) {
-    d.gticket[g] = 0u;  // every block of the group has counted
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) d.gpartials[(size_t)g * kNQ + q] = sout[q];
-    *s_last = (ticket_add(d.ticket) == (unsigned int)(d.ngroups - 1));
-  }
-  __syncthreads();
-  if (!*s_last) return;
-
-  // ---- last group: fold the group rows, then the background update ---------
-  fold_rows<NQ>(d.gpartials, d.ngroups, sout);
-  if (tid != 0) return;
-
-  Background* bgp = d.bg;
-  const Background bg = *bgp;
-  Background nb = bg;
   const double Sd = (double)d.S;
-  double sum_pi2 = 0.0, sum_phiD = 0.0, sum_V = 0.0;
-  double fpi2[NF], fphiD[NF], fdphi[NF], fdphi2[NF];
+  sum_pi2 = 0.0;
+  sum_phiD = 0.0;
   if constexpr (PREC == PREC_FP64) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -427,7 +417,8 @@ __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int 
       fdphi[f] = (mode == MODE_FLUSH) ? sout[SL::DPHI + f] : 0.0;
       fdphi2[f] = (mode == MODE_FLUSH) ? sout[SL::DPHI2 + f] : 0.0;
     }
-    sum_V = sout[SL::V];
+    // the chaotic model's FP64 site accumulates 2V (see Ctx::site)
+    sum_V = (MODEL == M_CHAOTIC2) ? 0.5 * sout[SL::V] : sout[SL::V];
   } else {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -442,13 +433,38 @@ __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int 
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) { sum_pi2 += fpi2[f]; sum_phiD += fphiD[f]; }
+}
+
+// Phi_H3(h): p_a += h a^3 [sum phi D/(a^2 dx^2) - 4 sum V]   (Eq. split-Phi)
+__device__ __forceinline__ double pa_kick(const Coef& k, const SimDesc& d, double sum_phiD,
+                                          double sum_V) {
+  const double a = k.a;
+  return k.pa + k.h * (a * sum_phiD * d.dx2inv - 4.0 * (a * a * a) * sum_V);
+}
+
+// ---------------------------------------------------------------------------
+// Background update after a stage, from the stage's lattice sums `sout`
+// (NQ doubles, slot layout Slots<NF, PREC>): the p_a kick of Phi_H3 (Eq.
+// split-Phi) and the stage/step counters for a sweep; the H = 0 root (Eq. H2),
+// the synchronised sums and the field statistics for a flush.  Shared by the
+// per-launch kernels (last block) and the persistent kernel.
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC, typename C>
+__device__ __forceinline__ void post_stage(const C& cx, const SimDesc& d, int mode,
+                                           const double* sout, const Background& bg,
+                                           Background& nb) {
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  nb = bg;
+  double sum_pi2, sum_phiD, sum_V;
+  double fpi2[NF], fphiD[NF], fdphi[NF], fdphi2[NF];
+  stage_sums<MODEL, PREC>(cx, d, mode, sout, fpi2, fphiD, fdphi, fdphi2, sum_pi2, sum_phiD, sum_V);
 
   const Coef& k = cx.k;
   double a = k.a, pa = k.pa;
   bool ok = is_fin(sum_pi2) && is_fin(sum_phiD) && is_fin(sum_V);
   if (mode == MODE_SWEEP) {
-    // Phi_H3(h): p_a += h a^3 [sum phi D/(a^2 dx^2) - 4 sum V]
-    pa = pa + k.h * (a * sum_phiD * d.dx2inv - 4.0 * (a * a * a) * sum_V);
+    pa = pa_kick(k, d, sum_phiD, sum_V);
     nb.eta = bg.eta + k.h;
     nb.h_prev = k.h;
     nb.stage = bg.stage + 1;
@@ -504,6 +520,94 @@ __device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int 
     nb.error = 1;
     nb.mode = MODE_IDLE;
   }
+}
+
+// After a SWEEP stage: the Background fields that Ctx::init of the next stage
+// reads (h_prev, stage, a, p_a, sum pi^2, split background and re-centring
+// shifts, FP64 variance shift), computed with exactly the expressions of
+// post_stage, so that a caller can derive the next stage's coefficients
+// without waiting for the rest of the bookkeeping.
+template <int MODEL, int PREC, typename C>
+__device__ __forceinline__ void next_init_fields(const C& cx, const SimDesc& d, const double* sout,
+                                                 const Background& bg, Background& nb) {
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  double sum_pi2, sum_phiD, sum_V;
+  double fpi2[NF], fphiD[NF], fdphi[NF], fdphi2[NF];
+  stage_sums<MODEL, PREC>(cx, d, MODE_SWEEP, sout, fpi2, fphiD, fdphi, fdphi2, sum_pi2, sum_phiD,
+                          sum_V);
+  nb.h_prev = cx.k.h;
+  nb.stage = bg.stage + 1;
+  if (nb.stage >= d.nstages) nb.stage = 0;
+  nb.a = cx.k.a;
+  nb.pa = pa_kick(cx.k, d, sum_phiD, sum_V);
+  nb.sum_pi2 = sum_pi2;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    nb.shift[f] = bg.shift[f];
+    if constexpr (PREC == PREC_SPLIT) {
+      nb.phi0[f] = cx.phi0s[f];
+      nb.mu_phi[f] = fdphi[f] * d.invS;
+      nb.pi0[f] = cx.pi0s[f];
+      nb.mu_pi[f] = sout[SL::DPI + f] * d.invS;
+    }
+  }
+}
+
+// Ticket increment with acquire-release semantics at GPU scope: it publishes
+// the caller's earlier stores (the row it wrote) and, for the block that takes
+// the last ticket, makes every other block's row visible.
+__device__ __forceinline__ unsigned int ticket_add(unsigned int* p) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
+// ---------------------------------------------------------------------------
+// Block finish: partials, tickets, and (last block) the background update.
+// sout holds this block's NQ sums on entry.  Two levels, so that almost all
+// of the fold overlaps the sweep: the last block of each group of kGroup
+// consecutive blocks folds the group's rows into one group row; the last group
+// to finish folds the group rows and advances the background.  Thread 0 writes
+// each row and takes the ticket; the block barrier after it orders the other
+// threads' reads of the rows.
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC, typename C>
+__device__ __forceinline__ void finish_block(const C& cx, const SimDesc& d, int mode, int cta,
+                                             double* sout, int* s_last) {
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  const int tid = threadIdx.x;
+  const int g = cta / kGroup;
+  const int g0 = g * kGroup;
+  const int gn = min(kGroup, d.ncta - g0);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) d.partials[(size_t)cta * kNQ + q] = sout[q];
+    *s_last = (ticket_add(&d.gticket[g]) == (unsigned int)(gn - 1));
+  }
+  __syncthreads();
+  if (!*s_last) return;
+
+  // ---- last block of group g: fold the group's rows ------------------------
+  fold_rows<NQ>(d.partials + (size_t)g0 * kNQ, gn, sout);
+  if (tid == 0) {
+    d.gticket[g] = 0u;  // every block of the group has counted
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) d.gpartials[(size_t)g * kNQ + q] = sout[q];
+    *s_last = (ticket_add(d.ticket) == (unsigned int)(d.ngroups - 1));
+  }
+  __syncthreads();
+  if (!*s_last) return;
+
+  // ---- last group: fold the group rows, then the background update ---------
+  fold_rows<NQ>(d.gpartials, d.ngroups, sout);
+  if (tid != 0) return;
+
+  Background* bgp = d.bg;
+  Background nb;
+  post_stage<MODEL, PREC>(cx, d, mode, sout, *bgp, nb);
   *bgp = nb;  // published to the next launch by the kernel boundary
   *d.ticket = 0u;
 }
@@ -548,12 +652,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 // Bounded wait: gives up after ~2^31 clocks (about a second) and reports it.
+// (try_wait itself suspends the thread for a while; the clock is read only
+// every 32 polls so that a waiting warp issues few instructions.)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
-  return true;
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 31u) == 0u && clock64() - t0 > (1ll << 31)) return false;
+  }
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
