@@ -48,13 +48,26 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-# FP64 floating-point operations per site and stage sweep (FMA = 2), counted
-# from the sweep kernel's arithmetic with the 7-point stencil:
-#   drift 2/field, Laplacian 7/field (4 adds in-plane, 1 FMA, 2 adds across z),
-#   kick 4/field, sums pi^2 and phi D 4/field + 1 for V, plus the potential:
-#   chaotic2 9, oscillon 11, qball 12 (+ one float64 log, not counted), free 3.
+# Algorithmic float64 operations per site (FMA = 2) of the method with the
+# 7-point stencil, counted from the arithmetic each site needs (not from the
+# instructions the kernel issues):
+#   stage sweep: drift 2/field, Laplacian 7/field (6 adds + the centre FMA),
+#     kick 4/field, sums pi^2 and phi D 4/field, sum V 1, plus the potential and
+#     its gradient (chaotic2 9, oscillon 11, qball 12 + one log, free 3);
+#   flush: drift 2/field, Laplacian 7/field, sums pi^2, phi D 4/field,
+#     sum (phi - K) 1/field, sum (phi - K)^2 2/field, sum V 1, plus V alone
+#     (chaotic2 5, oscillon 6, qball 6 + one log, free 2).
 FP64_FLOPS_PER_SITE = {"chaotic2": 44.0, "oscillon": 29.0, "qball": 47.0, "free": 21.0}
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (recipe nominal); measured 1.19 with a DFMA loop
+FP64_FLUSH_FLOPS_PER_SITE = {"chaotic2": 38.0, "oscillon": 23.0, "qball": 39.0, "free": 19.0}
+# GB300 float64 peak: 2 DFMA lanes per SM per clock (ncu: 304 predicated-on
+# DFMA thread instructions per cycle for the 152 SMs) x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# persistent kernel, from one ncu capture of this workload (profiles/
+# evolve_persist_preheat128_ncu.md); None where no capture of the current
+# kernel exists.
+NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 244.513280e6 + 203.176448e6,
+                          ("preheat128", "split_fp32"): 33.670400e6 + 35.013120e6}
 
 
 class ClockSampler:
@@ -354,36 +367,42 @@ def main():
                                   "launches": r["launches"], "status": r["status"]}), flush=True)
         return 0
 
-    def summarize(prec, word, bytes_flush_per_site):
+    def summarize(prec, word):
         r = res[prec]
         s = r["stages"]
         total_s = tot[prec] / 1e3
         rate = ws * S * s * args.steps / total_s
-        # algorithmic bytes: read + write phi and pi per sweep; the flush reads both, writes phi
-        sweep_bytes = 4 * nf * word * S
-        flush_bytes = bytes_flush_per_site * nf * word * S
-        per_rank_bytes = args.steps * (s * sweep_bytes + flush_bytes)
-        launches = r["launches"]
-        sweeps = args.steps * (s + 1)
-        avg_launch_s = total_s / sweeps
-        gbs = per_rank_bytes / total_s / 1e9
-        return rate, gbs, avg_launch_s, launches, sweep_bytes
+        # algorithmic bytes per launch (one launch = one time step: s sweeps
+        # that read and write phi and pi, then the flush that reads both and
+        # writes phi)
+        launch_bytes = (s * 4 + 3) * nf * word * S
+        gbs = launch_bytes * args.steps / total_s / 1e9
+        return rate, gbs, r["launches"], launch_bytes
 
-    r64, gbs64, t64, l64, b64 = summarize("fp64", 8, 3)
-    r32, gbs32, t32, l32, b32 = summarize("split_fp32", 4, 3)
-    flops_site = FP64_FLOPS_PER_SITE.get(w["model"], 40.0)
+    r64, gbs64, l64, b64 = summarize("fp64", 8)
+    r32, gbs32, l32, b32 = summarize("split_fp32", 4)
     s = res["fp64"]["stages"]
-    fp64_tflops = S * s * args.steps * flops_site / (tot["fp64"] / 1e3) / 1e12
+    launch_flops = S * (s * FP64_FLOPS_PER_SITE.get(w["model"], 40.0)
+                        + FP64_FLUSH_FLOPS_PER_SITE.get(w["model"], 35.0))
+    fp64_tflops = launch_flops * args.steps / (tot["fp64"] / 1e3) / 1e12
+    kname = {"chaotic2": "chaotic2", "oscillon": "oscillon", "qball": "qball", "free": "free"}[w["model"]]
     roof64 = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS,
-              "unit": "TFLOP/s", "frac": fp64_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-              "kernel": "sweep_tma<chaotic2,7pt,fp64>",
-              "peak_kind": "recipe nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)",
-              "hbm_frac": gbs64 / hbm, "achieved_gbs": gbs64,
-              "flops_per_site_stage": flops_site}
+              "unit": "TFLOP/s", "frac": fp64_tflops / FP64_PEAK_TFLOPS,
+              "traffic": NCU_TRAFFIC_PER_LAUNCH.get((args.workload, "fp64")),
+              "kernel": f"evolve_persist<{kname},7pt,FP64> (one launch per time step)",
+              "peak_kind": "float64 pipe: 2 DFMA/SM/clk x 152 SMs x 2.07 GHz (GB300 FP64 is "
+                           "1/64 of FP32; float64 arithmetic binds this form, not HBM)",
+              "flops_per_launch": launch_flops, "algorithmic_bytes_per_launch": b64,
+              "achieved_gbs": gbs64, "hbm_frac": gbs64 / hbm}
     roof32 = {"bound": "hbm", "achieved": gbs32, "peak": hbm, "unit": "GB/s",
-              "frac": gbs32 / hbm, "traffic": None, "kernel": "sweep_tma<chaotic2,7pt,split>",
-              "peak_kind": f"{peak_kind} (copy test)", "note": "state fits in L2 (flushed "
-              "between steps, not between the sweeps of a step)"}
+              "frac": gbs32 / hbm,
+              "traffic": NCU_TRAFFIC_PER_LAUNCH.get((args.workload, "split_fp32")),
+              "kernel": f"evolve_persist<{kname},7pt,split>",
+              "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+              "algorithmic_bytes_per_launch": b32,
+              "note": ("state fits in L2: the first stage of a step reads HBM (L2 flushed "
+                       "between steps), later stages of the step hit L2")
+              if S * nf * 4 * 4 < 120e6 else "state larger than L2"}
 
     # e2e through the public API with host buffers (FP64 form)
     e2e = None
