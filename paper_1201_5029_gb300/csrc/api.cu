@@ -99,10 +99,13 @@ Layout sim_layout(const pycool_config& c) {
 
 // Persistent geometry.  Tiles are 32 vx x 16 sites (vx sites per lane along
 // x, vx * N_f * word <= 16 bytes); the z-axis of every tile is cut into R
-// ranges (units = tiles x R, range-major).  R minimises the planes on the
-// busiest block, counting each unit's two z-halo planes at a fraction h of a
-// plane (FP64: only their drift is recomputed; split: their loads cost about
-// as much as the compute).
+// ranges (units = tiles x R, range-major, block b owns units b, b + G, ...).
+// For each R the planes of every block are counted exactly (range lengths
+// differ by one; each unit's two z-halo planes count as a fraction h of a
+// plane: FP64 recomputes only their drift, the split form's cost is mostly
+// their loads).  R minimises the busiest block's planes; a cut that leaves
+// blocks with fewer units than others idles those SMs for part of every
+// stage, so it must be 5 % better to win; ties go to fewer planes in total.
 PGeo choose_pgeo(int n, int word, int nf, int prec, int sms) {
   PGeo g;
   std::memset(&g, 0, sizeof(g));
@@ -115,16 +118,25 @@ PGeo choose_pgeo(int n, int word, int nf, int prec, int sms) {
   g.ntiles = g.tiles_x * (n / 16);
   const double h = prec == PREC_FP64 ? 0.1 : 0.5;
   const int cap = std::min(sms, kMaxPBlocks);
-  double best = 1e300;
+  double best = 1e300, best_tot = 1e300;
   for (int R = 1; R <= n; ++R) {
     const long long U = (long long)g.ntiles * R;
     const long long G = std::min<long long>(U, cap);
-    const long long per = (U + G - 1) / G;
-    if (per > kMaxPUnits) continue;
-    const int zr = (n + R - 1) / R;
-    const double cost = (double)per * (zr + 2.0 * h);
-    if (cost < best - 1e-9) {
-      best = cost;
+    if ((U + G - 1) / G > kMaxPUnits) continue;
+    double mx = 0.0, tot = 0.0;
+    for (long long b = 0; b < G; ++b) {
+      double planes = 0.0;
+      for (long long u = b; u < U; u += G) {
+        const long long r = u / g.ntiles;
+        planes += (double)((r + 1) * n / R - r * n / R) + 2.0 * h;
+      }
+      mx = std::max(mx, planes);
+      tot += planes;
+    }
+    const double score = mx * ((U % G == 0) ? 1.0 : 1.05);
+    if (score < best - 1e-9 || (score < best + 1e-9 && tot < best_tot)) {
+      best = score;
+      best_tot = tot;
       g.nranges = R;
       g.nunits = (int)U;
       g.G = (int)G;
