@@ -131,7 +131,7 @@ inline Geometry choose_geometry(int n, int word, int nf) {
 // Persistent evolve kernel (persist.cuh): one cooperative launch per evolve()
 // call, one 512-thread block per SM, tiles of 32 vx x 16 sites.
 // ---------------------------------------------------------------------------
-constexpr int kMaxPBlocks = 1024;          // partial-sum rows reserved in the workspace
+constexpr int kMaxPBlocks = 208;           // blocks (SMs) of the persistent kernel at most
 constexpr int kMaxPUnits = 64;             // work units per block
 
 // Geometry, chosen on the host (a function of n, word, N_f and the SM count).

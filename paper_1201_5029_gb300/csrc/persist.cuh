@@ -639,6 +639,15 @@ __device__ __forceinline__ void prefetch_plane(const PParams& p, const PShared& 
   sm.issued[gp % NSLOT] = gp + 1;
 }
 
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing on `bar` (transaction count).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
@@ -660,9 +669,11 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
   static_assert(NQ <= kPWarps, "one warp per reduced quantity");
   static_assert(NQ + LEAD <= kPWarps, "stage-start prefetch: one warp per plane beside the folds");
+  static_assert((size_t)kMaxPBlocks * kNQ * 8 <= (size_t)NQ * kPThreads * 8,
+                "the rows of every block fit the reduction scratch");
 
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT];
+  __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT], foldbar;
   // background and stage coefficients, double-buffered: at a stage boundary
   // one thread derives the next coefficients while another does the rest of
   // the background bookkeeping
@@ -702,6 +713,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kPWarps);
     }
+    mbar_init(&foldbar, 1);
     fence_mbar_init();
     s_bad = 0;
   }
@@ -787,8 +799,10 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
         double v = x[0];
 #pragma unroll
         for (int h = 16; h >= 1; h >>= 1) v += __shfl_down_sync(0xffffffffu, v, h);
-        if (lane == 0)
+        if (lane == 0) {
           reinterpret_cast<double*>(p.rows)[((size_t)(k & 1) * G + blockIdx.x) * kNQ + warp] = v;
+          fence_proxy_async_global();   // the rows are read back by bulk copies
+        }
       }
     } else {
       if (warp < NQ) {
@@ -804,11 +818,15 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
           const float bl = __shfl_down_sync(0xffffffffu, lo, h);
           pair_add(hi, lo, bh, bl);
         }
-        if (lane == 0)
+        if (lane == 0) {
           reinterpret_cast<float2*>(p.rows)[((size_t)(k & 1) * G + blockIdx.x) * kNQ + warp] =
               make_float2(hi, lo);
+          fence_proxy_async_global();   // the rows are read back by bulk copies
+        }
       }
     }
+    // the reduction scratch is overwritten by the rows' bulk copy below
+    fence_proxy_async();
     if (!grid_barrier(p.bar, p.bar_base + (unsigned long long)(k + 1) * G)) s_bad = 1;
     __syncthreads();
     // @released
@@ -824,39 +842,35 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     //   warp 14 also takes 1/a for the next stage's coefficients ----
     const int ib_next = ib ^ (mode == MODE_SWEEP ? 3 : 1);
     const bool pre = k < K;
-    constexpr int kPreThreads = (NQ + LEAD) * 32;
+    constexpr int kPreThreads = (1 + LEAD) * 32;
+    using FT = typename std::conditional<PREC == PREC_FP64, double, float2>::type;
+    // every block's row arrives by one bulk copy into the (now free) reduction
+    // scratch: one request stream per block instead of 8-byte loads of the
+    // same lines by every block
+    FT* srows = reinterpret_cast<FT*>(PREC == PREC_FP64 ? (void*)sm.red : (void*)sm.kahan);
+    if (warp == 0) {
+      if (lane == 0) {
+        const uint32_t bytes = (uint32_t)(G * kNQ * sizeof(FT));
+        mbar_expect_tx(&foldbar, bytes);
+        bulk_load(srows, reinterpret_cast<const FT*>(p.rows) + (size_t)(k & 1) * G * kNQ, bytes,
+                  &foldbar);
+      }
+      __syncwarp();
+      if (pre) named_arrive(1, kPreThreads);   // the next stage's copies queue behind it
+    }
     if (warp < NQ) {
-      using FT = typename std::conditional<PREC == PREC_FP64, double, float2>::type;
-      const FT* rows = reinterpret_cast<const FT*>(p.rows) + (size_t)(k & 1) * G * kNQ;
-      FT x[8];
+      if (!mbar_wait(&foldbar, (uint32_t)(k & 1))) atomicOr(&s_bad, 1);
       if constexpr (PREC == PREC_FP64) {
         double v = 0.0;
-        for (int r0 = 0; r0 < G; r0 += 32 * 8) {   // 8 loads in flight, added in row order
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int r = r0 + lane + 32 * j;
-            if (r < G) x[j] = __ldcg(&rows[(size_t)r * kNQ + warp]);
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (r0 + lane + 32 * j < G) v += x[j];
-          if (r0 == 0 && pre) named_arrive(1, kPreThreads);   // our loads have landed
-        }
+        for (int r = lane; r < G; r += 32) v += srows[(size_t)r * kNQ + warp];   // row order
 #pragma unroll
         for (int h = 16; h >= 1; h >>= 1) v += __shfl_down_sync(0xffffffffu, v, h);
         if (lane == 0) sums[warp] = v;
       } else {
         float hi = 0.f, lo = 0.f;
-        for (int r0 = 0; r0 < G; r0 += 32 * 8) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int r = r0 + lane + 32 * j;
-            if (r < G) x[j] = __ldcg(&rows[(size_t)r * kNQ + warp]);
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (r0 + lane + 32 * j < G) pair_add(hi, lo, x[j].x, x[j].y);
-          if (r0 == 0 && pre) named_arrive(1, kPreThreads);   // our loads have landed
+        for (int r = lane; r < G; r += 32) {
+          const float2 x = srows[(size_t)r * kNQ + warp];
+          pair_add(hi, lo, x.x, x.y);
         }
 #pragma unroll
         for (int h = 16; h >= 1; h >>= 1) {
@@ -905,6 +919,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     if (fault) atomicOr(p.fault, 1);
     for (int s = 0; s < NSLOT; ++s)
       if (s_issued[s]) mbar_wait(&full[s], ((s_issued[s] - 1u) / NSLOT) & 1u);
+    if (fault) mbar_wait(&foldbar, 0u), mbar_wait(&foldbar, 1u);   // a pending rows copy, if any
   }
   if (fault) return;   // the state is not trusted any more (the host poisons the simulation)
   if (blockIdx.x == 0 && tid < (int)(sizeof(Background) / 8))
