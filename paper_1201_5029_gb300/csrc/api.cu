@@ -85,6 +85,7 @@ Layout layout_for(const pycool_config& c) {
   L.state_bytes = L.off_fields + 4 * L.field_bytes;
   workspace_layout(L.geo.ncta, L);
   L.off_prows = 0;
+  L.off_punits = 0;
   return L;
 }
 
@@ -92,21 +93,28 @@ Layout sim_layout(const pycool_config& c) {
   Layout L = layout_for(c);
   if (L.geo.tma) {
     L.off_prows = align256(L.ws_bytes);
-    L.ws_bytes = L.off_prows + align256((size_t)2 * kMaxPBlocks * kNQ * sizeof(double));
+    L.off_punits = L.off_prows + align256((size_t)2 * kMaxPBlocks * kNQ * sizeof(double));
+    L.ws_bytes = L.off_punits + align256((size_t)kMaxPBlocks * kMaxPUnits * sizeof(int4)) +
+                 align256((size_t)(kMaxPBlocks + 1) * sizeof(int));
   }
   return L;
 }
 
-// Persistent geometry.  Tiles are 32 vx x 16 sites (vx sites per lane along
-// x, vx * N_f * word <= 16 bytes); the z-axis of every tile is cut into R
-// ranges (units = tiles x R, range-major, block b owns units b, b + G, ...).
-// For each R the planes of every block are counted exactly (range lengths
-// differ by one; each unit's two z-halo planes count as a fraction h of a
-// plane: FP64 recomputes only their drift, the split form's cost is mostly
-// their loads).  R minimises the busiest block's planes; a cut that leaves
-// blocks with fewer units than others idles those SMs for part of every
-// stage, so it must be 5 % better to win; ties go to fewer planes in total.
-PGeo choose_pgeo(int n, int word, int nf, int prec, int sms) {
+// Persistent geometry and work assignment.  Tiles are 32 vx x 16 sites (vx
+// sites per lane along x, vx * N_f * word <= 16 bytes).  Each tile's z-axis is
+// cut into equal ranges: rc of them for tiles clear of the periodic y boundary,
+// rw for the tiles whose halo rows cross it (their TMA copies take one box per
+// field instead of one for all fields).  A unit (tile, z-range) costs its
+// planes, each of its two z-halo planes counted as a fraction h of a plane
+// (FP64: only their drift is recomputed; split: their loads cost about as
+// much as the compute), times a penalty for the wrap tiles (split: 1.2,
+// measured; FP64, bound by float64 arithmetic: 1).  The units are dealt in
+// z-major order (blocks that run together work on neighbouring tiles at the
+// same z, so halo rows and columns hit L2), each to the least loaded block; a
+// block processes its units in the order dealt.  (rc, rw) minimises the
+// busiest block's cost, then the total.
+PGeo plan_units(int n, int word, int nf, int prec, int sms, std::vector<int4>* units,
+                std::vector<int>* off) {
   PGeo g;
   std::memset(&g, 0, sizeof(g));
   g.n = n;
@@ -115,31 +123,96 @@ PGeo choose_pgeo(int n, int word, int nf, int prec, int sms) {
     if (v * nf * word <= 16 && n % (32 * v) == 0) { g.vx = v; break; }
   g.tx = 32 * g.vx;
   g.tiles_x = n / g.tx;
-  g.ntiles = g.tiles_x * (n / 16);
+  const int tiles_y = n / 16;
+  g.ntiles = g.tiles_x * tiles_y;
   const double h = prec == PREC_FP64 ? 0.1 : 0.5;
+  const double pen = prec == PREC_FP64 ? 1.0 : 1.2;
   const int cap = std::min(sms, kMaxPBlocks);
-  double best = 1e300, best_tot = 1e300;
-  for (int R = 1; R <= n; ++R) {
-    const long long U = (long long)g.ntiles * R;
-    const long long G = std::min<long long>(U, cap);
-    if ((U + G - 1) / G > kMaxPUnits) continue;
-    double mx = 0.0, tot = 0.0;
-    for (long long b = 0; b < G; ++b) {
-      double planes = 0.0;
-      for (long long u = b; u < U; u += G) {
-        const long long r = u / g.ntiles;
-        planes += (double)((r + 1) * n / R - r * n / R) + 2.0 * h;
+  auto is_wrap = [&](int t) {
+    const int ty = t / g.tiles_x;
+    return ty == 0 || ty == tiles_y - 1;
+  };
+  struct U { int z0, z1, t; double c; };
+  auto deal = [&](int rc, int rw, std::vector<U>& list, std::vector<int>& owner, int& G,
+                  double& mx, double& tot, int& maxcount) {
+    list.clear();
+    for (int t = 0; t < g.ntiles; ++t) {
+      const bool w = is_wrap(t);
+      const int R = w ? rw : rc;
+      for (int r = 0; r < R; ++r) {
+        U u;
+        u.z0 = (int)((long long)r * n / R);
+        u.z1 = (int)((long long)(r + 1) * n / R);
+        u.t = t;
+        u.c = ((double)(u.z1 - u.z0) + 2.0 * h) * (w ? pen : 1.0);
+        list.push_back(u);
       }
-      mx = std::max(mx, planes);
-      tot += planes;
     }
-    const double score = mx * ((U % G == 0) ? 1.0 : 1.05);
-    if (score < best - 1e-9 || (score < best + 1e-9 && tot < best_tot)) {
-      best = score;
-      best_tot = tot;
-      g.nranges = R;
-      g.nunits = (int)U;
-      g.G = (int)G;
+    std::stable_sort(list.begin(), list.end(), [](const U& a, const U& b) {
+      return a.z0 != b.z0 ? a.z0 < b.z0 : a.t < b.t;
+    });
+    G = (int)std::min<size_t>(list.size(), (size_t)cap);
+    std::vector<double> load(G, 0.0);
+    std::vector<int> count(G, 0);
+    owner.assign(list.size(), 0);
+    // least loaded block, ties to the lower index (deterministic)
+    std::vector<std::pair<double, int>> heap;
+    for (int b = 0; b < G; ++b) heap.push_back({0.0, b});
+    auto cmp = [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+      return a.first != b.first ? a.first > b.first : a.second > b.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (size_t i = 0; i < list.size(); ++i) {
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto& top = heap.back();
+      owner[i] = top.second;
+      top.first += list[i].c;
+      load[top.second] = top.first;
+      count[top.second] += 1;
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    mx = *std::max_element(load.begin(), load.end());
+    tot = 0.0;
+    for (double v : load) tot += v;
+    maxcount = *std::max_element(count.begin(), count.end());
+  };
+  double best = 1e300, best_tot = 1e300;
+  std::vector<U> list;
+  std::vector<int> owner;
+  for (int rc = 1; rc <= std::min(n, 64); ++rc) {
+    const int rws[4] = {rc, (rc * 11 + 9) / 10, (rc * 12 + 9) / 10, (rc * 13 + 9) / 10};
+    for (int k = 0; k < 4; ++k) {
+      const int rw = std::min(rws[k], n);
+      if (k > 0 && rw == rws[k - 1]) continue;
+      if (pen == 1.0 && rw != rc) continue;
+      int G, maxcount;
+      double mx, tot;
+      deal(rc, rw, list, owner, G, mx, tot, maxcount);
+      if (maxcount > kMaxPUnits) continue;
+      if (mx < best - 1e-9 || (mx < best + 1e-9 && tot < best_tot - 1e-9)) {
+        best = mx;
+        best_tot = tot;
+        g.rc = rc;
+        g.rw = rw;
+      }
+    }
+  }
+  int G, maxcount;
+  double mx, tot;
+  deal(g.rc, g.rw, list, owner, G, mx, tot, maxcount);
+  g.G = G;
+  g.nunits = (int)list.size();
+  if (units && off) {
+    off->assign(G + 1, 0);
+    for (size_t i = 0; i < list.size(); ++i) (*off)[owner[i] + 1] += 1;
+    for (int b = 0; b < G; ++b) (*off)[b + 1] += (*off)[b];
+    units->assign(list.size(), int4{0, 0, 0, 0});
+    std::vector<int> fill(off->begin(), off->end() - 1);
+    for (size_t i = 0; i < list.size(); ++i) {   // per block, in the order dealt
+      const U& u = list[i];
+      const int t = u.t;
+      (*units)[fill[owner[i]]++] =
+          int4{(t % g.tiles_x) * g.tx, (t / g.tiles_x) * 16, u.z0, u.z1 - u.z0 + 2};
     }
   }
   return g;
@@ -458,10 +531,21 @@ static pycool_status setup_persist(pycool_sim* sim) {
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
   const int word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
-  PGeo g = choose_pgeo(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms);
+  std::vector<int4> units;
+  std::vector<int> uoff;
+  PGeo g = plan_units(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms, &units, &uoff);
   PParams& p = sim->pp;
   std::memset(&p, 0, sizeof(p));
   p.g = g;
+  int4* d_units = (int4*)(sim->ws + sim->L.off_punits);
+  int* d_uoff = (int*)(sim->ws + sim->L.off_punits +
+                       align256((size_t)kMaxPBlocks * kMaxPUnits * sizeof(int4)));
+  if (units.size() > (size_t)kMaxPBlocks * kMaxPUnits || uoff.size() > (size_t)kMaxPBlocks + 1)
+    return PYCOOL_E_INVALID;
+  CK(cudaMemcpy(d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_uoff, uoff.data(), uoff.size() * sizeof(int), cudaMemcpyHostToDevice));
+  p.units = d_units;
+  p.uoff = d_uoff;
   CK(encode_persist_maps(sim->hdesc, g, p));
   p.d = sim->d_desc;
   p.bg = sim->d_bg;

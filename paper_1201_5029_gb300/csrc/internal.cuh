@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace pycool {
 
@@ -134,11 +135,13 @@ inline Geometry choose_geometry(int n, int word, int nf) {
 constexpr int kMaxPBlocks = 208;           // blocks (SMs) of the persistent kernel at most
 constexpr int kMaxPUnits = 64;             // work units per block
 
-// Geometry, chosen on the host (a function of n, word, N_f and the SM count).
-//   units = tiles x z-ranges, ordered range-major; block b owns units
-//   b, b + G, b + 2G, ...
+// Geometry, chosen on the host (a function of n, word, N_f and the SM count):
+// tiles of tx x 16 sites, each tile's z-axis cut into ranges (rc ranges for
+// tiles clear of the periodic y boundary, rw for the tiles whose halo rows
+// cross it); the units (tile, z-range) are dealt to the G blocks by the host
+// (plan_units) and read by each block from a table.
 struct PGeo {
-  int n, vx, tx, tiles_x, ntiles, nranges, nunits, G;
+  int n, vx, tx, tiles_x, ntiles, rc, rw, nunits, G;
 };
 
 // Kernel parameters, passed as one __grid_constant__ struct (the tensor maps
@@ -160,12 +163,17 @@ struct PParams {
   unsigned long long* bar;       // grid barrier: arrivals so far (monotonic)
   unsigned long long bar_base;   // arrivals before this launch
   void* rows;              // [2][G][kNQ] doubles (FP64) or float pairs (split)
+  const int4* units;       // every block's units in processing order: (x0, y0, z0, planes)
+  const int* uoff;         // block b's units are units[uoff[b] .. uoff[b + 1])
   int32_t* fault;
   PGeo g;
   long long nsweeps;       // stage sweeps of this launch (then one flush)
 };
 
-PGeo choose_pgeo(int n, int word, int nf, int prec, int sms);
+// The persistent geometry and its unit table (units grouped by block; off has
+// G + 1 entries).
+PGeo plan_units(int n, int word, int nf, int prec, int sms, std::vector<int4>* units,
+                std::vector<int>* off);
 
 // Launchers (one translation unit per precision).
 cudaError_t launch_sweep_fp64(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,

@@ -705,8 +705,8 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   sm.empty = empty;
   sm.units = s_units;
   sm.issued = s_issued;
-  sm.nunits = ((int)blockIdx.x < p.g.nunits) ? (p.g.nunits - (int)blockIdx.x + G - 1) / G : 0;
-  if (sm.nunits > kMaxPUnits) sm.nunits = kMaxPUnits;   // the host never asks for more
+  const int ubeg = __ldg(&p.uoff[blockIdx.x]);
+  sm.nunits = min(__ldg(&p.uoff[blockIdx.x + 1]) - ubeg, kMaxPUnits);   // host: <= kMaxPUnits
 
   if (tid == 0) {
     for (int s = 0; s < NSLOT; ++s) {
@@ -722,13 +722,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     const CUtensorMap* m = &p.tm[tid];
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
   }
-  if (tid < sm.nunits) {   // this block's units: tiles x z-ranges, range-major
-    const int id = (int)blockIdx.x + tid * G;
-    const int t = id % p.g.ntiles, r = id / p.g.ntiles;
-    const int z0 = (int)(((long long)r * p.g.n) / p.g.nranges);
-    const int z1 = (int)(((long long)(r + 1) * p.g.n) / p.g.nranges);
-    s_units[tid] = make_int4((t % p.g.tiles_x) * p.g.tx, (t / p.g.tiles_x) * kPTY, z0, z1 - z0 + 2);
-  }
+  if (tid < sm.nunits) s_units[tid] = p.units[ubeg + tid];   // this block's units, in order
   static_assert(sizeof(Background) % 8 == 0, "background copied as 8-byte words");
   if (tid < (int)(sizeof(Background) / 8))
     reinterpret_cast<unsigned long long*>(&sbv[0])[tid] =

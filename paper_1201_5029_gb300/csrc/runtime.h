@@ -19,6 +19,7 @@ struct Layout {
   size_t off_bg, off_desc, off_fields, state_bytes;
   size_t off_ticket, off_gticket, off_partials, off_gpartials, ws_bytes;
   size_t off_prows;   // single-simulation API: rows of the persistent kernel (0 = none)
+  size_t off_punits;  // single-simulation API: the persistent kernel's unit table
 };
 
 // Workspace layout of a launch of `ncta` blocks (fills the off_* / ws_bytes fields).
