@@ -126,6 +126,27 @@ def _dist():
     return ws, rank, local
 
 
+def slowest_rank_ms(tot, forms, device):
+    """Max over ranks of each form's timed total (ms).
+
+    The replicas run independently; the job ends when the slowest rank ends,
+    so the whole-job time of a form is the maximum of the ranks' totals.
+    Identity when no process group is initialised (one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return {f: float(tot[f]) for f in forms}
+    t = torch.tensor([tot[f] for f in forms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return {f: float(t[i]) for i, f in enumerate(forms)}
+
+
+def whole_job_rate(ws, sites, stages, steps, total_ms):
+    """Site-updates per second of the whole job: every rank updated `sites`
+    sites `stages` times per step for `steps` steps within `total_ms`."""
+    return ws * sites * stages * steps / (total_ms / 1e3)
+
+
 def run_form(P, torch, w, precision, steps, warmup, flush_buf, phi, pi, stream):
     """Time `steps` evolve(1) calls of one form; returns a dict of measurements."""
     cfg = P.config_from_workload(w, precision=precision)
@@ -353,17 +374,14 @@ def main():
     clocks = clk.summary()
 
     # slowest rank decides
-    tot = {k: v["total_ms"] for k, v in res.items()}
-    if ws > 1:
-        t = torch.tensor([tot[f] for f in forms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = {f: float(t[i]) for i, f in enumerate(forms)}
+    tot = slowest_rank_ms({k: v["total_ms"] for k, v in res.items()}, forms, "cuda")
     if forms != ["fp64", "split_fp32"]:
         if rank == 0:  # profiling run: a short line per form, no baselines
             for f in forms:
                 r = res[f]
-                print(json.dumps({"form": f, "value": ws * S * r["stages"] * args.steps /
-                                  (tot[f] / 1e3), "unit": UNIT, "ms_per_step": tot[f] / args.steps,
+                print(json.dumps({"form": f, "value": whole_job_rate(ws, S, r["stages"],
+                                                                      args.steps, tot[f]),
+                                  "unit": UNIT, "ms_per_step": tot[f] / args.steps,
                                   "launches": r["launches"], "status": r["status"]}), flush=True)
         return 0
 
@@ -371,7 +389,7 @@ def main():
         r = res[prec]
         s = r["stages"]
         total_s = tot[prec] / 1e3
-        rate = ws * S * s * args.steps / total_s
+        rate = whole_job_rate(ws, S, s, args.steps, tot[prec])
         # algorithmic bytes per launch (one launch = one time step: s sweeps
         # that read and write phi and pi, then the flush that reads both and
         # writes phi)
