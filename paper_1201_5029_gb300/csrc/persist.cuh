@@ -679,7 +679,11 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   // the background bookkeeping
   __shared__ __align__(16) Background sbv[2];
   __shared__ C sctxv[2];
-  __shared__ double s_ia;
+  // formed during the fold: the sums-to-kick coefficients of this stage and
+  // the sums-independent half of the next stage's scalar half-steps
+  __shared__ SumCoef<NF> s_sc;
+  __shared__ PreCoef s_qn;
+  __shared__ double s_p0[2 * NF];   // split form: the next stage's re-centred background
   // the scalar chain between stages reads the descriptor many times; the
   // ring leaves little L1, so it is kept in shared memory
   __shared__ __align__(64) SimDesc s_desc;
@@ -822,6 +826,19 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     // the reduction scratch is overwritten by the rows' bulk copy below
     fence_proxy_async();
     if (!grid_barrier(p.bar, p.bar_base + (unsigned long long)(k + 1) * G)) s_bad = 1;
+    // while thread 0 waits for the other blocks, warp 14 forms what the scalar
+    // chain needs that does not depend on the sums: this stage's SumCoef and
+    // the next stage's PreCoef (it starts from a = k.a, h_prev = k.h)
+    if (warp == kPWarps - 2 && lane == 0) {
+      s_sc = sum_coef<MODEL, PREC>(sctxv[cb], d);
+      if (k < K) {
+        const int mn = k + 1 < K ? MODE_SWEEP : MODE_FLUSH;
+        const int sn = sbv[cb].stage + 1 < d.nstages ? sbv[cb].stage + 1 : 0;
+        const double hn = (mn == MODE_SWEEP) ? d.w[sn] * d.dt : 0.0;
+        const Coef& kc = sctxv[cb].k;
+        s_qn = prestage_a(kc.a, __drcp_rn(kc.a), kc.h, hn, d, mn);
+      }
+    }
     __syncthreads();
     // @released
     if (s_bad) { fault = true; break; }
@@ -832,8 +849,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     //     critical loads have landed (named barrier 1), so that they are not
     //     queued behind the copies;
     //   warps 15, 14, ... issue the next stage's first planes, one each (its
-    //     buffers are known: a sweep swaps phi and pi, a flush swaps phi);
-    //   warp 14 also takes 1/a for the next stage's coefficients ----
+    //     buffers are known: a sweep swaps phi and pi, a flush swaps phi) ----
     const int ib_next = ib ^ (mode == MODE_SWEEP ? 3 : 1);
     const bool pre = k < K;
     constexpr int kPreThreads = (1 + LEAD) * 32;
@@ -882,21 +898,50 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
         prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib_next, gq, l);
       }
       // @prefetch-issued
-      if (warp == kPWarps - 2 && lane == 0)
-        s_ia = __drcp_rn(sctxv[cb].k.a);   // the next stage's Background has a = k.a
     }
     __syncthreads();
     // @folded
-    // ---- the next stage's coefficients (warp 14) and the bookkeeping of this
-    //      stage (warp 13), in parallel; identical in every block ----
-    if (tid == kPThreads - 64) {
-      if (k < K) {
-        Background nb = sbv[cb];
-        next_init_fields<MODEL, PREC>(sctxv[cb], d, sums, sbv[cb], nb);
-        sctxv[cb ^ 1].init(nb, d, k + 1 < K ? MODE_SWEEP : MODE_FLUSH, s_ia);
+    // ---- in parallel, on warps of different schedulers, identically in
+    //      every block: the next stage's coefficients (warp 14: sums -> p_a
+    //      kick -> scalar half-steps -> split background), the split form's
+    //      re-centring (warp 12, joined to warp 14 by named barrier 2) and the
+    //      bookkeeping of this stage (warp 13) ----
+    // (the current Ctx is read from shared memory here, not from the sweep's
+    // register copy, so that the copy's live range ends with the sweep)
+    const C& cc = sctxv[cb];
+    if (warp == kPWarps - 2) {
+      if (pre) {
+        const int mn = k + 1 < K ? MODE_SWEEP : MODE_FLUSH;
+        C& nx = sctxv[cb ^ 1];
+        if (lane == 0) {
+          nx.set_coef(chain_coef<MODEL, PREC>(cc, s_sc, s_qn, d, sums, mn), d, mn, cc.pk);
+          if constexpr (PREC == PREC_FP64) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) nx.shiftK[f] = (typename C::T)sbv[cb].shift[f];
+          }
+        }
+        if constexpr (PREC == PREC_SPLIT) {
+          __syncwarp();
+          named_sync(2, 64);
+          if (lane == 0) nx.split_tail(d, mn, s_p0);
+        }
+      }
+      // @chain-done
+    } else if (warp == kPWarps - 4) {
+      if constexpr (PREC == PREC_SPLIT) {
+        if (pre) {
+          if (lane == 0) {
+            double mphi[NF], mpi[NF];
+            chain_means<PREC>(cc, d, sums, mphi, mpi);
+            sctxv[cb ^ 1].recenter(mphi, mpi, cc.phi0s, cc.pi0s, s_p0);
+          }
+          __syncwarp();
+          named_arrive(2, 64);
+        }
       }
     } else if (tid == kPThreads - 96) {
-      post_stage<MODEL, PREC>(sctxv[cb], d, mode, sums, sbv[cb], sbv[cb ^ 1]);
+      post_stage<MODEL, PREC>(cc, s_sc, d, mode, sums, sbv[cb], sbv[cb ^ 1]);
+      // @book-done
     }
     __syncthreads();
     // @coefficients

@@ -64,40 +64,75 @@ struct Coef {
   double h;      // this stage's step (0 for a flush)
 };
 
+// The boundary between two stages splits into the part that needs only a,
+// h_prev and h (PreCoef: formed ahead of the lattice sums where the caller
+// can) and the part that needs p_a and sum pi^2 (prestage_p).
+struct PreCoef {
+  double a;      // a before the leading Phi_H1's
+  double ia3;    // 1/a^3
+  double hh;     // h_prev/2
+  double c0;     // h_prev/(2 a^2): the trailing drift of the previous stage
+  double g1;     // -(h_prev [+ h])/2 / (12 V_L m^2): the Phi_H1 flows' da/dp_a
+  double nVLrm;  // -V_L rho_m
+  double hn;     // h/2
+  double hdx;    // h / dx^2
+  double h;      // this stage's step (0 for a flush)
+};
+
+// ia: 1/a (the caller's reciprocal, so that it can be formed early).
+__device__ __forceinline__ PreCoef prestage_a(double a, double ia, double hp, double h,
+                                              const SimDesc& d, int mode) {
+  PreCoef q;
+  const double ia2 = ia * ia;
+  q.a = a;
+  q.ia3 = ia2 * ia;
+  q.hh = 0.5 * hp;
+  q.c0 = q.hh * ia2;
+  q.nVLrm = -(d.VL * d.rho_m0);
+  if (mode == MODE_SWEEP) {
+    q.g1 = -(d.inv6VLm2 * (0.5 * (hp + h)));
+    q.hn = 0.5 * h;
+    q.hdx = h * d.dx2inv;
+    q.h = h;
+  } else {
+    q.g1 = -(d.inv6VLm2 * q.hh);
+    q.hn = 0.0; q.hdx = 0.0; q.h = 0.0;
+  }
+  return q;
+}
+
+// The scalar half-steps of a stage boundary, given p_a and sum pi^2 (pi is
+// unchanged by H1 and H2, so the previous sweep's sum serves both Phi_H2's).
+__device__ __forceinline__ Coef prestage_p(const PreCoef& q, double pa, double s2, int mode) {
+  Coef k;
+  // trailing Phi_H2(h_prev/2) of the previous stage: p_a += [sum pi^2/a^3 - V_L rho_m] h_prev/2
+  pa = fma(fma(s2, q.ia3, q.nVLrm), q.hh, pa);
+  // Phi_H1(h_prev/2) [Phi_H1(h/2)] merged (p_a is constant under H1): a -= p_a dt' / (12 V_L m^2)
+  const double a = fma(pa, q.g1, q.a);
+  k.a = a;
+  if (mode != MODE_SWEEP) {
+    k.c = q.c0; k.kD = 0.0; k.kV = 0.0; k.pa = pa; k.h = 0.0;
+    return k;
+  }
+  // one reciprocal per value of a instead of divisions: an FP64 division costs
+  // ~450 cycles of a single thread on GB300
+  const double ia = __drcp_rn(a), ia2 = ia * ia;
+  // leading Phi_H2(h/2)
+  k.pa = fma(fma(s2, ia2 * ia, q.nVLrm), q.hn, pa);
+  k.c = fma(q.hn, ia2, q.c0);
+  const double a2 = a * a;
+  k.kD = a2 * q.hdx;
+  k.kV = (a2 * a2) * q.h;
+  k.h = q.h;
+  return k;
+}
+
 // ia_a: 1/b.a if the caller already has it (a negative value means "compute it").
 __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, int mode,
                                          double ia_a = -1.0) {
-  Coef k;
-  const double hp = b.h_prev;
   const double h = (mode == MODE_SWEEP) ? d.w[b.stage] * d.dt : 0.0;
-  double a = b.a;
-  double pa = b.pa;
-  const double s2 = b.sum_pi2;
-  const double VLrm = d.VL * d.rho_m0;
-  // one reciprocal per value of a instead of divisions: an FP64 division costs
-  // ~450 cycles of a single thread on GB300, and this runs at every block start
-  double ia = ia_a > 0.0 ? ia_a : __drcp_rn(a), ia2 = ia * ia;
-  // trailing Phi_H2(h_prev/2) of the previous stage: p_a += [sum pi^2/a^3 - V_L rho_m] h_prev/2
-  pa = pa + (s2 * (ia2 * ia) - VLrm) * (0.5 * hp);
-  double c = (0.5 * hp) * ia2;
-  if (mode != MODE_SWEEP) {
-    // trailing Phi_H1(h_prev/2): a -= p_a h_prev / (12 V_L m^2)
-    a = a - pa * d.inv6VLm2 * (0.5 * hp);
-    k.c = c; k.kD = 0.0; k.kV = 0.0; k.a = a; k.pa = pa; k.h = 0.0;
-    return k;
-  }
-  // Phi_H1(h_prev/2) Phi_H1(h/2) merged (p_a is constant under H1)
-  a = a - pa * d.inv6VLm2 * (0.5 * (hp + h));
-  ia = __drcp_rn(a);
-  ia2 = ia * ia;
-  // leading Phi_H2(h/2)
-  pa = pa + (s2 * (ia2 * ia) - VLrm) * (0.5 * h);
-  c = c + (0.5 * h) * ia2;
-  k.c = c;
-  k.kD = a * a * h * d.dx2inv;
-  k.kV = (a * a) * (a * a) * h;
-  k.a = a; k.pa = pa; k.h = h;
-  return k;
+  const double ia = ia_a > 0.0 ? ia_a : __drcp_rn(b.a);
+  return prestage_p(prestage_a(b.a, ia, b.h_prev, h, d, mode), b.pa, b.sum_pi2, mode);
 }
 
 // Explicitly typed fused multiply-add: float arithmetic must stay on the FP32
@@ -212,35 +247,54 @@ struct Ctx {
 
   __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode,
                                        double ia_a = -1.0) {
-    k = prestage(bg, d, mode, ia_a);
-    pk = P::prep(d.params, d.derived);
-    V0 = 0.0;
+    set_coef(prestage(bg, d, mode, ia_a), d, mode, P::prep(d.params, d.derived));
     if constexpr (PREC == PREC_SPLIT) {
-      cdrift = (T)k.c; kD = (T)k.kD; kV = (T)k.kV;
-      double phi0p[NF], pi0p[NF], dV0[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        // re-centring: the float means mu move into the float64 background
-        mu_phi[f] = (float)bg.mu_phi[f];
-        mu_pi[f] = (float)bg.mu_pi[f];
-        phi0p[f] = bg.phi0[f] + (double)mu_phi[f];
-        pi0p[f] = bg.pi0[f] + (double)mu_pi[f];
-        phi0s[f] = fma(k.c, pi0p[f], phi0p[f]);   // background drift
-        shiftK[f] = 0;
-      }
-      sk = P::split_prep(pk, d.params, d.derived, d.fparams, phi0s, dV0, V0);
-#pragma unroll
-      for (int f = 0; f < NF; ++f)  // background kick (D[phi0] = 0)
-        pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], pi0p[f]) : pi0p[f];
+      double p0[2 * NF];
+      recenter(bg.mu_phi, bg.mu_pi, bg.phi0, bg.pi0, p0);
+      split_tail(d, mode, p0);
     } else {
-      cdrift = k.c; kD = k.kD; kV = k.kV;
-      if constexpr (MODEL == M_CHAOTIC2) nkVg = -k.kV * d.params[1];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        mu_phi[f] = 0; mu_pi[f] = 0; phi0s[f] = 0; pi0s[f] = 0;
-        shiftK[f] = (T)bg.shift[f];
-      }
+      for (int f = 0; f < NF; ++f) shiftK[f] = (T)bg.shift[f];
     }
+  }
+
+  // The pieces of init, in the order a stage boundary can form them.
+  //   set_coef: the working-precision coefficients of the scalar half-steps
+  __device__ __forceinline__ void set_coef(const Coef& kk, const SimDesc& d, int mode,
+                                           const typename P::K& pkk) {
+    k = kk;
+    pk = pkk;
+    cdrift = (T)k.c; kD = (T)k.kD; kV = (T)k.kV;
+    if constexpr (PREC == PREC_FP64) {
+      if constexpr (MODEL == M_CHAOTIC2) nkVg = -k.kV * d.params[1];
+      V0 = 0.0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) { mu_phi[f] = 0; mu_pi[f] = 0; phi0s[f] = 0; pi0s[f] = 0; }
+    }
+  }
+  //   recenter (split form): the float means mu of the fluctuations move into
+  //   the float64 background; p0 = re-centred (phi0[0..NF), pi0[0..NF))
+  __device__ __forceinline__ void recenter(const double* mphi, const double* mpi,
+                                           const double* phi0, const double* pi0, double* p0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      mu_phi[f] = (T)mphi[f];
+      mu_pi[f] = (T)mpi[f];
+      p0[f] = phi0[f] + (double)mu_phi[f];
+      p0[NF + f] = pi0[f] + (double)mu_pi[f];
+      shiftK[f] = 0;
+    }
+  }
+  //   split_tail (split form): the background's own drift and kick, and the
+  //   float constants of the difference forms at the drifted background
+  __device__ __forceinline__ void split_tail(const SimDesc& d, int mode, const double* p0) {
+    double dV0[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) phi0s[f] = fma(k.c, p0[NF + f], p0[f]);   // background drift
+    sk = P::split_prep(pk, d.params, d.derived, d.fparams, phi0s, dV0, V0);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)  // background kick (D[phi0] = 0)
+      pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], p0[NF + f]) : p0[NF + f];
   }
 
   // The kick of Phi_H3 and the per-site sums for one site.
@@ -391,24 +445,47 @@ __device__ __forceinline__ void fold_rows(const double* src, int P, double* out)
 }
 
 // ---------------------------------------------------------------------------
-// Background update after a stage, from the stage's lattice sums `sout`
-// (NQ doubles, slot layout Slots<NF, PREC>): the p_a kick of Phi_H3 (Eq.
-// split-Phi) and the stage/step counters for a sweep; the H = 0 root (Eq. H2),
-// the synchronised sums and the field statistics for a flush.  Shared by the
-// per-launch kernels (last block) and the persistent kernel (every block).
+// Scalars between stages.
 // ---------------------------------------------------------------------------
+// The coefficients that turn a stage's reduced slots into lattice sums and
+// the p_a kick; they depend only on the stage's Ctx, so a caller can form
+// them before the sums arrive.
+template <int NF> struct SumCoef {
+  double ka, kb, pa;         // Phi_H3: p_a += ka sum phi D + kb sum V
+  double spi[NF], tpi[NF];   // split form: S pi0s and 2 pi0s
+};
+
+template <int MODEL, int PREC, typename C>
+__device__ __forceinline__ SumCoef<C::NF> sum_coef(const C& cx, const SimDesc& d) {
+  SumCoef<C::NF> q;
+  // Phi_H3(h): p_a += h a^3 [sum phi D/(a^2 dx^2) - 4 sum V]   (Eq. split-Phi)
+  const double a = cx.k.a, h = cx.k.h;
+  q.ka = (h * a) * d.dx2inv;
+  q.kb = -4.0 * (h * ((a * a) * a));
+  q.pa = cx.k.pa;
+#pragma unroll
+  for (int f = 0; f < C::NF; ++f) {
+    q.spi[f] = (PREC == PREC_SPLIT) ? (double)d.S * cx.pi0s[f] : 0.0;
+    q.tpi[f] = (PREC == PREC_SPLIT) ? 2.0 * cx.pi0s[f] : 0.0;
+  }
+  return q;
+}
+
+template <int NF>
+__device__ __forceinline__ double pa_kick(const SumCoef<NF>& q, double sum_phiD, double sum_V) {
+  return fma(q.ka, sum_phiD, fma(q.kb, sum_V, q.pa));
+}
+
 // Lattice sums of a stage from its reduced slots (NQ doubles, Slots<NF, PREC>):
 // per field sum pi^2, sum phi D, sum (phi - K), sum (phi - K)^2, and sum V.
 template <int MODEL, int PREC, typename C>
-__device__ __forceinline__ void stage_sums(const C& cx, const SimDesc& d, int mode,
-                                           const double* sout, double* fpi2, double* fphiD,
-                                           double* fdphi, double* fdphi2, double& sum_pi2,
-                                           double& sum_phiD, double& sum_V) {
+__device__ __forceinline__ void stage_sums(const C& cx, const SumCoef<C::NF>& q,
+                                           const SimDesc& d, int mode, const double* sout,
+                                           double* fpi2, double* fphiD, double* fdphi,
+                                           double* fdphi2, double& sum_pi2, double& sum_phiD,
+                                           double& sum_V) {
   using SL = typename C::SL;
   constexpr int NF = C::NF;
-  const double Sd = (double)d.S;
-  sum_pi2 = 0.0;
-  sum_phiD = 0.0;
   if constexpr (PREC == PREC_FP64) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -423,23 +500,17 @@ __device__ __forceinline__ void stage_sums(const C& cx, const SimDesc& d, int mo
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       // sum (pi0 + dpi)^2 = S pi0^2 + 2 pi0 sum dpi + sum dpi^2
-      fpi2[f] = fma(Sd * cx.pi0s[f], cx.pi0s[f],
-                    fma(2.0 * cx.pi0s[f], sout[SL::DPI + f], sout[SL::DPI2 + f]));
+      fpi2[f] = fma(q.spi[f], cx.pi0s[f], fma(q.tpi[f], sout[SL::DPI + f], sout[SL::DPI2 + f]));
       fphiD[f] = sout[SL::PHID + f];  // sum (phi0 + d) D[d] = sum d D[d]  (sum D = 0)
       fdphi[f] = sout[SL::DPHI + f];
       fdphi2[f] = sout[SL::DPHI2 + f];
     }
-    sum_V = fma(Sd, cx.V0, sout[SL::V]);  // sum V = S V(phi0) + sum dV
+    sum_V = fma((double)d.S, cx.V0, sout[SL::V]);  // sum V = S V(phi0) + sum dV
   }
+  sum_pi2 = fpi2[0];
+  sum_phiD = fphiD[0];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) { sum_pi2 += fpi2[f]; sum_phiD += fphiD[f]; }
-}
-
-// Phi_H3(h): p_a += h a^3 [sum phi D/(a^2 dx^2) - 4 sum V]   (Eq. split-Phi)
-__device__ __forceinline__ double pa_kick(const Coef& k, const SimDesc& d, double sum_phiD,
-                                          double sum_V) {
-  const double a = k.a;
-  return k.pa + k.h * (a * sum_phiD * d.dx2inv - 4.0 * (a * a * a) * sum_V);
+  for (int f = 1; f < NF; ++f) { sum_pi2 += fpi2[f]; sum_phiD += fphiD[f]; }
 }
 
 // ---------------------------------------------------------------------------
@@ -450,21 +521,22 @@ __device__ __forceinline__ double pa_kick(const Coef& k, const SimDesc& d, doubl
 // per-launch kernels (last block) and the persistent kernel.
 // ---------------------------------------------------------------------------
 template <int MODEL, int PREC, typename C>
-__device__ __forceinline__ void post_stage(const C& cx, const SimDesc& d, int mode,
-                                           const double* sout, const Background& bg,
-                                           Background& nb) {
+__device__ __forceinline__ void post_stage(const C& cx, const SumCoef<C::NF>& q,
+                                           const SimDesc& d, int mode, const double* sout,
+                                           const Background& bg, Background& nb) {
   using SL = typename C::SL;
   constexpr int NF = C::NF;
   nb = bg;
   double sum_pi2, sum_phiD, sum_V;
   double fpi2[NF], fphiD[NF], fdphi[NF], fdphi2[NF];
-  stage_sums<MODEL, PREC>(cx, d, mode, sout, fpi2, fphiD, fdphi, fdphi2, sum_pi2, sum_phiD, sum_V);
+  stage_sums<MODEL, PREC>(cx, q, d, mode, sout, fpi2, fphiD, fdphi, fdphi2, sum_pi2, sum_phiD,
+                          sum_V);
 
   const Coef& k = cx.k;
   double a = k.a, pa = k.pa;
   bool ok = is_fin(sum_pi2) && is_fin(sum_phiD) && is_fin(sum_V);
   if (mode == MODE_SWEEP) {
-    pa = pa_kick(k, d, sum_phiD, sum_V);
+    pa = pa_kick(q, sum_phiD, sum_V);
     nb.eta = bg.eta + k.h;
     nb.h_prev = k.h;
     nb.stage = bg.stage + 1;
@@ -522,35 +594,39 @@ __device__ __forceinline__ void post_stage(const C& cx, const SimDesc& d, int mo
   }
 }
 
-// After a SWEEP stage: the Background fields that Ctx::init of the next stage
-// reads (h_prev, stage, a, p_a, sum pi^2, split background and re-centring
-// shifts, FP64 variance shift), computed with exactly the expressions of
-// post_stage, so that a caller can derive the next stage's coefficients
-// without waiting for the rest of the bookkeeping.
 template <int MODEL, int PREC, typename C>
-__device__ __forceinline__ void next_init_fields(const C& cx, const SimDesc& d, const double* sout,
-                                                 const Background& bg, Background& nb) {
-  using SL = typename C::SL;
+__device__ __forceinline__ void post_stage(const C& cx, const SimDesc& d, int mode,
+                                           const double* sout, const Background& bg,
+                                           Background& nb) {
+  post_stage<MODEL, PREC>(cx, sum_coef<MODEL, PREC>(cx, d), d, mode, sout, bg, nb);
+}
+
+// The next stage's Ctx from this SWEEP stage's reduced slots, in the pieces
+// that a stage boundary can run on different threads; together they give
+// exactly what post_stage followed by Ctx::init gives.
+//   chain_coef: sum pi^2, sum phi D, sum V -> p_a kick -> the next stage's
+//     scalar half-steps (qn: prestage_a of the next stage, formed early)
+template <int MODEL, int PREC, typename C>
+__device__ __forceinline__ Coef chain_coef(const C& cx, const SumCoef<C::NF>& q,
+                                           const PreCoef& qn, const SimDesc& d,
+                                           const double* sout, int mode_next) {
   constexpr int NF = C::NF;
   double sum_pi2, sum_phiD, sum_V;
   double fpi2[NF], fphiD[NF], fdphi[NF], fdphi2[NF];
-  stage_sums<MODEL, PREC>(cx, d, MODE_SWEEP, sout, fpi2, fphiD, fdphi, fdphi2, sum_pi2, sum_phiD,
-                          sum_V);
-  nb.h_prev = cx.k.h;
-  nb.stage = bg.stage + 1;
-  if (nb.stage >= d.nstages) nb.stage = 0;
-  nb.a = cx.k.a;
-  nb.pa = pa_kick(cx.k, d, sum_phiD, sum_V);
-  nb.sum_pi2 = sum_pi2;
+  stage_sums<MODEL, PREC>(cx, q, d, MODE_SWEEP, sout, fpi2, fphiD, fdphi, fdphi2, sum_pi2,
+                          sum_phiD, sum_V);
+  return prestage_p(qn, pa_kick(q, sum_phiD, sum_V), sum_pi2, mode_next);
+}
+//   chain_means (split form): the re-centring shifts of the next stage
+//     (post_stage's mu_phi, mu_pi) and the background they move into
+template <int PREC, typename C>
+__device__ __forceinline__ void chain_means(const C& cx, const SimDesc& d, const double* sout,
+                                            double* mphi, double* mpi) {
+  using SL = typename C::SL;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    nb.shift[f] = bg.shift[f];
-    if constexpr (PREC == PREC_SPLIT) {
-      nb.phi0[f] = cx.phi0s[f];
-      nb.mu_phi[f] = fdphi[f] * d.invS;
-      nb.pi0[f] = cx.pi0s[f];
-      nb.mu_pi[f] = sout[SL::DPI + f] * d.invS;
-    }
+  for (int f = 0; f < C::NF; ++f) {
+    mphi[f] = sout[SL::DPHI + f] * d.invS;
+    mpi[f] = sout[SL::DPI + f] * d.invS;
   }
 }
 
