@@ -107,6 +107,8 @@ def _load():
         "pycool_checkpoint_load": (S, [P, P, C.c_size_t]),
         "pycool_set_stream": (S, [P, P]),
         "pycool_kernel_launches": (C.c_int64, [P]),
+        "pycool_persist_plan": (S, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                                    C.POINTER(C.c_int32), P, C.c_int32, P, C.c_int32]),
         "pycool_destroy": (None, [P]),
         "pycool_strerror": (C.c_char_p, [S]),
         "pycool_server_create": (S, [C.c_size_t, C.c_int32, C.POINTER(P)]),
@@ -290,6 +292,23 @@ def pycool_set_stream(sim, stream) -> None:
 
 def pycool_kernel_launches(sim) -> int:
     return int(lib.pycool_kernel_launches(sim))
+
+
+def pycool_persist_plan(n: int, nf: int, precision: int, sms: int, l2_bytes: int):
+    """The persistent kernel's work plan (host only): (geo, units, uoff) with
+    geo a dict, units an int32 array (units, 4) of (x0, y0, z0, planes + 2)
+    and uoff the int32 block offsets into units."""
+    import numpy as np
+    geo = (C.c_int32 * 9)()
+    _check(lib.pycool_persist_plan(n, nf, precision, sms, l2_bytes, geo, None, 0, None, 0),
+           "pycool_persist_plan")
+    keys = ("n", "vx", "tx", "tiles_x", "ntiles", "rc", "rw", "nunits", "G")
+    g = dict(zip(keys, list(geo)))
+    units = np.zeros((g["nunits"], 4), dtype=np.int32)
+    uoff = np.zeros(g["G"] + 1, dtype=np.int32)
+    _check(lib.pycool_persist_plan(n, nf, precision, sms, l2_bytes, geo, units.ctypes.data,
+                                   g["nunits"], uoff.ctypes.data, g["G"]), "pycool_persist_plan")
+    return g, units, uoff
 
 
 def pycool_destroy(sim) -> None:

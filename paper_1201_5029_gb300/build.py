@@ -38,7 +38,7 @@ def cuda_home() -> str:
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-                   "-Xcompiler", "-fPIC,-fvisibility=hidden,-O2",
+                   "-Xcompiler", "-fPIC,-fvisibility=hidden,-O2,-ffp-contract=off",
                    "-I", os.path.join(ROOT, "include")]
 
 

@@ -113,8 +113,8 @@ Layout sim_layout(const pycool_config& c) {
 // same z, so halo rows and columns hit L2), each to the least loaded block; a
 // block processes its units in the order dealt.  (rc, rw) minimises the
 // busiest block's cost, then the total.
-PGeo plan_units(int n, int word, int nf, int prec, int sms, std::vector<int4>* units,
-                std::vector<int>* off) {
+PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
+                std::vector<int4>* units, std::vector<int>* off) {
   PGeo g;
   std::memset(&g, 0, sizeof(g));
   g.n = n;
@@ -125,97 +125,187 @@ PGeo plan_units(int n, int word, int nf, int prec, int sms, std::vector<int4>* u
   g.tiles_x = n / g.tx;
   const int tiles_y = n / 16;
   g.ntiles = g.tiles_x * tiles_y;
-  const double h = prec == PREC_FP64 ? 0.1 : 0.5;
-  const double pen = prec == PREC_FP64 ? 1.0 : 1.2;
+  // Cost of a block's work, fitted to per-block timings of the persistent
+  // kernel on GB300: a plane costs 1 (pen for the tiles at the y wrap, whose
+  // halo rows arrive by per-field boxes) and a unit adds 2h (its two z-halo
+  // planes and the switch).  In the split form a unit costs ~2 us more
+  // than its planes whether or not the stage's traffic stays in L2; in plane
+  // units that is h ~1.5 for an L2-resident lattice (fast planes) and ~0.3
+  // for a larger one.  The float64 form is bound by its arithmetic: h ~0.25.
+  const double stage_bytes = 4.0 * nf * (double)n * n * n * word;   // phi, pi read and written
+  const bool l2_resident = l2_bytes > 0 && stage_bytes <= 0.75 * (double)l2_bytes;
+  const double h = prec == PREC_FP64 ? 0.25 : (l2_resident ? 1.5 : 0.3);
+  const double pen = prec == PREC_FP64 ? 1.0 : 1.24;
+  constexpr int kMinPiece = 4;   // planes: no unit shorter than this is cut off a chunk
   const int cap = std::min(sms, kMaxPBlocks);
   auto is_wrap = [&](int t) {
     const int ty = t / g.tiles_x;
     return ty == 0 || ty == tiles_y - 1;
   };
-  struct U { int z0, z1, t; double c; };
-  auto deal = [&](int rc, int rw, std::vector<U>& list, std::vector<int>& owner, int& G,
-                  double& mx, double& tot, int& maxcount) {
-    list.clear();
+  struct U { int z0, z1, t, b; };
+  // Deal at target T: the tiles' z-chunks (rc per clear tile, rw per wrap
+  // tile) in z-major order, each to the least loaded block (ties to the lower
+  // index); a chunk that would take that block past T is cut there and its
+  // rest stays at the head of the list.  false: T is too small for cap blocks.
+  std::vector<U> base, out;
+  std::vector<std::pair<double, int>> heap;
+  auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first != y.first ? x.first > y.first : x.second > y.second;
+  };
+  auto chunks = [&](int rc, int rw) {
+    base.clear();
     for (int t = 0; t < g.ntiles; ++t) {
-      const bool w = is_wrap(t);
-      const int R = w ? rw : rc;
-      for (int r = 0; r < R; ++r) {
-        U u;
-        u.z0 = (int)((long long)r * n / R);
-        u.z1 = (int)((long long)(r + 1) * n / R);
-        u.t = t;
-        u.c = ((double)(u.z1 - u.z0) + 2.0 * h) * (w ? pen : 1.0);
-        list.push_back(u);
+      const int R = is_wrap(t) ? rw : rc;
+      for (int r = 0; r < R; ++r)
+        base.push_back(U{(int)((long long)r * n / R), (int)((long long)(r + 1) * n / R), t, -1});
+    }
+    std::stable_sort(base.begin(), base.end(), [](const U& x, const U& y) {
+      return x.z0 != y.z0 ? x.z0 < y.z0 : x.t < y.t;
+    });
+  };
+  auto deal = [&](double T) -> bool {
+    out.clear();
+    heap.clear();
+    for (int b = 0; b < cap; ++b) heap.push_back({0.0, b});
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (size_t i = 0; i < base.size(); ++i) {
+      U u = base[i];
+      while (u.z0 < u.z1) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto& top = heap.back();
+        const double p = is_wrap(u.t) ? pen : 1.0;
+        const int len = u.z1 - u.z0;
+        int k = len;
+        if (top.first + (len + 2.0 * h) * p > T + 1e-9) {
+          k = (int)std::floor((T - top.first) / p - 2.0 * h);
+          if (len - k < kMinPiece) k = len - kMinPiece;
+          if (k < kMinPiece) return false;   // the least loaded block is full: so are all
+        }
+        out.push_back(U{u.z0, u.z0 + k, u.t, top.second});
+        top.first += (k + 2.0 * h) * p;
+        std::push_heap(heap.begin(), heap.end(), cmp);
+        u.z0 += k;
       }
     }
-    std::stable_sort(list.begin(), list.end(), [](const U& a, const U& b) {
-      return a.z0 != b.z0 ? a.z0 < b.z0 : a.t < b.t;
-    });
-    G = (int)std::min<size_t>(list.size(), (size_t)cap);
-    std::vector<double> load(G, 0.0);
-    std::vector<int> count(G, 0);
-    owner.assign(list.size(), 0);
-    // least loaded block, ties to the lower index (deterministic)
-    std::vector<std::pair<double, int>> heap;
-    for (int b = 0; b < G; ++b) heap.push_back({0.0, b});
-    auto cmp = [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
-      return a.first != b.first ? a.first > b.first : a.second > b.second;
-    };
-    std::make_heap(heap.begin(), heap.end(), cmp);
-    for (size_t i = 0; i < list.size(); ++i) {
-      std::pop_heap(heap.begin(), heap.end(), cmp);
-      auto& top = heap.back();
-      owner[i] = top.second;
-      top.first += list[i].c;
-      load[top.second] = top.first;
-      count[top.second] += 1;
-      std::push_heap(heap.begin(), heap.end(), cmp);
+    return true;
+  };
+  auto measure = [&](double& mx, double& tot, int& maxcount, int& used) {
+    std::vector<double> load(cap, 0.0);
+    std::vector<int> count(cap, 0);
+    for (const U& u : out) {
+      load[u.b] += (u.z1 - u.z0 + 2.0 * h) * (is_wrap(u.t) ? pen : 1.0);
+      count[u.b] += 1;
     }
     mx = *std::max_element(load.begin(), load.end());
     tot = 0.0;
     for (double v : load) tot += v;
     maxcount = *std::max_element(count.begin(), count.end());
+    used = 0;
+    for (int b = 0; b < cap; ++b) used += count[b] > 0;
   };
-  double best = 1e300, best_tot = 1e300;
-  std::vector<U> list;
-  std::vector<int> owner;
-  for (int rc = 1; rc <= std::min(n, 64); ++rc) {
-    const int rws[4] = {rc, (rc * 11 + 9) / 10, (rc * 12 + 9) / 10, (rc * 13 + 9) / 10};
-    for (int k = 0; k < 4; ++k) {
-      const int rw = std::min(rws[k], n);
-      if (k > 0 && rw == rws[k - 1]) continue;
+  // the smallest feasible T for each chunking (bisection), then the chunking
+  // with the least loaded slowest block (ties: less total work, fewer chunks)
+  const double work = (double)n * g.tiles_x * ((tiles_y - 2) + 2 * pen);
+  double best = 1e300, best_tot = 1e300, best_T = 0.0;
+  for (int rc = 1; rc <= std::min(16, std::max(1, n / kMinPiece)); ++rc) {
+    const int rws[3] = {rc, (rc * 12 + 9) / 10, (rc * 13 + 9) / 10};
+    for (int j = 0; j < 3; ++j) {
+      const int rw = std::min(rws[j], std::max(1, n / kMinPiece));
+      if (j > 0 && rw == std::min(rws[j - 1], std::max(1, n / kMinPiece))) continue;
       if (pen == 1.0 && rw != rc) continue;
-      int G, maxcount;
+      chunks(rc, rw);
+      double lo = work / cap, hi = (double)n * pen + 2.0 * h * pen + lo;
+      while (!deal(hi)) hi *= 2.0;
+      for (int it = 0; it < 40 && hi - lo > 1e-3; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (deal(mid)) hi = mid; else lo = mid;
+      }
+      deal(hi);
       double mx, tot;
-      deal(rc, rw, list, owner, G, mx, tot, maxcount);
+      int maxcount, used;
+      measure(mx, tot, maxcount, used);
       if (maxcount > kMaxPUnits) continue;
       if (mx < best - 1e-9 || (mx < best + 1e-9 && tot < best_tot - 1e-9)) {
         best = mx;
         best_tot = tot;
+        best_T = hi;
         g.rc = rc;
         g.rw = rw;
       }
     }
   }
-  int G, maxcount;
-  double mx, tot;
-  deal(g.rc, g.rw, list, owner, G, mx, tot, maxcount);
+  chunks(g.rc, g.rw);
+  deal(best_T);
+  // blocks without a unit (small lattices) are dropped: ties go to the lower
+  // index, so the used blocks are 0 .. G-1
+  int G = 0;
+  for (const U& u : out) G = std::max(G, u.b + 1);
   g.G = G;
-  g.nunits = (int)list.size();
+  g.nunits = (int)out.size();
   if (units && off) {
     off->assign(G + 1, 0);
-    for (size_t i = 0; i < list.size(); ++i) (*off)[owner[i] + 1] += 1;
+    for (const U& u : out) (*off)[u.b + 1] += 1;
     for (int b = 0; b < G; ++b) (*off)[b + 1] += (*off)[b];
-    units->assign(list.size(), int4{0, 0, 0, 0});
+    units->assign(out.size(), int4{0, 0, 0, 0});
     std::vector<int> fill(off->begin(), off->end() - 1);
-    for (size_t i = 0; i < list.size(); ++i) {   // per block, in the order dealt
-      const U& u = list[i];
-      const int t = u.t;
-      (*units)[fill[owner[i]]++] =
-          int4{(t % g.tiles_x) * g.tx, (t / g.tiles_x) * 16, u.z0, u.z1 - u.z0 + 2};
-    }
+    for (const U& u : out)   // per block, in the order dealt
+      (*units)[fill[u.b]++] =
+          int4{(u.t % g.tiles_x) * g.tx, (u.t / g.tiles_x) * 16, u.z0, u.z1 - u.z0 + 2};
   }
   return g;
+}
+
+// A plan the kernel may trust: every unit inside the lattice, every (tile, z)
+// pair in exactly one unit, at most kMaxPUnits units per block.
+static bool check_plan(const PGeo& g, const std::vector<int4>& units, const std::vector<int>& off) {
+  if (g.G < 1 || g.G > kMaxPBlocks || (int)off.size() != g.G + 1 || off[0] != 0 ||
+      off[g.G] != (int)units.size() || (int)units.size() != g.nunits)
+    return false;
+  std::vector<unsigned char> seen((size_t)g.ntiles * g.n, 0);
+  for (int b = 0; b < g.G; ++b) {
+    if (off[b + 1] < off[b] || off[b + 1] - off[b] > kMaxPUnits) return false;
+    for (int i = off[b]; i < off[b + 1]; ++i) {
+      const int4 u = units[i];
+      const int planes = u.w - 2;
+      if (u.x < 0 || u.x % g.tx || u.x + g.tx > g.n || u.y < 0 || u.y % 16 || u.y + 16 > g.n ||
+          u.z < 0 || planes < 1 || u.z + planes > g.n)
+        return false;
+      const size_t t = (size_t)(u.y / 16) * g.tiles_x + u.x / g.tx;
+      for (int z = u.z; z < u.z + planes; ++z)
+        if (seen[t * g.n + z]++) return false;
+    }
+  }
+  for (unsigned char c : seen)
+    if (c != 1) return false;
+  return true;
+}
+
+PYCOOL_API pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision,
+                                             int32_t sms, int64_t l2_bytes, int32_t* geo,
+                                             int32_t* units, int32_t cap_units, int32_t* uoff,
+                                             int32_t cap_blocks) {
+  if (n < 32 || n % 32 || (nf != 1 && nf != 2) || sms < 1 || l2_bytes < 0 || !geo ||
+      (precision != PYCOOL_FP64 && precision != PYCOOL_SPLIT_FP32))
+    return PYCOOL_E_INVALID;
+  const int prec = precision == PYCOOL_FP64 ? PREC_FP64 : PREC_SPLIT;
+  std::vector<int4> u;
+  std::vector<int> off;
+  const PGeo g = plan_units(n, prec == PREC_FP64 ? 8 : 4, nf, prec, sms, l2_bytes, &u, &off);
+  if (!check_plan(g, u, off)) return PYCOOL_E_INVALID;
+  const int32_t vals[9] = {g.n, g.vx, g.tx, g.tiles_x, g.ntiles, g.rc, g.rw, g.nunits, g.G};
+  for (int i = 0; i < 9; ++i) geo[i] = vals[i];
+  if (units) {
+    if (cap_units < g.nunits) return PYCOOL_E_INVALID;
+    for (int i = 0; i < g.nunits; ++i) {
+      units[4 * i + 0] = u[i].x; units[4 * i + 1] = u[i].y;
+      units[4 * i + 2] = u[i].z; units[4 * i + 3] = u[i].w;
+    }
+  }
+  if (uoff) {
+    if (cap_blocks < g.G) return PYCOOL_E_INVALID;
+    for (int b = 0; b <= g.G; ++b) uoff[b] = off[b];
+  }
+  return PYCOOL_OK;
 }
 
 void workspace_layout(int ncta, Layout& L) {
@@ -533,14 +623,17 @@ static pycool_status setup_persist(pycool_sim* sim) {
   const int word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
   std::vector<int4> units;
   std::vector<int> uoff;
-  PGeo g = plan_units(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms, &units, &uoff);
+  int l2 = 0;
+  CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, sim->device));
+  PGeo g = plan_units(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms, l2, &units, &uoff);
   PParams& p = sim->pp;
   std::memset(&p, 0, sizeof(p));
   p.g = g;
   int4* d_units = (int4*)(sim->ws + sim->L.off_punits);
   int* d_uoff = (int*)(sim->ws + sim->L.off_punits +
                        align256((size_t)kMaxPBlocks * kMaxPUnits * sizeof(int4)));
-  if (units.size() > (size_t)kMaxPBlocks * kMaxPUnits || uoff.size() > (size_t)kMaxPBlocks + 1)
+  if (units.size() > (size_t)kMaxPBlocks * kMaxPUnits || uoff.size() > (size_t)kMaxPBlocks + 1 ||
+      !check_plan(g, units, uoff))
     return PYCOOL_E_INVALID;
   CK(cudaMemcpy(d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_uoff, uoff.data(), uoff.size() * sizeof(int), cudaMemcpyHostToDevice));

@@ -172,8 +172,8 @@ struct PParams {
 
 // The persistent geometry and its unit table (units grouped by block; off has
 // G + 1 entries).
-PGeo plan_units(int n, int word, int nf, int prec, int sms, std::vector<int4>* units,
-                std::vector<int>* off);
+PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
+                std::vector<int4>* units, std::vector<int>* off);
 
 // Launchers (one translation unit per precision).
 cudaError_t launch_sweep_fp64(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
