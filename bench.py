@@ -63,11 +63,12 @@ FP64_FLUSH_FLOPS_PER_SITE = {"chaotic2": 38.0, "oscillon": 23.0, "qball": 39.0, 
 # DFMA thread instructions per cycle for the 152 SMs) x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# persistent kernel, from one ncu capture of this workload (profiles/
-# evolve_persist_preheat128_ncu.md); None where no capture of the current
-# kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 244.513280e6 + 203.176448e6,
-                          ("preheat128", "split_fp32"): 33.670400e6 + 35.013120e6}
+# persistent kernel, from one ncu capture of that workload and form
+# (profiles/evolve_persist_preheat128_ncu.md, profiles/evolve_persist_oscillon256_split_ncu.md);
+# a workload/form without a capture of the current kernel reports None.
+NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 250.802688e6 + 200.228864e6,
+                          ("preheat128", "split_fp32"): 33.699328e6 + 35.833088e6,
+                          ("oscillon256", "split_fp32"): 1140.986e6 + 983.708672e6}
 
 
 class ClockSampler:
