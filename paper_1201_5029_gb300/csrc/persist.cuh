@@ -39,7 +39,9 @@ constexpr int kPThreads = 512;               // one block per SM
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPTY = kPWarps;                // tile rows: one per warp
 constexpr int kColFieldBytes = 512;          // halo column of one field (y-wrap layout)
-constexpr int kPSmemBudget = 200 * 1024;     // dynamic shared memory per block
+constexpr int kPSmemBudget = 220 * 1024;     // dynamic shared memory per block (227 KB less static)
+constexpr int kKahanGroups = kPThreads / 4;  // split form: one compensated sum per 4 lanes
+constexpr int kSplitSlack = 3;               // split ring: slots beyond the planes in flight
 static_assert(kPTY * 16 == 256, "column box layout assumes 16 rows of 16 bytes");
 static_assert((kPTY + 2) * 16 <= kColFieldBytes, "a dense 18-row column fits a field's slot");
 
@@ -70,26 +72,32 @@ struct PLayout {
 
 // TMA ring of a form: NSLOT slots, LEAD planes in flight ahead of the plane
 // being computed.  FP64 (ALU-bound): three slots.  Split (memory-bound): as
-// many slots as fit beside the per-thread compensated sums (NQ float pairs per
-// thread), at most eight.
+// many slots as fit beside the compensated sums, at most ten, and LEAD = NSLOT
+// less kSplitSlack (the slack lets the producer run ahead of a late warp).
 //   FP64 extra: two drifted-plane buffers [NF][TY+2][TX] (one per plane parity)
 //               and the block-reduction scratch [NQ][threads].
-//   split extra: the per-thread compensated sums [NQ][threads] float pairs.
+//   split extra: the compensated sums [NQ][threads / 4] float pairs, or every
+//               block's row of the stage sums (the fold reads them there),
+//               whichever is larger.
 template <int PREC, int NF, int VX, int NQ>
 struct PRing {
   using LY = PLayout<NF, VX, PREC == PREC_FP64 ? 8 : 4>;
   static constexpr int DRIFT_ELEMS = NF * (kPTY + 2) * LY::TX;
+  static constexpr int KAHAN_BYTES = NQ * kKahanGroups * 8;
+  static constexpr int ROWS_BYTES = kMaxPBlocks * kNQ * 8;
   static constexpr int EXTRA_BYTES =
-      PREC == PREC_FP64 ? 2 * DRIFT_ELEMS * 8 + NQ * kPThreads * 8 : NQ * kPThreads * 8;
+      PREC == PREC_FP64 ? 2 * DRIFT_ELEMS * 8 + NQ * kPThreads * 8
+                        : (KAHAN_BYTES > ROWS_BYTES ? KAHAN_BYTES : ROWS_BYTES);
   static constexpr int FIT = (kPSmemBudget - EXTRA_BYTES) / LY::SLOT_BYTES;
-  static constexpr int NSLOT = PREC == PREC_FP64 ? 3 : (FIT < 8 ? FIT : 8);
-  // planes ahead: the slots less two, and at most the warps that do not fold
-  // the block sums (each issues one of a stage's first planes)
-  static constexpr int LEAD = PREC == PREC_FP64 ? 2
-                              : (NSLOT - 2 < kPWarps - NQ ? NSLOT - 2 : kPWarps - NQ);
+  static constexpr int NSLOT = PREC == PREC_FP64 ? 3 : (FIT < 10 ? FIT : 10);
+  static constexpr int LEAD = PREC == PREC_FP64 ? 2 : NSLOT - kSplitSlack;
+  // warps that issue a stage's first LEAD planes at a stage boundary (the
+  // others fold the block sums), each every PRE-th plane
+  static constexpr int PRE = LEAD < kPWarps - NQ ? LEAD : kPWarps - NQ;
   static constexpr int RING_BYTES = NSLOT * LY::SLOT_BYTES;
   static constexpr int SMEM_BYTES = RING_BYTES + EXTRA_BYTES;
-  static_assert(NSLOT >= 4 || PREC == PREC_FP64, "split ring too shallow");
+  static_assert(NSLOT >= 5 || PREC == PREC_FP64, "split ring too shallow");
+  static_assert(PRE >= 1, "a warp to issue the first planes beside the folds");
 };
 
 template <int MODEL, int PREC, int VX>
@@ -101,7 +109,7 @@ constexpr size_t persist_smem_bytes() {
 struct PShared {
   const SimDesc* d;       // shared-memory copy of the simulation descriptor
   unsigned char* ring;
-  float2* kahan;          // split: [NQ][kPThreads] compensated sums (s, c)
+  float2* kahan;          // split: [NQ][kKahanGroups] compensated sums (s, c)
   double* drift;          // FP64: two drifted planes [parity][NF][TY+2][TX]
   double* red;            // FP64: block-reduction scratch [NQ][kPThreads]
   uint64_t* full;
@@ -447,17 +455,28 @@ __device__ __noinline__ bool produce_split(const PParams& p, const PShared& sm, 
   return true;
 }
 
-// Add a thread's float partials into its compensated sums (shared memory).
+// Add the float partials of each group of four lanes into the group's
+// compensated sums (shared memory, one (s, c) pair per group and quantity):
+// the four lanes' partials are summed first by a butterfly (the same sum in
+// every lane of the group, whatever the order of the adds).  Every lane of
+// the warp calls it.
 template <int NQ>
 __device__ __forceinline__ void kahan_flush(float2* kahan, float (&ps)[NQ]) {
+  const int grp = threadIdx.x >> 2;
+  const bool lead = (threadIdx.x & 3) == 0;
 #pragma unroll
   for (int i = 0; i < NQ; ++i) {
-    float2 v = kahan[i * kPThreads + threadIdx.x];
-    const float y = ps[i] - v.y;
-    const float t = v.x + y;
-    v.y = (t - v.x) - y;
-    v.x = t;
-    kahan[i * kPThreads + threadIdx.x] = v;
+    float x = ps[i];
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    if (lead) {
+      float2 v = kahan[i * kKahanGroups + grp];
+      const float y = x - v.y;
+      const float t = v.x + y;
+      v.y = (t - v.x) - y;
+      v.x = t;
+      kahan[i * kKahanGroups + grp] = v;
+    }
     ps[i] = 0.f;
   }
 }
@@ -496,7 +515,8 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
   const int own = (ly + 1) * TX + lane * VX;
 
 #pragma unroll
-  for (int i = 0; i < NQ; ++i) sm.kahan[i * kPThreads + tid] = make_float2(0.f, 0.f);
+  for (int i = 0; i < NQ; ++i)   // each group's lead lane owns its sums
+    if ((tid & 3) == 0) sm.kahan[i * kKahanGroups + (tid >> 2)] = make_float2(0.f, 0.f);
   float ps[NQ];
 #pragma unroll
   for (int i = 0; i < NQ; ++i) ps[i] = 0.f;
@@ -666,10 +686,9 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   constexpr int NF = C::NF;
   constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
   using RG = PRing<PREC, NF, VX, NQ>;
-  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD, PRE = RG::PRE;
   static_assert(NQ <= kPWarps, "one warp per reduced quantity");
-  static_assert(NQ + LEAD <= kPWarps, "stage-start prefetch: one warp per plane beside the folds");
-  static_assert((size_t)kMaxPBlocks * kNQ * 8 <= (size_t)NQ * kPThreads * 8,
+  static_assert(PREC == PREC_SPLIT || (size_t)kMaxPBlocks * kNQ * 8 <= (size_t)NQ * kPThreads * 8,
                 "the rows of every block fit the reduction scratch");
 
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -747,8 +766,8 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   // stage 0: its first planes are in flight while one thread derives the
   // scalar coefficients (the FP64 chain of the merged half-stages)
   {
-    const int l = kPWarps - 1 - warp;   // warp 15 - l issues plane l
-    if (l < LEAD) prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib, gq, l);
+    for (int l = kPWarps - 1 - warp; l < LEAD; l += kPWarps)   // warp 15 - l issues plane l
+      prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib, gq, l);
     if (tid == 0) sctxv[0].init(sbv[0], d, K > 0 ? MODE_SWEEP : MODE_FLUSH);
     __syncthreads();
     fault = s_bad != 0;
@@ -806,8 +825,8 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       if (warp < NQ) {
         float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int r = 0; r < kPThreads / 32; ++r) {
-          const float2 v = sm.kahan[warp * kPThreads + lane + 32 * r];
+        for (int r = 0; r < kKahanGroups / 32; ++r) {
+          const float2 v = sm.kahan[warp * kKahanGroups + lane + 32 * r];
           pair_add(hi, lo, v.x, -v.y);
         }
 #pragma unroll
@@ -848,11 +867,12 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     //     every block); the next stage's copies wait until these latency-
     //     critical loads have landed (named barrier 1), so that they are not
     //     queued behind the copies;
-    //   warps 15, 14, ... issue the next stage's first planes, one each (its
-    //     buffers are known: a sweep swaps phi and pi, a flush swaps phi) ----
+    //   warps 15, 14, ... (PRE of them) issue the next stage's first LEAD
+    //     planes, every PRE-th plane each (its buffers are known: a sweep
+    //     swaps phi and pi, a flush swaps phi) ----
     const int ib_next = ib ^ (mode == MODE_SWEEP ? 3 : 1);
     const bool pre = k < K;
-    constexpr int kPreThreads = (1 + LEAD) * 32;
+    constexpr int kPreThreads = (1 + PRE) * 32;
     using FT = typename std::conditional<PREC == PREC_FP64, double, float2>::type;
     // every block's row arrives by one bulk copy into the (now free) reduction
     // scratch: one request stream per block instead of 8-byte loads of the
@@ -892,10 +912,11 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       }
       // @sums-written
     } else {
-      const int l = kPWarps - 1 - warp;
-      if (pre && l < LEAD) {
+      const int l0 = kPWarps - 1 - warp;
+      if (pre && l0 < PRE) {
         named_sync(1, kPreThreads);
-        prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib_next, gq, l);
+        for (int l = l0; l < LEAD; l += PRE)
+          prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib_next, gq, l);
       }
       // @prefetch-issued
     }
