@@ -41,7 +41,8 @@ constexpr int kPTY = kPWarps;                // tile rows: one per warp
 constexpr int kColFieldBytes = 512;          // halo column of one field (y-wrap layout)
 constexpr int kPSmemBudget = 220 * 1024;     // dynamic shared memory per block (227 KB less static)
 constexpr int kKahanGroups = kPThreads / 4;  // split form: one compensated sum per 4 lanes
-constexpr int kSplitSlack = 3;               // split ring: slots beyond the planes in flight
+constexpr int kSplitLead = 6;                // split ring: planes in flight at most ...
+constexpr int kSplitSlack = 3;               // ... and at least this many slots beyond them
 static_assert(kPTY * 16 == 256, "column box layout assumes 16 rows of 16 bytes");
 static_assert((kPTY + 2) * 16 <= kColFieldBytes, "a dense 18-row column fits a field's slot");
 
@@ -72,8 +73,12 @@ struct PLayout {
 
 // TMA ring of a form: NSLOT slots, LEAD planes in flight ahead of the plane
 // being computed.  FP64 (ALU-bound): three slots.  Split (memory-bound): as
-// many slots as fit beside the compensated sums, at most ten, and LEAD = NSLOT
-// less kSplitSlack (the slack lets the producer run ahead of a late warp).
+// many slots as fit beside the compensated sums, at most ten, and LEAD =
+// min(kSplitLead, NSLOT - kSplitSlack).  The slack lets the producer (whose
+// role rotates over the warps) refill a slot while the slowest warp is still
+// a few planes behind; on GB300, 6 planes in flight with 3-4 slots of slack
+// beat both more planes with less slack and fewer planes with more (256^3:
+// 7/3 0.446, 6/4 0.428, 5/5 0.434 ms per step).
 //   FP64 extra: two drifted-plane buffers [NF][TY+2][TX] (one per plane parity)
 //               and the block-reduction scratch [NQ][threads].
 //   split extra: the compensated sums [NQ][threads / 4] float pairs, or every
@@ -90,7 +95,8 @@ struct PRing {
                         : (KAHAN_BYTES > ROWS_BYTES ? KAHAN_BYTES : ROWS_BYTES);
   static constexpr int FIT = (kPSmemBudget - EXTRA_BYTES) / LY::SLOT_BYTES;
   static constexpr int NSLOT = PREC == PREC_FP64 ? 3 : (FIT < 10 ? FIT : 10);
-  static constexpr int LEAD = PREC == PREC_FP64 ? 2 : NSLOT - kSplitSlack;
+  static constexpr int LEAD = PREC == PREC_FP64 ? 2
+                              : (NSLOT - kSplitSlack < kSplitLead ? NSLOT - kSplitSlack : kSplitLead);
   // warps that issue a stage's first LEAD planes at a stage boundary (the
   // others fold the block sums), each every PRE-th plane
   static constexpr int PRE = LEAD < kPWarps - NQ ? LEAD : kPWarps - NQ;
