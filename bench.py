@@ -64,11 +64,13 @@ FP64_FLUSH_FLOPS_PER_SITE = {"chaotic2": 38.0, "oscillon": 23.0, "qball": 39.0, 
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # persistent kernel, from one ncu capture of that workload and form
-# (profiles/evolve_persist_preheat128_ncu.md, profiles/evolve_persist_oscillon256_split_ncu.md);
+# (profiles/evolve_persist_preheat128_ncu.md,
+# profiles/evolve_persist_split_oscillon256_qball256_ncu.md);
 # a workload/form without a capture of the current kernel reports None.
-NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 250.802688e6 + 200.228864e6,
-                          ("preheat128", "split_fp32"): 33.699328e6 + 35.833088e6,
-                          ("oscillon256", "split_fp32"): 1140.986e6 + 983.708672e6}
+NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 253.694208e6 + 200.814336e6,
+                          ("preheat128", "split_fp32"): 33.72672e6 + 36.259584e6,
+                          ("oscillon256", "split_fp32"): 1139.579e6 + 982.367232e6,
+                          ("qball256", "split_fp32"): 4878.135e6 + 4138.095e6}
 
 
 class ClockSampler:
