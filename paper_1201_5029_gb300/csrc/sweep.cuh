@@ -1060,9 +1060,11 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
 
 // Depth of the split sweep's TMA ring: kPipeSlots slots, kPipeLead planes in
 // flight ahead of the plane being computed (the slot being recycled was
-// released kPipeSlots - kPipeLead planes earlier).
-constexpr int kPipeSlots = 6;
-constexpr int kPipeLead = 4;
+// released kPipeSlots - kPipeLead planes earlier).  On GB300 the serving mix
+// ran 1.8 % faster closed-loop with 8 slots / 5 in flight than with 6 / 4
+// (two 85 KB blocks per SM).
+constexpr int kPipeSlots = 8;
+constexpr int kPipeLead = 5;
 
 template <int NF, int VX>
 constexpr size_t pipe_smem_bytes() {
