@@ -125,6 +125,18 @@ struct PShared {
   uint32_t* issued;       // per slot: 1 + ring index of the last plane issued
 };
 
+// Vector store to global memory (st.global: the output arrays are global, and
+// a generic store would make the address space a run-time question).
+template <typename T, int VX>
+__device__ __forceinline__ void gstore(T* p, const T (&v)[VX]) {
+  using VT = typename Vec<T, VX>::type;
+  VT x;
+  T* e = reinterpret_cast<T*>(&x);
+#pragma unroll
+  for (int j = 0; j < VX; ++j) e[j] = v[j];
+  __stwb(reinterpret_cast<VT*>(p), x);
+}
+
 // Advance a (unit, plane) position by one plane.
 __device__ __forceinline__ void padvance(const PShared& sm, int& ui, int& uq) {
   if (ui < sm.nunits && ++uq == sm.units[ui].w) { ++ui; uq = 0; }
@@ -414,8 +426,8 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          vstore<T, VX>(phi_out + f * S + o, ph_m[f]);
-          if (MODE == MODE_SWEEP) vstore<T, VX>(pi_out + f * S + o, pin[f]);
+          gstore<T, VX>(phi_out + f * S + o, ph_m[f]);
+          if (MODE == MODE_SWEEP) gstore<T, VX>(pi_out + f * S + o, pin[f]);
         }
       }
       if (mid) {
@@ -528,29 +540,47 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
   for (int i = 0; i < NQ; ++i) ps[i] = 0.f;
   int kg = 0;
 
+  // producer position, LEAD planes ahead (pQ: planes of its unit, 0 past the last)
   int pui = 0, puq = 0;
   for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  int pQ = pui < sm.nunits ? sm.units[pui].w : 0;
   bool ok = true;
   uint32_t g = gq;
+  // ring slot of plane g and the parity of its pass over the ring, kept
+  // incrementally (NSLOT need not be a power of two)
+  int s = (int)(gq % NSLOT);
+  uint32_t par = (gq / NSLOT) & 1u;
   for (int i = 0; i < sm.nunits; ++i) {
     const int4 u = sm.units[i];
     const int Q = u.w;
     const bool clear = yclear(u, n);
     const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
+    // this lane's halo-column rows in a slot (the layout differs at the y wrap)
+    int crow[NF][CR];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int rr = 0; rr < CR; ++rr) {
+        const int r = ly + 1 + rr - (CR - 1) / 2;
+        crow[f][rr] = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+      }
     float part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int jj = 0; jj < VX; ++jj) part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = 0.f;
     for (int q = 0; q < Q; ++q, ++g) {
-      const int s = g % NSLOT;
-      if (pui < sm.nunits) {
+      if (pQ > 0) {
         const uint32_t gp = g + LEAD;
         if ((int)(gp % kPWarps) == ly)
           ok = produce_split<NF, VX, CORNERS, NSLOT>(p, sm, ib, gp, sm.units[pui], puq) && ok;
-        padvance(sm, pui, puq);
+        if (++puq == pQ) {
+          ++pui;
+          puq = 0;
+          pQ = pui < sm.nunits ? sm.units[pui].w : 0;
+        }
       }
-      ok = ok && mbar_wait(&sm.full[s], (g / NSLOT) & 1);
+      ok = ok && mbar_wait(&sm.full[s], par);
       if (!__all_sync(0xffffffffu, ok)) return false;
       const float* sl = (const float*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
       // the three rows this warp needs and the halo-column values, drifted in registers
@@ -578,14 +608,11 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
         const float* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
         const float* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
 #pragma unroll
-        for (int rr = 0; rr < CR; ++rr) {
-          const int r = ly + 1 + rr - (CR - 1) / 2;
-          const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
-          el[f][rr] = madd(cd, cpi[row], cph[row]);
-        }
+        for (int rr = 0; rr < CR; ++rr) el[f][rr] = madd(cd, cpi[crow[f][rr]], cph[crow[f][rr]]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the slot
+      if (++s == NSLOT) { s = 0; par ^= 1u; }
 
       const bool mid = q > 0 && q < Q - 1;   // the z-halo planes need S_off only
       float so_new[NF][VX], smid_new[NF][VX];
@@ -617,8 +644,8 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          vstore<float, VX>(phi_out + f * S + o, phs[f]);
-          if (MODE == MODE_SWEEP) vstore<float, VX>(pi_out + f * S + o, pin[f]);
+          gstore<float, VX>(phi_out + f * S + o, phs[f]);
+          if (MODE == MODE_SWEEP) gstore<float, VX>(pi_out + f * S + o, pin[f]);
         }
         if (++kg == KGROUP) {
           kg = 0;
