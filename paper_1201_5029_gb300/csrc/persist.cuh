@@ -569,6 +569,10 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int jj = 0; jj < VX; ++jj) part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = 0.f;
+    // two planes per trip lets the compiler rename the rotated registers
+    // (the 27-point stencil keeps one: it would spill)
+    constexpr int kUnroll = CORNERS ? 1 : 2;
+#pragma unroll kUnroll
     for (int q = 0; q < Q; ++q, ++g) {
       if (pQ > 0) {
         const uint32_t gp = g + LEAD;
