@@ -792,14 +792,6 @@ PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, 
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(sim->hdesc.phi[0], phi, count * sizeof(double), kind, sim->stream));
     CK(cudaMemcpyAsync(sim->hdesc.pi[0], pi, count * sizeof(double), kind, sim->stream));
-    for (int f = 0; f < nf; ++f) {
-      double v = 0.0;
-      if (on_device)
-        CK(cudaMemcpy(&v, phi + (size_t)f * S, sizeof(double), cudaMemcpyDeviceToHost));
-      else
-        v = phi[(size_t)f * S];
-      b.shift[f] = v;
-    }
   } else {
     // split form: phi0 = lattice mean (float64), dphi = phi - phi0 in float32
     std::vector<double> hphi, hpi;

@@ -49,7 +49,7 @@ struct alignas(16) Background {
   // Sums of the last flush (synchronised state), per field.
   double s_pi2[kMaxFields], s_phiD[kMaxFields], s_V;
   double mean[kMaxFields], var[kMaxFields];         // field mean and variance
-  double shift[kMaxFields];                         // FP64 form: shift K of the variance sums
+  double shift[kMaxFields];                         // unused (kept: checkpoint layout)
   // Split form: lattice-mean background and pending re-centring shifts.
   double phi0[kMaxFields], pi0[kMaxFields];
   double mu_phi[kMaxFields], mu_pi[kMaxFields];

@@ -114,15 +114,6 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
   b.mode = flush ? MODE_FLUSH : MODE_SWEEP;
   b.cur = 0;
   b.init_pa = (flush && state->init_pa) ? 1 : 0;
-  const int nf = d.nf;
-  if (flush) {  // shift of the variance sums: one value of each field
-    for (int f = 0; f < nf; ++f) {
-      if (cudaMemcpyAsync(&b.shift[f], phi_in + (size_t)f * d.S, sizeof(double),
-                          cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-        return PYCOOL_E_CUDA;
-    }
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return PYCOOL_E_CUDA;
-  }
 
   // the shared scratch keeps the last call's contents: tickets and fault must start at 0
   if (cudaMemcpyAsync(base + kOffDesc, &d, sizeof(d), cudaMemcpyHostToDevice, stream) !=

@@ -973,9 +973,10 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
         C& nx = sctxv[cb ^ 1];
         if (lane == 0) {
           nx.set_coef(chain_coef<MODEL, PREC>(cc, s_sc, s_qn, d, sums, mn), d, mn, cc.pk);
-          if constexpr (PREC == PREC_FP64) {
+          if constexpr (PREC == PREC_FP64) {   // the next stage's input is this stage's output
 #pragma unroll
-            for (int f = 0; f < NF; ++f) nx.shiftK[f] = (typename C::T)sbv[cb].shift[f];
+            for (int f = 0; f < NF; ++f)
+              nx.shiftK[f] = (mn == MODE_FLUSH) ? flush_shift(d, ib_next, f, nx.k.c) : 0.0;
           }
         }
         if constexpr (PREC == PREC_SPLIT) {

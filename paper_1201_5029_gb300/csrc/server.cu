@@ -271,7 +271,6 @@ pycool_status admit(pycool_server* s, const Request& r, int slot) {
   b.init_pa = 1;
   b.mode = MODE_FLUSH;  // the first launch only reduces (h_prev = 0)
   for (int f = 0; f < d.nf; ++f) {
-    b.shift[f] = r.ic.background[f];
     if (split) {
       b.phi0[f] = r.ic.background[f];
       b.pi0[f] = r.ic.momentum[f];

@@ -230,6 +230,19 @@ template <typename T> struct Acc {
 // Per-launch context: the coefficients every block derives from the
 // Background (identically), and the per-site update.
 // ---------------------------------------------------------------------------
+// Shift K of a flush's variance sums, sum (phi - K) and sum (phi - K)^2
+// (FP64 form): the drifted value of field f at site 0, read from the flush's
+// input arrays (buffers `cur`; c: the flush's drift coefficient).  A value of
+// the field itself lies within a few standard deviations of its lattice mean,
+// so the two sums do not cancel; a stale shift (the previous flush's mean)
+// would, since the mean moves by O(1) over an oscillation while the variance
+// can be 1e-10.  Every block computes the same K from the same two values.
+__device__ __forceinline__ double flush_shift(const SimDesc& d, int cur, int f, double c) {
+  const double* ph = static_cast<const double*>(d.phi[cur & 1]);
+  const double* pv = static_cast<const double*>(d.pi[(cur >> 1) & 1]);
+  return fma(c, __ldcg(pv + (size_t)f * d.S), __ldcg(ph + (size_t)f * d.S));
+}
+
 template <int MODEL, int PREC>
 struct Ctx {
   using P = Pot<MODEL>;
@@ -254,7 +267,8 @@ struct Ctx {
       split_tail(d, mode, p0);
     } else {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) shiftK[f] = (T)bg.shift[f];
+      for (int f = 0; f < NF; ++f)
+        shiftK[f] = (mode == MODE_FLUSH) ? (T)flush_shift(d, bg.cur, f, k.c) : (T)0;
     }
   }
 
@@ -561,14 +575,12 @@ __device__ __forceinline__ void post_stage(const C& cx, const SumCoef<C::NF>& q,
     for (int f = 0; f < NF; ++f) {
       nb.s_pi2[f] = fpi2[f];
       nb.s_phiD[f] = fphiD[f];
-      // shifted-data mean and variance: K = shift (FP64) or phi0 (split)
-      const double K = (PREC == PREC_FP64) ? bg.shift[f] : cx.phi0s[f];
+      // shifted-data mean and variance: K = the flush's shift (FP64) or phi0 (split)
+      const double K = (PREC == PREC_FP64) ? (double)cx.shiftK[f] : cx.phi0s[f];
       const double m1 = fdphi[f] * d.invS;
       nb.mean[f] = K + m1;
       nb.var[f] = fma(fdphi2[f], d.invS, -m1 * m1);
       ok = ok && is_fin(fdphi[f]) && is_fin(fdphi2[f]);
-      // the next flush shifts by the mean just measured (keeps the variance well-conditioned)
-      if (PREC == PREC_FP64) nb.shift[f] = nb.mean[f];
     }
     nb.s_V = sum_V;
   }

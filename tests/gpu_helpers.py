@@ -57,3 +57,56 @@ def field_errors(g: np.ndarray, o: np.ndarray) -> list:
 
 def rel(a: float, b: float) -> float:
     return abs(a - b) / max(abs(b), 1e-300)
+
+
+def stats_of(e: dict, variances) -> dict:
+    """The statistics a long chaotic run is compared on: a, rho and its parts,
+    and the per-field variances, as one flat dict of floats."""
+    out = {"a": float(e["a"]), "rho": float(e["rho"]), "rho_pot": float(e["rho_pot"])}
+    for f, v in enumerate(variances):
+        out[f"rho_kin{f}"] = float(e["rho_kin"][f])
+        out[f"rho_grad{f}"] = float(e["rho_grad"][f])
+        out[f"var{f}"] = float(v)
+    return out
+
+
+def _nudge(x, rng):
+    """x moved by one ulp up or down at every entry (seeded signs)."""
+    up = rng.random(np.shape(x)) < 0.5
+    return np.where(up, np.nextafter(x, np.inf), np.nextafter(x, -np.inf))
+
+
+def oracle_checkpoints(args):
+    """Oracle run for the long-run statistics test (one process each):
+    args = (workload name, n, order, dt, steps, every, perturbation, seed).
+    The perturbation models the rounding of an implementation that computes
+    the same method in another order or precision, applied after every step:
+      "none" : the oracle as it stands;
+      "ulp"  : every value of phi and pi, and a and p_a, moved by one ulp up
+               or down (seeded signs): rounding differences of the FP64 form;
+      "fp32" : the fluctuations of phi and pi about their lattice means
+               rounded to float32: the split form's representation of them.
+    Returns the statistics at every `every` steps."""
+    name, n, order, dt, steps, every, kind, seed = args
+    w = I.workload(name)
+    phi, pi = I.initial_fields(w, n=n)
+    cfg = oracle_cfg(w, n=n, order=order, dt=dt)
+    st = O.make_state(cfg, phi, pi)
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(steps):
+        O.step(cfg, st)
+        if kind == "ulp":
+            st.phi[...] = _nudge(st.phi, rng)
+            st.pi[...] = _nudge(st.pi, rng)
+            st.a = float(_nudge(st.a, rng))
+            st.pa = float(_nudge(st.pa, rng))
+        elif kind == "fp32":
+            for arr in (st.phi, st.pi):
+                for f in range(arr.shape[0]):
+                    m = float(np.mean(arr[f]))
+                    arr[f] = m + (arr[f] - m).astype(np.float32).astype(np.float64)
+        if (k + 1) % every == 0:
+            e = O.energies(cfg, st)
+            out.append(stats_of(e, [O.field_stats(st, f)[1] for f in range(phi.shape[0])]))
+    return out
