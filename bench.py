@@ -67,10 +67,10 @@ FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 # (profiles/evolve_persist_preheat128_ncu.md,
 # profiles/evolve_persist_split_oscillon256_qball256_ncu.md);
 # a workload/form without a capture of the current kernel reports None.
-NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 253.694208e6 + 200.814336e6,
-                          ("preheat128", "split_fp32"): 33.72672e6 + 36.259584e6,
-                          ("oscillon256", "split_fp32"): 1139.579e6 + 982.367232e6,
-                          ("qball256", "split_fp32"): 4878.135e6 + 4138.095e6}
+NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 250.650112e6 + 199.634944e6,
+                          ("preheat128", "split_fp32"): 33.702144e6 + 35.682304e6,
+                          ("oscillon256", "split_fp32"): 1138.847e6 + 981.85344e6,
+                          ("qball256", "split_fp32"): 4872.848e6 + 4137.886e6}
 
 
 class ClockSampler:
