@@ -229,10 +229,11 @@ def _serve(P, items, arrivals, slots=64, budget=96 << 30):
                 completed=s["completed"], failed=int(bad), wall_s=wall)
 
 
-def serving_leg(P, I, count, steps_scale, load):
+def serving_leg(P, I, count, steps_scale, load, other_loads=()):
     """Serving mix (sizes 32..384^3, three models, orders 2..8): a closed-loop
     calibration of the FP64 form's capacity, then the same Poisson arrival
-    stream at `load` x that capacity for each form."""
+    stream at `load` x that capacity for each form (the headline), and at each
+    of `other_loads` x that capacity (reported under "by_load")."""
     reqs = I.serving_requests(count=count, steps_scale=steps_scale)
     mean_work = sum(r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])
                     for r in reqs) / len(reqs)
@@ -245,8 +246,18 @@ def serving_leg(P, I, count, steps_scale, load):
            "arrival_rate_per_s": rate, "capacity_fp64_req_per_s": capacity,
            "mean_site_stages_per_request": mean_work,
            "latency": "submit (Poisson arrival) -> observables read back on the host"}
-    for prec, items in (("fp64", items64), ("split_fp32", _serving_configs(P, I, reqs, "split_fp32"))):
+    items32 = _serving_configs(P, I, reqs, "split_fp32")
+    for prec, items in (("fp64", items64), ("split_fp32", items32)):
         out[prec] = _serve(P, items, arr)
+    by_load = {}
+    for lo in other_loads:
+        arr_lo = I.poisson_arrivals(lo * capacity, len(reqs), I.SERVING_MIX["arrival_seed"])
+        by_load[str(lo)] = {prec: {k: v for k, v in _serve(P, items, arr_lo).items()
+                                   if k in ("p50_s", "p99_s", "site_updates_per_s", "completed",
+                                            "failed")}
+                            for prec, items in (("fp64", items64), ("split_fp32", items32))}
+    if by_load:
+        out["by_load"] = by_load
     return out
 
 
@@ -334,6 +345,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=60)
     ap.add_argument("--serving-steps-scale", type=float, default=0.02)
     ap.add_argument("--serving-load", type=float, default=0.7)
+    ap.add_argument("--serving-other-loads", default="0.5,0.9",
+                    help="further offered loads (comma list) reported beside the headline")
     ap.add_argument("--forms", default="fp64,split_fp32",
                     help="comma list of forms to time (profiling a single kernel)")
     args = ap.parse_args()
@@ -443,7 +456,8 @@ def main():
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_leg(P, I, args.serving_requests, args.serving_steps_scale,
-                              args.serving_load)
+                              args.serving_load,
+                              [float(x) for x in args.serving_other_loads.split(",") if x])
 
     if rank == 0:
         cpu = None
