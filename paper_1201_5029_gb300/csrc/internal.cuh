@@ -135,11 +135,11 @@ inline Geometry choose_geometry(int n, int word, int nf) {
 constexpr int kMaxPBlocks = 208;           // blocks (SMs) of the persistent kernel at most
 constexpr int kMaxPUnits = 64;             // work units per block
 
-// Geometry, chosen on the host (a function of n, word, N_f and the SM count):
-// tiles of tx x 16 sites, each tile's z-axis cut into ranges (rc ranges for
-// tiles clear of the periodic y boundary, rw for the tiles whose halo rows
-// cross it); the units (tile, z-range) are dealt to the G blocks by the host
-// (plan_units) and read by each block from a table.
+// Geometry, chosen on the host (a function of n, word, N_f, the SM count and
+// the L2 size): tiles of tx x 16 sites, each tile's z-axis cut into chunks (rc
+// for tiles clear of the periodic y boundary, rw for the tiles whose halo rows
+// cross it), the chunks dealt to the G blocks and cut where a block reaches
+// the common target (plan_units); each block reads its units from a table.
 struct PGeo {
   int n, vx, tx, tiles_x, ntiles, rc, rw, nunits, G;
 };

@@ -8,17 +8,18 @@
 // needs a and p_a after Phi_H3 of stage i, i.e. lattice-wide sums of stage i),
 // so a per-stage launch pays the launch ramp, the tail of its last block and a
 // re-derivation of the scalar coefficients in every block, every stage.  Here:
-//   - each block owns a fixed list of work units (tile x z-range), ordered
-//     range-major so that blocks running together are neighbouring tiles at
-//     the same z (their halo rows and columns hit L2);
+//   - each block walks a fixed list of work units (tile x z-range) that the
+//     host planned (plan_units: chunks of the tiles' z-columns dealt in z order
+//     to the least-loaded block, cut to a common target), and the TMA ring
+//     runs on across unit ends;
 //   - all loads are TMA (tile, two halo rows, two 16-byte halo-column boxes,
 //     and for the 27-point stencil four corner cells) into an mbarrier ring;
 //   - at the end of a stage every block writes one row of partial sums; a
-//     grid barrier (atomic arrival counter + generation word, bounded spin)
-//     separates stages; every block then folds all rows in the same fixed
-//     order, so every block derives bit-identical sums, background and
-//     coefficients without another launch, and block 0 alone writes the final
-//     Background back.
+//     grid barrier (monotonic arrival counter, bounded spin) separates
+//     stages; every block then copies all rows into shared memory (one bulk
+//     copy) and folds them in the same fixed order, so every block derives
+//     bit-identical sums, background and coefficients without another
+//     launch, and block 0 alone writes the final Background back.
 // The per-site arithmetic (drift, Eq. D, kick, sums) is that of sweep.cuh
 // (Ctx<>::site, the same potentials and difference forms), so the FP64 and
 // split-FP32 forms compute what the per-launch kernels compute, in a different
@@ -678,7 +679,7 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
 }
 
 // Plane l (< LEAD) of a stage, issued by lane 0 of the calling warp.  Used at
-// stage starts, one warp per plane.  Every plane of the previous stage has
+// stage starts, the first LEAD planes spread over a few warps.  Every plane of the previous stage has
 // been consumed and released before the block barrier that precedes this
 // call, so the slot needs no wait (the "empty" phases still complete as usual).
 template <int PREC, int NF, int VX, bool CORNERS, int NSLOT>
