@@ -327,7 +327,8 @@ def _config(w):
             "n": w["n"], "fields": len(w["background"]), "order": w["order"],
             "stencil": "7pt", "ic": w.get("ic", "white"), "seed": w["seed"],
             "step": "evolve(1): one fused sweep per stage + synchronising flush",
-            "l2": "flushed between timed steps (256 MiB write); state < L2",
+            "l2": "flushed between timed steps (256 MiB write); FP64 state "
+                  + ("< L2" if 2 * len(w["background"]) * w["n"] ** 3 * 8 < 120e6 else "> L2"),
             "parallelism": "replicas (independent lattice per GPU)"}
 
 
