@@ -196,8 +196,11 @@ template <> struct Pot<M_QBALL> {
     }
     return k;
   }
+  // GENERAL: the caller knows k.direct == 0 (a background away from the
+  // origin, every stage of a practical run), so the test per site is dropped.
+  template <bool GENERAL = false>
   __device__ static void diff(const SplitK& k, const float* d, float* dVd, float& dVv) {
-    if (k.direct) {  // background at the origin: V(phi0) = V'(phi0) = 0
+    if (!GENERAL && k.direct) {  // background at the origin: V(phi0) = V'(phi0) = 0
       const float u = 0.5f * fmaf(d[0], d[0], d[1] * d[1]);
       if (u > 0.f) {
         const float l = logf(u) - k.lnM2;

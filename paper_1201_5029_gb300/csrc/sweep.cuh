@@ -313,6 +313,8 @@ struct Ctx {
 
   // The kick of Phi_H3 and the per-site sums for one site.
   //   phj: drifted fields, D: Laplacian, pim: momenta -> pin: new momenta
+  // GENERAL (split Q-ball): the background is away from the origin (see Pot::diff).
+  template <bool GENERAL = false>
   __device__ __forceinline__ void site(int mode, const T (&phj)[NF], const T (&D)[NF],
                                        const T (&pim)[NF], T (&pin)[NF], T* ps) const {
     if constexpr (PREC == PREC_FP64 && MODEL == M_CHAOTIC2) {
@@ -358,7 +360,8 @@ struct Ctx {
       ps[SL::V] += V;
     } else {
       float dVd[NF], dVv;
-      P::diff(sk, phj, dVd, dVv);
+      if constexpr (MODEL == M_QBALL) P::template diff<GENERAL>(sk, phj, dVd, dVv);
+      else P::diff(sk, phj, dVd, dVv);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         pin[f] = (mode == MODE_SWEEP) ? madd(kD, D[f], madd(-kV, dVd[f], pim[f])) : pim[f];
