@@ -70,7 +70,7 @@ FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 250.650112e6 + 199.634944e6,
                           ("preheat128", "split_fp32"): 33.702144e6 + 35.682304e6,
                           ("oscillon256", "split_fp32"): 1138.847e6 + 981.85344e6,
-                          ("qball256", "split_fp32"): 4872.848e6 + 4137.886e6}
+                          ("qball256", "split_fp32"): 4894.694e6 + 4139.030e6}
 
 
 class ClockSampler:
