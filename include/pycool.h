@@ -214,6 +214,31 @@ pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int3
                                   int64_t l2_bytes, int32_t* geo, int32_t* units,
                                   int32_t cap_units, int32_t* uoff, int32_t cap_blocks);
 
+/* Growth functions of the linearised evolution (Sec. 2.2, Eqs. a-lin, phi-0,
+ * Phik-1): the homogeneous background (a, p_a, phi0, pi0) evolved without the
+ * perturbations, and for each of nk values of k_eff^2 (the symbol of the
+ * discrete Laplacian, dimensionless: -D applied to a plane wave) the
+ * 2N_f x 2N_f matrix T with (dPhi_k, dPi_k)(eta) = T (dPhi_k, dPi_k)(0) for
+ * every Fourier mode k of the perturbations with that k_eff^2, after `steps`
+ * time steps of the configuration's order, d-eta and potential (n and L set
+ * V_L and dx; precision and stencil are not used).  The equations of the modes
+ * are linear, so modes with equal k_eff^2 share one T: the caller reconstructs
+ * each mode as T times its initial values.
+ *   phi0, pi0 (in, N_f each): the initial background fields and momenta;
+ *     a0 > 0, pa0: scale factor and its momentum
+ *   k2 (in, host, nk values); T (out, host, nk x (2N_f)^2 doubles, row-major
+ *     per value, rows dPhi_1..dPhi_N, dPi_1..dPi_N, columns the initial
+ *     components in the same order); background (out, host, 2 + 2 N_f doubles:
+ *     a, p_a, phi0[N_f], pi0[N_f] at the end)
+ * Work on `cuda_stream` (NULL: the default stream); the call allocates its
+ * device buffers and synchronises the stream before it returns.
+ * Errors: E_INVALID (bad config or arguments), E_UNSTABLE_DT, E_NOMEM, E_CUDA.
+ * The Q-ball's second derivatives need |Phi0| > 0 throughout. */
+pycool_status pycool_linear_growth(const pycool_config* cfg, double a0, double pa0,
+                                   const double* phi0, const double* pi0, const double* k2,
+                                   int64_t nk, int64_t steps, double* T, double* background,
+                                   void* cuda_stream);
+
 /* Release the simulation and whatever the library allocated for it.  Waits for
  * the simulation's queued work first.  NULL is ignored. */
 void pycool_destroy(pycool_sim* sim);

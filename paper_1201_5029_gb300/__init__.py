@@ -107,6 +107,8 @@ def _load():
         "pycool_checkpoint_load": (S, [P, P, C.c_size_t]),
         "pycool_set_stream": (S, [P, P]),
         "pycool_kernel_launches": (C.c_int64, [P]),
+        "pycool_linear_growth": (S, [C.POINTER(pycool_config), C.c_double, C.c_double, P, P, P,
+                                     C.c_int64, C.c_int64, P, P, P]),
         "pycool_persist_plan": (S, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                     C.POINTER(C.c_int32), P, C.c_int32, P, C.c_int32]),
         "pycool_destroy": (None, [P]),
@@ -292,6 +294,24 @@ def pycool_set_stream(sim, stream) -> None:
 
 def pycool_kernel_launches(sim) -> int:
     return int(lib.pycool_kernel_launches(sim))
+
+
+def pycool_linear_growth(cfg: pycool_config, a0: float, pa0: float, phi0, pi0, k2, steps: int,
+                         stream=None):
+    """Growth functions of the linearised evolution: (T, background) with T of
+    shape (len(k2), 2 N_f, 2 N_f) and background = (a, p_a, phi0, pi0)."""
+    import numpy as np
+    nf = len(phi0)
+    f0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    p0 = np.ascontiguousarray(pi0, dtype=np.float64)
+    kk = np.ascontiguousarray(k2, dtype=np.float64).ravel()
+    T = np.zeros((kk.size, 2 * nf, 2 * nf))
+    bg = np.zeros(2 + 2 * nf)
+    _check(lib.pycool_linear_growth(C.byref(cfg), float(a0), float(pa0), f0.ctypes.data,
+                                    p0.ctypes.data, kk.ctypes.data, kk.size, int(steps),
+                                    T.ctypes.data, bg.ctypes.data, _stream_ptr(stream)),
+           "pycool_linear_growth")
+    return T, (bg[0], bg[1], bg[2:2 + nf].copy(), bg[2 + nf:].copy())
 
 
 def pycool_persist_plan(n: int, nf: int, precision: int, sms: int, l2_bytes: int):

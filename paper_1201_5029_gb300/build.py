@@ -22,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpycool.so")
 SOURCES = ("api.cu", "sweep_fp64.cu", "sweep_split.cu", "persist_fp64.cu", "persist_split.cu",
+           "linear.cu",
            "server.cu", "noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
