@@ -320,6 +320,41 @@ def reference_arm(args, w):
     return 0
 
 
+def linear_leg(P, w, steps):
+    """Growth functions of the linearised evolution (Sec. 2.2) for the
+    workload's lattice: one transfer matrix per distinct k_eff^2 of the
+    7-point stencil (closed form 4 sum sin^2(pi m / n)), advanced `steps` time
+    steps with the homogeneous background.  Times the whole call (device
+    buffers, copies and the kernel) after one warm-up call."""
+    import numpy as np
+    n = w["n"]
+    s = 4.0 * np.sin(np.pi * np.fft.fftfreq(n)) ** 2
+    k2 = s[:, None, None] + s[None, :, None] + s[None, None, :]
+    vals = np.unique(np.round(k2, 12))
+    cfg = P.config_from_workload(w)
+    nf = len(w["background"])
+    phi0 = np.array(w["background"], dtype=np.float64)
+    pi0 = np.array(w["momentum"], dtype=np.float64)
+    # p_a of the homogeneous background from the library's own constraint
+    with P.Simulation(P.config_from_workload(w, n=32)) as sim:
+        sim.set_initial(np.broadcast_to(phi0[:, None, None, None], (nf, 32, 32, 32)).copy(),
+                        np.broadcast_to(pi0[:, None, None, None], (nf, 32, 32, 32)).copy())
+        pa32 = sim.energies()["pa"]
+    pa0 = pa32 * (n / 32.0) ** 3          # p_a scales with V_L for a homogeneous state
+    stages = P.pycool_stages_per_step(w["order"])
+    P.pycool_linear_growth(cfg, 1.0, pa0, phi0, pi0, vals, 1)
+    t0 = time.perf_counter()
+    T, bg = P.pycool_linear_growth(cfg, 1.0, pa0, phi0, pi0, vals, steps)
+    el = time.perf_counter() - t0
+    ok = bool(np.all(np.isfinite(T)))
+    return {"metric": "linearised evolution: growth-function stage updates/s (one per distinct "
+                      "k_eff^2 and stage)",
+            "value": len(vals) * steps * stages / el, "unit": "k-value stage updates/s",
+            "distinct_k2": int(len(vals)), "lattice_modes": n ** 3, "steps": steps,
+            "seconds": el, "lattice_equivalent_site_updates_per_s": n ** 3 * steps * stages / el,
+            "finite": ok, "a_end": bg[0], "config": _config(w)}
+
+
 def _config(w):
     return {"workload": f"{w['name']}: {w['model']} {len(w['background'])}-field, "
                         f"{w['n']}^3 periodic lattice, L={w['L']}, order {w['order']} "
@@ -340,6 +375,8 @@ def main():
     ap.add_argument("--workload", default="preheat128")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--linear", action="store_true",
+                    help="time the linearised evolution's growth functions instead")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -359,6 +396,10 @@ def main():
     w["name"] = args.workload
     if args.impl == "reference":
         return reference_arm(args, w)
+    if args.linear:
+        import paper_1201_5029_gb300 as P
+        print(json.dumps(linear_leg(P, w, args.steps)), flush=True)
+        return 0
 
     import numpy as np
     import torch
