@@ -322,15 +322,13 @@ def reference_arm(args, w):
 
 def linear_leg(P, w, steps):
     """Growth functions of the linearised evolution (Sec. 2.2) for the
-    workload's lattice: one transfer matrix per distinct k_eff^2 of the
-    7-point stencil (closed form 4 sum sin^2(pi m / n)), advanced `steps` time
-    steps with the homogeneous background.  Times the whole call (device
-    buffers, copies and the kernel) after one warm-up call."""
+    workload's lattice: one transfer matrix per distinct k_eff^2 of its
+    stencil (the library's grouping), advanced `steps` time steps with the
+    homogeneous background.  Times the growth-function call (device buffers,
+    copies and the kernel) after one warm-up call."""
     import numpy as np
     n = w["n"]
-    s = 4.0 * np.sin(np.pi * np.fft.fftfreq(n)) ** 2
-    k2 = s[:, None, None] + s[None, :, None] + s[None, None, :]
-    vals = np.unique(np.round(k2, 12))
+    vals, _ = P.pycool_linear_modes(n, w.get("stencil", "7pt"))
     cfg = P.config_from_workload(w)
     nf = len(w["background"])
     phi0 = np.array(w["background"], dtype=np.float64)

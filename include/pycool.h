@@ -234,6 +234,16 @@ pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int3
  * device buffers and synchronises the stream before it returns.
  * Errors: E_INVALID (bad config or arguments), E_UNSTABLE_DT, E_NOMEM, E_CUDA.
  * The Q-ball's second derivatives need |Phi0| > 0 throughout. */
+/* The distinct k_eff^2 values of an n^3 lattice (host arithmetic only): the
+ * symbol of -D (Eq. D, stencil PYCOOL_STENCIL_7PT or _ISO27) on every plane
+ * wave exp(2 pi i m.x / n), m in numpy's FFT order ([z][y][x], x fastest);
+ * values closer than 1e-12 (relative) count as one.
+ *   values (out, room for cap, may be NULL), ascending; count (out): how many;
+ *   index (out, n^3 int32, may be NULL): each mode's position in values.
+ * E_INVALID: bad n (1..1024) or stencil, count NULL, or cap too small. */
+pycool_status pycool_linear_modes(int32_t n, int32_t stencil, double* values, int64_t cap,
+                                  int64_t* count, int32_t* index);
+
 pycool_status pycool_linear_growth(const pycool_config* cfg, double a0, double pa0,
                                    const double* phi0, const double* pi0, const double* k2,
                                    int64_t nk, int64_t steps, double* T, double* background,

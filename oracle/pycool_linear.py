@@ -175,13 +175,20 @@ def evolve(cfg: O.LatticeConfig, s: LinearState, steps: int) -> LinearState:
     return s
 
 
-def distinct_k2(k2: np.ndarray, decimals: int = 12) -> Tuple[np.ndarray, np.ndarray]:
-    """The distinct k_eff^2 values of a lattice (rounded to `decimals` digits so
-    that equal symbols computed through different cosines coincide) and, for
-    every mode, the index of its value."""
-    r = np.round(k2, decimals)
-    vals, inv = np.unique(r.ravel(), return_inverse=True)
-    return vals, inv.reshape(k2.shape)
+def distinct_k2(k2: np.ndarray, tol: float = 1e-12) -> Tuple[np.ndarray, np.ndarray]:
+    """The distinct k_eff^2 values of a lattice, ascending, and for every mode
+    the index of its value.  Values closer than `tol` (relative to max(1, |v|))
+    are one value: the same symbol reached through different cosines differs
+    only in rounding (Sec. 2.2: equal k_eff^2 at several positions)."""
+    flat = np.sort(k2.ravel())
+    vals = [flat[0]]
+    for v in flat[1:]:
+        if v - vals[-1] > tol * max(1.0, abs(v)):
+            vals.append(v)
+    vals = np.array(vals)
+    pos = np.searchsorted(vals, k2.ravel() + tol * np.maximum(1.0, np.abs(k2.ravel())),
+                          side="right") - 1
+    return vals, pos.reshape(k2.shape)
 
 
 def transfer_matrices(cfg: O.LatticeConfig, a0: float, pa0: float, phi0: np.ndarray,

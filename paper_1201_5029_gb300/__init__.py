@@ -107,6 +107,7 @@ def _load():
         "pycool_checkpoint_load": (S, [P, P, C.c_size_t]),
         "pycool_set_stream": (S, [P, P]),
         "pycool_kernel_launches": (C.c_int64, [P]),
+        "pycool_linear_modes": (S, [C.c_int32, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64), P]),
         "pycool_linear_growth": (S, [C.POINTER(pycool_config), C.c_double, C.c_double, P, P, P,
                                      C.c_int64, C.c_int64, P, P, P]),
         "pycool_persist_plan": (S, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
@@ -294,6 +295,20 @@ def pycool_set_stream(sim, stream) -> None:
 
 def pycool_kernel_launches(sim) -> int:
     return int(lib.pycool_kernel_launches(sim))
+
+
+def pycool_linear_modes(n: int, stencil="7pt"):
+    """(values, index): the distinct k_eff^2 of an n^3 lattice (ascending) and
+    each mode's index into them, shape (n, n, n) in numpy FFT order."""
+    import numpy as np
+    st = STENCILS[stencil] if isinstance(stencil, str) else int(stencil)
+    cnt = C.c_int64()
+    _check(lib.pycool_linear_modes(int(n), st, None, 0, C.byref(cnt), None), "pycool_linear_modes")
+    vals = np.zeros(cnt.value)
+    idx = np.zeros((n, n, n), dtype=np.int32)
+    _check(lib.pycool_linear_modes(int(n), st, vals.ctypes.data, cnt.value, C.byref(cnt),
+                                   idx.ctypes.data), "pycool_linear_modes")
+    return vals, idx
 
 
 def pycool_linear_growth(cfg: pycool_config, a0: float, pa0: float, phi0, pi0, k2, steps: int,

@@ -14,8 +14,10 @@
 // thread evolves the (identical) background itself, so threads never wait on
 // one another; the work is FP64 scalar arithmetic, a few hundred operations
 // per stage and k_eff^2 value.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 #include "models.cuh"
@@ -154,6 +156,57 @@ cudaError_t launch_linear_growth(int model, const LinArgs& a, cudaStream_t s) {
 }  // namespace pycool
 
 using namespace pycool;
+
+// The distinct values of k_eff^2 (the symbol of -D on plane waves, Eq. D)
+// over the n^3 lattice modes, and each mode's index into them.  Values that
+// differ by less than 1e-12 (equal symbols reached through different cosines)
+// count as one.
+extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_modes(
+    int32_t n, int32_t stencil, double* values, int64_t cap, int64_t* count, int32_t* index) {
+  if (n < 1 || n > 1024 || !count || cap < 0 ||
+      (stencil != PYCOOL_STENCIL_7PT && stencil != PYCOOL_STENCIL_ISO27))
+    return PYCOOL_E_INVALID;
+  // coefficients by neighbour class (number of non-zero offsets), Eq. D
+  const double c7[4] = {-6.0, 1.0, 0.0, 0.0};
+  const double c27[4] = {-128.0 / 30.0, 14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0};
+  const double* c = stencil == PYCOOL_STENCIL_7PT ? c7 : c27;
+  // one axis: wave number m (numpy FFT order) -> cos(2 pi m / n)
+  std::vector<double> cs(n);
+  for (int m = 0; m < n; ++m) {
+    const int mm = m <= (n - 1) / 2 ? m : m - n;
+    cs[m] = std::cos(2.0 * M_PI * mm / n);
+  }
+  const size_t S = (size_t)n * n * n;
+  std::vector<double> k2(S);
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        const double cz = cs[z], cy = cs[y], cx = cs[x];
+        // sum over the offsets of each class of c_d cos(k.o): products of cosines
+        const double sym = c[0] + 2.0 * c[1] * (cz + cy + cx) +
+                           4.0 * c[2] * (cz * cy + cz * cx + cy * cx) + 8.0 * c[3] * cz * cy * cx;
+        k2[((size_t)z * n + y) * n + x] = -sym;
+      }
+  std::vector<double> sorted(k2);
+  std::sort(sorted.begin(), sorted.end());
+  std::vector<double> vals;
+  for (double v : sorted)
+    if (vals.empty() || v - vals.back() > 1e-12 * std::fmax(1.0, std::fabs(v))) vals.push_back(v);
+  *count = (int64_t)vals.size();
+  if (values) {
+    if (cap < (int64_t)vals.size()) return PYCOOL_E_INVALID;
+    for (size_t i = 0; i < vals.size(); ++i) values[i] = vals[i];
+  }
+  if (index) {
+    for (size_t i = 0; i < S; ++i) {
+      // the last value not above k2[i] + tolerance
+      const double v = k2[i];
+      auto it = std::upper_bound(vals.begin(), vals.end(), v + 1e-12 * std::fmax(1.0, std::fabs(v)));
+      index[i] = (int32_t)((it - vals.begin()) - 1);
+    }
+  }
+  return PYCOOL_OK;
+}
 
 extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_growth(
     const pycool_config* cfg, double a0, double pa0, const double* phi0, const double* pi0,
