@@ -15,7 +15,7 @@ What fixes it, independently of its own formulas:
   - a free field on a static background against the exact per-mode matrices
     of the second-order stage;
   - the growth functions (one transfer matrix per distinct k_eff^2) against the
-    direct evolution of every mode."""
+    direct evolution of every mode, and their symplecticity T^T J T = J."""
 import math
 
 import numpy as np
@@ -178,3 +178,22 @@ def test_growth_functions_reproduce_direct_evolution(model, bg, mom):
     for f in range(nf):
         assert np.max(np.abs(gphi[f] - ls.dphi[f])) < 1e-11 * np.max(np.abs(ls.dphi[f]))
         assert np.max(np.abs(gpi[f] - ls.dpi[f])) < 1e-11 * np.max(np.abs(ls.dpi[f]))
+
+
+@pytest.mark.parametrize("model,bg,mom", [("chaotic2", (1.0, 0.2), (-0.3, 0.1)),
+                                          ("qball", (1.3, 0.4), (0.0, 0.2))])
+def test_growth_functions_are_symplectic(model, bg, mom):
+    """Each sub-flow acts on (dPhi, dPi) as [[1, h/a^2], [0, 1]] or
+    [[1, 0], [-h K, 1]] with K = k_eff^2 a^2/dx^2 + a^4 M symmetric, so every
+    transfer matrix satisfies T^T J T = J (J the symplectic form): a fixed
+    property that a misplaced block or an asymmetric mass matrix breaks."""
+    n = 8
+    p = POINTS[model][0]
+    cfg = O.LatticeConfig(n=n, L=8.0, model=model, params=p, dt=0.02, order=6, mpl=10.0)
+    nf = len(bg)
+    vals, _ = L.distinct_k2(L.k_eff2(n))
+    T, _ = L.transfer_matrices(cfg, 1.0, -50.0, np.array(bg), np.array(mom), vals, 40)
+    J = np.block([[np.zeros((nf, nf)), np.eye(nf)], [-np.eye(nf), np.zeros((nf, nf))]])
+    for t in T:
+        err = np.max(np.abs(t.T @ J @ t - J)) / max(1.0, np.max(np.abs(t)) ** 2)
+        assert err < 1e-13
