@@ -375,6 +375,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--linear", action="store_true",
                     help="time the linearised evolution's growth functions instead")
+    ap.add_argument("--no-linear", action="store_true",
+                    help="leave the growth-function measurement out of the main line")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -499,6 +501,18 @@ def main():
                               args.serving_load,
                               [float(x) for x in args.serving_other_loads.split(",") if x])
 
+    # the linearised evolution's growth functions on the same lattice (Sec. 2.2):
+    # a side measurement, never allowed to take the main line down
+    linear = None
+    if rank == 0 and not args.no_linear:
+        try:
+            lin = linear_leg(P, w, 100)
+            linear = {k: lin[k] for k in ("metric", "value", "unit", "distinct_k2", "lattice_modes",
+                                          "steps", "seconds",
+                                          "lattice_equivalent_site_updates_per_s", "finite")}
+        except Exception as e:  # noqa: BLE001
+            linear = {"error": f"{type(e).__name__}: {e}"}
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -523,6 +537,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "serving": serving,
+            "linear": linear,
             "gpu_launches": int(l64 + l32),
             "clocks": clocks,
         }
