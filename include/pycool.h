@@ -334,9 +334,12 @@ void pycool_server_destroy(pycool_server* srv);
  * swaps its two buffer pairs between calls.  Arrays: float64 device memory,
  * [field][z][y][x], 16-byte aligned; config precision must be PYCOOL_FP64.
  *
- * Errors: E_INVALID for a bad config, bad pointers, or a lattice whose sweep
- * needs more than pycool_noalloc_max_blocks() blocks (about n <= 512 for two
- * fields); E_NONFINITE if a sum overflowed; E_CUDA / E_TIMEOUT as elsewhere.
+ * Errors: E_INVALID for a bad config, bad pointers, an output array that
+ * shares memory with an input array or with the other output (the sweep reads
+ * neighbours of the inputs while it writes the outputs), init_pa set on a
+ * non-flush call, or a lattice whose sweep needs more than
+ * pycool_noalloc_max_blocks() blocks (about n <= 512 for two fields);
+ * E_NONFINITE if a sum overflowed; E_CUDA / E_TIMEOUT as elsewhere.
  * The call synchronises the stream (it reads the background record back).
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.  Every call

@@ -398,7 +398,8 @@ def energies(cfg: LatticeConfig, s: State) -> Dict[str, object]:
 
 
 def field_stats(s: State, i: int) -> tuple:
-    """Lattice mean and variance of field i."""
+    """Lattice mean and variance of field i (the field statistics of the
+    post-processing, Sec. 2.4): mean = sum phi_i / S, variance = sum (phi_i - mean)^2 / S."""
     S = s.phi[i].size
     mean = lattice_sum(s.phi[i]) / S
     var = lattice_sum((s.phi[i] - mean) ** 2) / S

@@ -3,7 +3,10 @@
 Thin ctypes binding over the C ABI declared in ``include/pycool.h``: the same
 function names, argument marshalling only.  Every step of the evolution runs
 in the CUDA kernels of ``libpycool.so``; there is no CPU fallback.  If the
-library has not been built, importing the binding raises.
+library has not been built, importing the binding raises.  The library is
+mapped into the process at the first call (``load()``), so that importing the
+seeded input generators (``paper_1201_5029_gb300.inputs``), which hold none of
+the method's arithmetic, does not load the CUDA code.
 
 Host arrays are numpy float64 arrays of shape (N_f, n, n, n) ([field][z][y][x]);
 device arrays are CUDA torch tensors of the same shape and dtype (pass
@@ -134,7 +137,29 @@ def _load():
     return lib
 
 
-lib = _load()
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libpycool.so is not built ({LIB_PATH}); run "
+        "`python -m paper_1201_5029_gb300.build` (or __graft_entry__.build()) first")
+
+
+class _Library:
+    """The ctypes handle of libpycool.so, opened at the first attribute access."""
+    _handle = None
+
+    def __getattr__(self, name):
+        if _Library._handle is None:
+            _Library._handle = _load()
+        return getattr(_Library._handle, name)
+
+
+lib = _Library()
+
+
+def load():
+    """Map libpycool.so now (raises if it cannot be loaded); returns the handle."""
+    lib.pycool_strerror  # noqa: B018  (first access opens the library)
+    return _Library._handle
 
 
 def _check(status: int, what: str):
@@ -394,6 +419,16 @@ def pycool_server_destroy(srv) -> None:
     lib.pycool_server_destroy(srv)
 
 
+def _is_field_tensor(t, numel: int) -> bool:
+    """A contiguous float64 CUDA tensor of `numel` elements."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover - torch is how callers pass device memory
+        return False
+    return (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and t.numel() == numel)
+
+
 def pycool_noalloc_max_blocks() -> int:
     return int(lib.pycool_noalloc_max_blocks())
 
@@ -401,7 +436,16 @@ def pycool_noalloc_max_blocks() -> int:
 def pycool_sweep_noalloc(cfg: pycool_config, phi_in, pi_in, phi_out, pi_out, flush: bool,
                          state: pycool_stage_state, stream=None) -> int:
     """One stage sweep (flush=False) or synchronising flush (flush=True) with no
-    device allocation; arrays are CUDA tensors.  Returns the status code."""
+    device allocation; arrays are CUDA tensors.  Returns the status code.
+
+    Each array must be a contiguous float64 CUDA tensor of N_f n^3 elements
+    (pi_out may be None for a flush); anything else returns E_INVALID here,
+    before the library is called, since the kernel would read or write past a
+    shorter or differently typed buffer."""
+    need = MODEL_NF.get(int(cfg.model), 0) * int(cfg.n) ** 3
+    for t in (phi_in, pi_in, phi_out) + (() if flush and pi_out is None else (pi_out,)):
+        if t is None or not _is_field_tensor(t, need):
+            return E_INVALID
     ptr = lambda t: None if t is None else C.c_void_p(int(t.data_ptr()))  # noqa: E731
     return lib.pycool_sweep_noalloc(C.byref(cfg), ptr(phi_in), ptr(pi_in), ptr(phi_out),
                                     ptr(pi_out), 1 if flush else 0, C.byref(state),

@@ -59,6 +59,12 @@ cudaError_t scratch_base(char** out) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+// Do the byte ranges [a, a + bytes) and [b, b + bytes) share a byte?
+bool overlap(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
 }  // namespace
 
 PYCOOL_API size_t pycool_noalloc_max_blocks(void) {
@@ -85,6 +91,17 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
       (pi_out && !aligned16(pi_out)))
     return PYCOOL_E_INVALID;
   if (!(state->a > 0.0) || !std::isfinite(state->a)) return PYCOOL_E_INVALID;
+  // p_a from H = 0 is taken by a flush only (a run starts with one)
+  if (!flush && state->init_pa) return PYCOOL_E_INVALID;
+  // the sweep reads neighbours of phi_in while it writes phi_out (and pi_out):
+  // an output that shares memory with an input, or with the other output,
+  // would be read after it was overwritten
+  const size_t bytes = (size_t)model_nfields(cfg->model) * (size_t)cfg->n * (size_t)cfg->n *
+                       (size_t)cfg->n * sizeof(double);
+  if (overlap(phi_out, phi_in, bytes) || overlap(phi_out, pi_in, bytes)) return PYCOOL_E_INVALID;
+  if (!flush && (overlap(pi_out, pi_in, bytes) || overlap(pi_out, phi_in, bytes) ||
+                 overlap(pi_out, phi_out, bytes)))
+    return PYCOOL_E_INVALID;
   const Layout L = layout_for(*cfg);
   if (L.ws_bytes > kWsAvail) return PYCOOL_E_INVALID;  // too large for the scratch
   cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -104,7 +121,7 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
   Background b;
   std::memset(&b, 0, sizeof(b));
   b.a = state->a;
-  b.pa = state->init_pa ? 0.0 : state->pa;
+  b.pa = (flush && state->init_pa) ? 0.0 : state->pa;
   b.eta = state->eta;
   b.h_prev = state->h_prev;
   b.sum_pi2 = state->sum_pi2;
@@ -133,8 +150,8 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
   int32_t fault = 0;
   if (cudaMemcpyAsync(&r, base + kOffBg, sizeof(r), cudaMemcpyDeviceToHost, stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(&fault, base + kOffWs + 128, sizeof(fault), cudaMemcpyDeviceToHost,
-                      stream) != cudaSuccess ||
+      cudaMemcpyAsync(&fault, d.fault, sizeof(fault), cudaMemcpyDeviceToHost, stream) !=
+          cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess)
     return PYCOOL_E_CUDA;
   if (fault) return PYCOOL_E_TIMEOUT;

@@ -55,6 +55,51 @@ def field_errors(g: np.ndarray, o: np.ndarray) -> list:
     return out
 
 
+# Unit roundoff of float64 (round to nearest).
+EPS64 = 2.0 ** -53
+# Per-stage rounding budget of the fluctuation check, in units of EPS64 times
+# the field's magnitude: each stage rounds phi and pi a few times at the
+# magnitude of the field (drift, kick, stencil sum); two implementations that
+# round in different orders drift apart by at most a small multiple of that per
+# stage.  40 covers the measured errors of every FP64 parity case with a
+# margin of 10 or more.
+FLUCT_K = 40.0
+
+
+def fluct_errors(g: np.ndarray, o: np.ndarray) -> list:
+    """Per-field error at the scale of the fluctuations:
+    max|g - o| / max|o - mean(o)|.
+
+    A field that sits on a homogeneous background (phi ~ 1 with fluctuations
+    of 1e-5) is checked by field_errors only to ~1e-5 of the part the sweep
+    actually evolves; this measure divides by the fluctuations themselves."""
+    out = []
+    for f in range(o.shape[0]):
+        scale = float(np.max(np.abs(o[f] - o[f].mean())))
+        if scale == 0.0:
+            scale = float(np.max(np.abs(o[f]))) or 1.0
+        out.append(float(np.max(np.abs(g[f] - o[f]))) / scale)
+    return out
+
+
+def fluct_tolerances(o: np.ndarray, stages: int, floor: float) -> list:
+    """Bound of fluct_errors for the FP64 form after `stages` stage sweeps:
+    max(floor, FLUCT_K * stages * EPS64 * max|o| / max|o - mean(o)|).
+
+    The absolute rounding difference between two FP64 evaluations of the method
+    grows at most by about FLUCT_K EPS64 |o| per stage; relative to the
+    fluctuation scale that is the ratio of background to fluctuations times
+    that.  For a field with no background (ratio ~1) the bound is the normwise
+    tolerance `floor`."""
+    out = []
+    for f in range(o.shape[0]):
+        scale = float(np.max(np.abs(o[f] - o[f].mean())))
+        big = float(np.max(np.abs(o[f])))
+        ratio = big / scale if scale > 0 else 1.0
+        out.append(max(floor, FLUCT_K * max(stages, 1) * EPS64 * ratio))
+    return out
+
+
 def rel(a: float, b: float) -> float:
     return abs(a - b) / max(abs(b), 1e-300)
 

@@ -342,3 +342,29 @@ def potential_derivative_error(model: str, params, point, h=1e-5) -> float:
         fd = (O.potential(model, params, xp)[0] - O.potential(model, params, xm)[0]) / (2 * h)
         worst = max(worst, abs(fd - dV[i]) / max(1.0, abs(dV[i])))
     return worst
+
+
+# --- field statistics --------------------------------------------------------
+
+def field_stats_error(n: int = 8) -> float:
+    """Mean and variance of fields whose statistics are known in closed form:
+      c + A cos(2 pi m.x / n) with a lattice mode m whose doubled mode is not
+        zero mod n: the cosine sums to zero over the periods, its square to
+        S/2, so mean = c and variance = A^2/2 exactly;
+      a field equal to u on half the sites and v on the other half (the z < n/2
+        slab): mean (u + v)/2, variance ((u - v)/2)^2.
+    Returns the largest relative error of the oracle's (mean, variance)."""
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    worst = 0.0
+    for c, A, m in ((1.0, 1e-3, (1, 2, 3)), (-0.5, 2.0, (0, 1, 0)), (3.0, 0.25, (2, 0, 1))):
+        wave = np.cos(2.0 * math.pi * (m[0] * z + m[1] * y + m[2] * x) / n)
+        s = O.State(a=1.0, pa=0.0, phi=(c + A * wave)[None].copy(), pi=np.zeros((1, n, n, n)))
+        mean, var = O.field_stats(s, 0)
+        worst = max(worst, abs(mean - c) / abs(c), abs(var - A * A / 2) / (A * A / 2))
+    u, v = 1.25, -0.75
+    f = np.where(z < n // 2, u, v).astype(np.float64)
+    s = O.State(a=1.0, pa=0.0, phi=np.stack([np.zeros_like(f), f]), pi=np.zeros((2, n, n, n)))
+    mean, var = O.field_stats(s, 1)
+    worst = max(worst, abs(mean - (u + v) / 2) / abs((u + v) / 2),
+                abs(var - ((u - v) / 2) ** 2) / ((u - v) / 2) ** 2)
+    return worst

@@ -87,6 +87,24 @@ def _initial_pa_factor(cfg, a, phi, pi):
     return -math.sqrt(6.0 * cfg.VL * cfg.mpl ** 2 * O._field_energy_sum(cfg, a, phi, pi))
 
 
+def _field_stats_unbiased(s, i):
+    S = s.phi[i].size
+    mean = O.lattice_sum(s.phi[i]) / S
+    return mean, O.lattice_sum((s.phi[i] - mean) ** 2) / (S - 1)
+
+
+def _field_stats_no_mean(s, i):
+    S = s.phi[i].size
+    return O.lattice_sum(s.phi[i]) / S, O.lattice_sum(s.phi[i] ** 2) / S
+
+
+def _field_stats_wrong_field(s, i):
+    return _orig_field_stats(s, 0)
+
+
+_orig_field_stats = O.field_stats
+
+
 def _checks():
     """Every pin as (name, passes?) with the same bounds as the pin tests."""
     def slope(f, *args):
@@ -105,6 +123,7 @@ def _checks():
                      and P.plane_wave_symbol_error("iso27", 8, (1, 2, 3)) < 1e-13,
         "dV": P.potential_derivative_error("chaotic2", (1.0, 1e4), (1.0, 0.3)) < 1e-8,
         "composition8": 7.7 < slope(P.composition_error_harmonic, (8, 10), (8, 20)) < 8.8,
+        "field_stats": P.field_stats_error() < 1e-12,
     }
     return out
 
@@ -123,6 +142,9 @@ MUTATIONS = {
     "stencil weight": ("stencil_coefficients", _stencil_bad_face),
     "dV term dropped": ("potential_derivative", _dV_chaotic_missing_term),
     "constraint factor 6 instead of 12": ("initial_pa", _initial_pa_factor),
+    "variance divided by S - 1": ("field_stats", _field_stats_unbiased),
+    "variance without the mean": ("field_stats", _field_stats_no_mean),
+    "statistics of the wrong field": ("field_stats", _field_stats_wrong_field),
 }
 
 

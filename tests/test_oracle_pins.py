@@ -173,3 +173,8 @@ def test_second_friedmann_equation():
 @pytest.mark.parametrize("stencil", ["7pt", "iso27"])
 def test_plane_wave_energies(stencil):
     assert P.plane_wave_energy_error(stencil) < 1e-14
+
+
+def test_field_stats_closed_forms():
+    """Mean c and variance A^2/2 of c + A cos(k.x); two-valued slab field."""
+    assert P.field_stats_error() < 1e-12   # inputs rounded at |c| eps, relative to A

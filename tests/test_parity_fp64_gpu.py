@@ -1,7 +1,10 @@
 """FP64 CUDA path against the CPU oracle, element by element (GPU).
 
 Tolerance: 1e-11 relative (per field, max|gpu - oracle| / max|oracle|; and
-relative on a, p_a) over the stated number of steps.  The two sides differ only
+relative on a, p_a) over the stated number of steps; and, at the scale of the
+fluctuations (max|gpu - oracle| / max|oracle - mean(oracle)|), the bound of
+gpu_helpers.fluct_tolerances: 40 float64 roundings at the field's magnitude
+per stage, relative to the fluctuations (never below 1e-11).  The two sides differ only
 in rounding order (the GPU merges the drifts of neighbouring half-stages and
 sums in a fixed blocked order; the oracle applies each flow separately and
 sums with correct rounding)."""
@@ -28,6 +31,14 @@ def _check(gphi, gpi, ge, st, oe, tol=TOL):
     assert max(ep) < tol, ("pi", ep)
     assert ea < tol and epa < tol, (ea, epa)
     assert ge["eta"] == pytest.approx(st.eta, rel=1e-13)
+    # the fluctuations about each field's mean, at their own scale
+    stages = int(ge["sweeps_done"]) + 1
+    for name, g, o in (("phi", gphi, st.phi), ("pi", gpi, st.pi)):
+        fe = G.fluct_errors(g, o)
+        ft = G.fluct_tolerances(o, stages, tol)
+        print(f"\nfluct {name}: err {['%.2e' % x for x in fe]} bound {['%.2e' % x for x in ft]} "
+              f"({stages} stages)")
+        assert all(e < t for e, t in zip(fe, ft)), (name, fe, ft)
     return max(ef + ep + [ea, epa])
 
 

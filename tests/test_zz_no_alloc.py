@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 P = pytest.importorskip("paper_1201_5029_gb300")
 from paper_1201_5029_gb300 import inputs as I  # noqa: E402
+import gpu_helpers as G  # noqa: E402
 
 TOL = 1e-11
 
@@ -70,6 +71,11 @@ def test_noalloc_matches_evolve_two_steps(n, order):
         gphi, gpi = phi.cpu().numpy(), pi.cpu().numpy()
         assert _rel_field(gphi, rf) < TOL
         assert _rel_field(gpi, rp) < TOL
+        # and at the scale of the fluctuations about each field's mean
+        sweeps = (step + 1) * (stages + 1)
+        for g, r in ((gphi, rf), (gpi, rp)):
+            fe, ft = G.fluct_errors(g, r), G.fluct_tolerances(r, sweeps, TOL)
+            assert all(e < t for e, t in zip(fe, ft)), (fe, ft)
         assert abs(st.a - re["a"]) / re["a"] < TOL
         assert abs(st.pa - re["pa"]) / abs(re["pa"]) < TOL
         assert st.steps_done == step + 1 and st.h_prev == 0.0
