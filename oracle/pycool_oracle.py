@@ -48,6 +48,10 @@ Readings of the paper taken here (the paper is silent or garbled):
    initial p_a is 0 (the constraint cannot be imposed).
 8. The complex Q-ball field is Phi = (phi_1 + i phi_2)/sqrt(2), so
    |Phi|^2 = (phi_1^2 + phi_2^2)/2 and V = dV = 0 at |Phi| = 0.
+9. The adaptive conformal step of Sec. 3.1 ("constant increases in physical
+   time", dt_phys = a d-eta): with time_step = "physical" each time step
+   takes d-eta = dt / a, a being the scale factor of the synchronised state at
+   the start of the step; all stages of that step use it (h_i = w_i d-eta).
 """
 from __future__ import annotations
 
@@ -246,6 +250,7 @@ class LatticeConfig:
     mpl: float = 1.0            # reduced Planck mass; inf = static background
     rho_rad0: float = 0.0       # homogeneous radiation, Eq. H2
     rho_mat0: float = 0.0       # homogeneous matter, Eq. H2
+    time_step: str = "conformal"  # "conformal": d-eta = dt; "physical": d-eta = dt / a (Sec. 3.1)
 
     @property
     def VL(self) -> float:
@@ -317,10 +322,24 @@ def second_order_stage(cfg: LatticeConfig, s: State, h: float) -> None:
     s.eta = s.eta + h
 
 
+def step_size(cfg: LatticeConfig, s: State) -> float:
+    """The conformal step d-eta of the next time step: dt (conformal time), or
+    dt / a at the synchronised state that starts the step (the adaptive
+    conformal step of Sec. 3.1: each step advances physical time t, dt = a
+    d-eta, by about dt)."""
+    if cfg.time_step == "conformal":
+        return cfg.dt
+    if cfg.time_step == "physical":
+        return cfg.dt / s.a
+    raise ValueError(f"unknown time step rule {cfg.time_step!r}")
+
+
 def step(cfg: LatticeConfig, s: State) -> None:
-    """One time step d-eta: the stages of the chosen order in sequence."""
+    """One time step: the stages of the chosen order in sequence, each with
+    h = w_i d-eta."""
+    deta = step_size(cfg, s)
     for w in stage_weights(cfg.order):
-        second_order_stage(cfg, s, w * cfg.dt)
+        second_order_stage(cfg, s, w * deta)
 
 
 def evolve(cfg: LatticeConfig, s: State, steps: int) -> State:

@@ -368,3 +368,88 @@ def field_stats_error(n: int = 8) -> float:
     worst = max(worst, abs(mean - (u + v) / 2) / abs((u + v) / 2),
                 abs(var - ((u - v) / 2) ** 2) / ((u - v) / 2) ** 2)
     return worst
+
+
+# --- the adaptive conformal step (physical-time steps, Sec. 3.1) -------------
+
+def homogeneous_error_physical(order: int, dt: float, steps: int = 24) -> float:
+    """Physical-time steps (d-eta = dt / a per step) on a homogeneous lattice
+    against DOP853 on the background ODEs (Sec. 2.2, Eqs. a-lin, phi-0), both
+    at the conformal time the steps reached; the oscillon potential at
+    m_pl = 1, where a grows several-fold.  Error ~ dt^order."""
+    from scipy.integrate import solve_ivp
+    n = 2
+    m2, lam, g = 1.0, 1.0, 0.5
+    cfg = O.LatticeConfig(n=n, L=1.0, model="oscillon", params=(m2, lam, g), dt=dt, order=order,
+                          mpl=1.0, time_step="physical")
+    phi = np.full((1, n, n, n), 0.8)
+    pi = np.full((1, n, n, n), 0.1)
+    st = O.make_state(cfg, phi, pi)
+    y0 = [st.a, st.pa, 0.8, 0.1]
+    VL = cfg.VL
+
+    def rhs(t, y):
+        a, pa, f, p = y
+        V = 0.5 * m2 * f ** 2 - 0.25 * lam * f ** 4 + g * f ** 6 / 6.0
+        dV = m2 * f - lam * f ** 3 + g * f ** 5
+        return [-pa / (6 * VL), VL * a ** 3 * (p * p / a ** 6 - 4 * V), p / a ** 2, -a ** 4 * dV]
+
+    O.evolve(cfg, st, steps * int(round(0.2 / dt)))
+    sol = solve_ivp(rhs, (0.0, st.eta), y0, method="DOP853", rtol=1e-13, atol=1e-14)
+    yT = sol.y[:, -1]
+    got = [st.a, st.pa, st.phi[0, 0, 0, 0], st.pi[0, 0, 0, 0]]
+    return float(max(abs(u - r) / max(abs(r), 1e-3) for u, r in zip(got, yT)))
+
+
+def constraint_error_physical(order: int, dt: float, T: float = 0.6) -> float:
+    """max |H| / (a^4 V_L rho) over a run of physical-time steps (Eq. H2 = 0)."""
+    cfg = _inhomogeneous_cfg(order, dt)
+    cfg.time_step = "physical"
+    phi, pi = _inhomogeneous_ics(cfg.n)
+    st = O.make_state(cfg, phi, pi)
+    worst = 0.0
+    for _ in range(int(round(T / dt))):
+        O.step(cfg, st)
+        e = O.energies(cfg, st)
+        worst = max(worst, abs(O.hamiltonian(cfg, st)) / (st.a ** 4 * cfg.VL * e["rho"]))
+    return worst
+
+
+def static_physical_equivalence() -> float:
+    """On a static background (m_pl = inf) a stays a0, so physical-time steps
+    of dt are conformal steps of dt / a0: with a0 = 2 (dt / a0 exact) the two
+    runs must agree bit for bit.  Returns the largest difference."""
+    cfg_p = _inhomogeneous_cfg(4, 0.03, n=8)
+    cfg_p.mpl = math.inf
+    cfg_p.time_step = "physical"
+    cfg_c = _inhomogeneous_cfg(4, 0.015, n=8)
+    cfg_c.mpl = math.inf
+    phi, pi = _inhomogeneous_ics(8)
+    sp = O.make_state(cfg_p, phi, pi, a0=2.0)
+    sc = O.make_state(cfg_c, phi, pi, a0=2.0)
+    O.evolve(cfg_p, sp, 12)
+    O.evolve(cfg_c, sc, 12)
+    return float(max(np.max(np.abs(sp.phi - sc.phi)), np.max(np.abs(sp.pi - sc.pi)),
+                     abs(sp.eta - sc.eta)))
+
+
+def radiation_physical_recurrence(order: int, rho_r0: float = 3.0, a0: float = 1.1,
+                                  dt: float = 0.07, steps: int = 40) -> float:
+    """Fields zero, radiation only: p_a is constant and every Phi_H1 moves a by
+    -p_a h / (6 V_L m^2), so a step of d-eta = dt / a_n (the stage weights sum
+    to one) gives a_{n+1} = a_n + C dt / a_n, C = -p_a / (6 V_L m^2), with a_n
+    the scale factor at the start of the step.  Largest relative deviation
+    from that recurrence."""
+    n = 2
+    cfg = O.LatticeConfig(n=n, L=1.0, model="free", params=(1.0,), dt=dt, order=order,
+                          mpl=1.0, rho_rad0=rho_r0, time_step="physical")
+    z = np.zeros((1, n, n, n))
+    st = O.make_state(cfg, z, z, a0=a0)
+    C = -st.pa / (6.0 * cfg.VL)
+    worst = 0.0
+    for _ in range(steps):
+        a_n = st.a
+        O.step(cfg, st)
+        want = a_n + C * dt / a_n
+        worst = max(worst, abs(st.a - want) / want)
+    return worst

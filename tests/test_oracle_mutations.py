@@ -105,6 +105,14 @@ def _field_stats_wrong_field(s, i):
 _orig_field_stats = O.field_stats
 
 
+def _step_size_a2(cfg, s):
+    return cfg.dt / s.a ** 2 if cfg.time_step == "physical" else cfg.dt
+
+
+def _step_size_ignores_a(cfg, s):
+    return cfg.dt
+
+
 def _checks():
     """Every pin as (name, passes?) with the same bounds as the pin tests."""
     def slope(f, *args):
@@ -124,6 +132,8 @@ def _checks():
         "dV": P.potential_derivative_error("chaotic2", (1.0, 1e4), (1.0, 0.3)) < 1e-8,
         "composition8": 7.7 < slope(P.composition_error_harmonic, (8, 10), (8, 20)) < 8.8,
         "field_stats": P.field_stats_error() < 1e-12,
+        "physical_radiation": P.radiation_physical_recurrence(4) < 1e-14,
+        "physical_static": P.static_physical_equivalence() == 0.0,
     }
     return out
 
@@ -145,6 +155,8 @@ MUTATIONS = {
     "variance divided by S - 1": ("field_stats", _field_stats_unbiased),
     "variance without the mean": ("field_stats", _field_stats_no_mean),
     "statistics of the wrong field": ("field_stats", _field_stats_wrong_field),
+    "physical step dt / a^2": ("step_size", _step_size_a2),
+    "physical step without a": ("step_size", _step_size_ignores_a),
 }
 
 

@@ -178,3 +178,26 @@ def test_plane_wave_energies(stencil):
 def test_field_stats_closed_forms():
     """Mean c and variance A^2/2 of c + A cos(k.x); two-valued slab field."""
     assert P.field_stats_error() < 1e-12   # inputs rounded at |c| eps, relative to A
+
+
+# --- the adaptive conformal step (Sec. 3.1) ----------------------------------
+
+@pytest.mark.parametrize("order,dts", [(2, (0.05, 0.025)), (4, (0.05, 0.025)), (6, (0.2, 0.1))])
+def test_physical_steps_homogeneous_mode_against_dop853(order, dts):
+    e1, e2 = (P.homogeneous_error_physical(order, dt) for dt in dts)
+    assert abs(math.log2(e1 / e2) - order) < 0.5, (e1, e2)
+
+
+@pytest.mark.parametrize("order,dts", [(2, (0.04, 0.02)), (4, (0.04, 0.02))])
+def test_physical_steps_constraint_error_scales_as_dt_to_the_order(order, dts):
+    e1, e2 = (P.constraint_error_physical(order, dt) for dt in dts)
+    assert abs(math.log2(e1 / e2) - order) < 0.4, (e1, e2)
+
+
+def test_physical_steps_on_static_background_are_conformal_steps_of_dt_over_a():
+    assert P.static_physical_equivalence() == 0.0
+
+
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_physical_steps_radiation_recurrence(order):
+    assert P.radiation_physical_recurrence(order) < 1e-14
