@@ -40,5 +40,8 @@ cudaError_t encode_tensor_maps(SimDesc& d);
 cudaError_t launch_arm(Background* bg, long long nsweeps, cudaStream_t s);
 void observables(const Background& b, const SimDesc& d, double mpl, double rho_r0,
                  double rho_m0, pycool_observables* out);
+// Fault injection (pycool_debug_fail_alloc): true if this device allocation
+// is to report failure (consumes one of the requested failures).
+bool injected_alloc_failure();
 
 }  // namespace pycool

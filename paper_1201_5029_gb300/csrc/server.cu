@@ -113,7 +113,8 @@ class Arena {
  public:
   bool init(size_t bytes) {
     bytes &= ~(size_t)255;
-    if (bytes == 0 || cudaMalloc((void**)&base_, bytes) != cudaSuccess) {
+    if (bytes == 0 || injected_alloc_failure() ||
+        cudaMalloc((void**)&base_, bytes) != cudaSuccess) {
       cudaGetLastError();
       base_ = nullptr;
       return false;
@@ -211,6 +212,7 @@ struct pycool_server {
   std::condition_variable cv_work, cv_done;
   std::deque<Request> queue;
   std::map<uint64_t, Result> results;
+  std::vector<uint64_t> cancel;                 // resident tickets to retire at the next boundary
   uint64_t next_ticket = 1;
   bool stop = false;
   pycool_status fatal = PYCOOL_OK;
@@ -342,19 +344,22 @@ pycool_status rebuild(pycool_server* s, Group& G) {
   return PYCOOL_OK;
 }
 
-void retire(pycool_server* s, int slot, const Background& b, int32_t fault) {
+void retire(pycool_server* s, int slot, const Background& b, int32_t fault, bool cancelled) {
   Member& m = *s->slots[slot];
   Result res;
   res.done = true;
-  res.status = fault ? PYCOOL_E_TIMEOUT : (b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK);
+  res.status = fault ? PYCOOL_E_TIMEOUT
+                     : (b.error ? PYCOOL_E_NONFINITE : (cancelled ? PYCOOL_E_CANCELLED : PYCOOL_OK));
   observables(b, m.hdesc, m.req.cfg.mpl, m.req.cfg.rho_rad0, m.req.cfg.rho_mat0, &res.obs);
   const double t = now_s();
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->results[m.req.ticket] = res;
-    s->latencies.push_back(t - m.req.t_submit);
-    s->site_updates += (double)m.hdesc.S * (double)b.sweeps_done;
-    s->t_last = t;
+    if (!cancelled) {   // the latency and rate figures describe completed requests only
+      s->latencies.push_back(t - m.req.t_submit);
+      s->site_updates += (double)m.hdesc.S * (double)b.sweeps_done;
+      s->t_last = t;
+    }
   }
   s->cv_done.notify_all();
   Group& G = s->groups[m.group];
@@ -413,7 +418,17 @@ void server_loop(pycool_server* s) {
     }
     if (!back.empty()) {
       std::lock_guard<std::mutex> lk(s->mu);
-      for (auto it = back.rbegin(); it != back.rend(); ++it) s->queue.push_front(*it);
+      for (auto it = back.rbegin(); it != back.rend(); ++it) {
+        auto c = std::find(s->cancel.begin(), s->cancel.end(), it->ticket);
+        if (c != s->cancel.end()) {   // cancelled while it waited for memory
+          s->cancel.erase(c);
+          s->results[it->ticket].done = true;
+          s->results[it->ticket].status = PYCOOL_E_CANCELLED;
+          s->cv_done.notify_all();
+          continue;
+        }
+        s->queue.push_front(*it);
+      }
     }
     // 2. one graph replay per group, then a copy of every member's record
     bool any = false;
@@ -436,10 +451,19 @@ void server_loop(pycool_server* s) {
       if (cudaStreamSynchronize(G.stream) != cudaSuccess) { fail_all(s, PYCOOL_E_CUDA); return; }
     }
     // 3. retire finished members (record idle after their flush, or stopped)
+    //    and cancelled ones (every launch of their group has completed here)
+    std::vector<uint64_t> cancel;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      cancel.swap(s->cancel);
+    }
     for (int slot = 0; slot < s->max_slots; ++slot) {
       if (!s->slots[slot]) continue;
       const Background& b = s->h_bg[slot];
-      if (b.mode == MODE_IDLE || s->h_fault[slot]) retire(s, slot, b, s->h_fault[slot]);
+      const bool cut = std::find(cancel.begin(), cancel.end(), s->slots[slot]->req.ticket) !=
+                       cancel.end();
+      if (b.mode == MODE_IDLE || s->h_fault[slot] || cut)
+        retire(s, slot, b, s->h_fault[slot], cut && b.mode != MODE_IDLE);
     }
   }
 }
@@ -475,6 +499,7 @@ PYCOOL_API pycool_status pycool_server_submit(pycool_server* s, const pycool_con
   if (!s || !cfg || !ic || !ticket || steps < 0) return PYCOOL_E_INVALID;
   const pycool_status st = validate(cfg);
   if (st != PYCOOL_OK) return st;
+  if (cfg->precision == PYCOOL_SPLIT_DD) return PYCOOL_E_INVALID;   // no per-stage DD kernel
   if (!std::isfinite(ic->noise) || ic->noise < 0.0) return PYCOOL_E_INVALID;
   if (footprint(*cfg) > s->arena.capacity()) return PYCOOL_E_NOMEM;  // could never fit
   Request r;
@@ -511,6 +536,28 @@ PYCOOL_API pycool_status pycool_server_wait(pycool_server* s, uint64_t ticket, d
   s->results.erase(ticket);
   if (out) *out = r.obs;
   return r.status;
+}
+
+PYCOOL_API pycool_status pycool_server_cancel(pycool_server* s, uint64_t ticket) {
+  if (!s) return PYCOOL_E_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return PYCOOL_E_NOT_FOUND;
+    if (it->second.done) return PYCOOL_E_STATE;   // finished already: collect it with wait
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+      if (q->ticket == ticket) {                  // not admitted yet: drop it from the queue
+        s->queue.erase(q);
+        it->second.done = true;
+        it->second.status = PYCOOL_E_CANCELLED;
+        s->cv_done.notify_all();
+        return PYCOOL_OK;
+      }
+    }
+    s->cancel.push_back(ticket);                  // resident (or being admitted)
+  }
+  s->cv_work.notify_all();
+  return PYCOOL_OK;
 }
 
 PYCOOL_API pycool_status pycool_server_stats(pycool_server* s, double* p50_s, double* p99_s,

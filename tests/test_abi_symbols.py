@@ -50,3 +50,11 @@ def test_host_only_calls_work_without_gpu():
     except P.PycoolError as e:
         assert e.status == P.E_UNSTABLE_DT
     assert "stability" in P.pycool_strerror(P.E_UNSTABLE_DT)
+
+
+def test_fault_injection_calls_check_their_arguments_without_gpu():
+    import paper_1201_5029_gb300 as P
+    assert P.pycool_debug_fail_alloc(-1) == P.E_INVALID
+    assert P.pycool_debug_barrier_stall(None, 1000) == P.E_INVALID
+    assert P.pycool_server_cancel(None, 1) == P.E_INVALID
+    assert P.pycool_strerror(P.E_CANCELLED) == "request cancelled"
