@@ -1,22 +1,27 @@
 """Throughput of the symplectic lattice step on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload preheat128]
-                    [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload qball256]
+                    [--extra preheat128,oscillon256] [--impl ours|reference]
 
-Workload (default): the two-field chaotic-preheating problem on a 128^3
-lattice, L = 10/m, 4th-order Yoshida triple jump (3 stages per step),
-d-eta = 0.01, seeded spectral initial fluctuations; both the FP64 form and the
-split-FP32 form.  A "step" is one time step through the C ABI: evolve(1) =
-3 fused stage sweeps + the synchronising flush sweep (every row of the hot
-path: background update, fused sweep, reductions, flush/energies).
+Headline workload (default): the curvaton Q-ball problem on a 256^3 lattice,
+two real field components, L = 200/m, 8th-order composition (15 stages per
+step), d-eta = 0.05, seeded white-noise initial fluctuations -- the largest
+configuration that is timed; its state (1.07 GB in FP64) is larger than L2.
+The two other timed configurations (two-field preheating at 128^3, order 4;
+the one-field oscillon at 256^3, order 6) are measured in the same run and
+reported under "extra".  Every workload is timed in each form (FP64 and
+split-FP32).  A "step" is one time step through the C ABI: evolve(1) = s
+fused stage sweeps + the synchronising flush sweep (every row of the hot
+path: background update, fused sweep, reductions, flush/energies), one launch
+of the persistent kernel.
 
 Metric: site-updates/s per stage = n^3 x stages / time, whole job (all ranks).
-The 128^3 state is smaller than L2, so L2 is flushed (256 MiB write) between
-timed steps; each step is timed with CUDA events on the simulation's stream.
+L2 is flushed (256 MiB write) between timed steps; each step is timed with CUDA
+events on the simulation's stream.
 
 --impl reference times the CPU oracle (oracle/pycool_oracle.py, the method as
-written in the paper) on the host cores on the same workload, one time step
-per timed step.
+written in the paper) on the host cores on the same workload: each timed step
+is one second-order stage of the workload (a bounded sample of a time step).
 
 Multi-GPU: the simulations are independent (replicas only, no collective on
 the data path); under torchrun each rank runs its own replica and rank 0
@@ -25,6 +30,8 @@ reports the whole-job rate over the slowest rank.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import math
 import os
@@ -38,6 +45,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "site-updates/s per stage vs HBM roofline (FP64, split-FP32); serving p50/p99"
 UNIT = "site-updates/s"
+FORMS = ("fp64", "split_fp32", "split_dd")
+WORD = {"fp64": 8, "split_fp32": 4, "split_dd": 8}
+KERNEL_FORM = {"fp64": "FP64", "split_fp32": "split", "split_dd": "splitDD"}
 
 
 def _peaks():
@@ -62,15 +72,35 @@ FP64_FLUSH_FLOPS_PER_SITE = {"chaotic2": 38.0, "oscillon": 23.0, "qball": 39.0, 
 # GB300 float64 peak: 2 DFMA lanes per SM per clock (ncu: 304 predicated-on
 # DFMA thread instructions per cycle for the 152 SMs) x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# persistent kernel, from one ncu capture of that workload and form
-# (profiles/evolve_persist_preheat128_ncu.md,
-# profiles/evolve_persist_split_oscillon256_qball256_ncu.md);
-# a workload/form without a capture of the current kernel reports None.
-NCU_TRAFFIC_PER_LAUNCH = {("preheat128", "fp64"): 250.650112e6 + 199.634944e6,
-                          ("preheat128", "split_fp32"): 33.702144e6 + 35.682304e6,
-                          ("oscillon256", "split_fp32"): 1138.847e6 + 981.85344e6,
-                          ("qball256", "split_fp32"): 4894.694e6 + 4139.030e6}
+# DRAM traffic per launch measured by ncu, one line per (workload, form):
+#   <workload> <form> <kernel source hash> <dram read bytes> <dram write bytes>
+# A figure counts only while the kernel sources still hash to the value it was
+# taken with; otherwise the line's traffic is reported as null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 (first 16 hex digits) of the CUDA sources of the library."""
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1201_5029_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, form: str):
+    """DRAM bytes per launch from the ncu capture of the current kernels, or None."""
+    try:
+        cur = kernel_source_hash()
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 5 and not line.startswith("#") and parts[0] == workload \
+                        and parts[1] == form and parts[2] == cur:
+                    return float(parts[3]) + float(parts[4])
+    except OSError:
+        pass
+    return None
 
 
 class ClockSampler:
@@ -197,6 +227,41 @@ def e2e_form(P, torch, w, precision, steps, phi_pin, pi_pin, out_phi, out_pi, st
     return dt
 
 
+def roofline(w, form, s, ms_per_step, hbm, peak_kind):
+    """Roofline object of the persistent kernel (one launch per time step of s
+    stages) of a workload and form, from the CUDA-event time per launch."""
+    S = w["n"] ** 3
+    nf = len(w["background"])
+    # algorithmic bytes per launch: s sweeps read and write phi and pi, the
+    # flush reads both and writes phi
+    launch_bytes = (s * 4 + 3) * nf * WORD[form] * S
+    gbs = launch_bytes / (ms_per_step / 1e3) / 1e9
+    kname = f"evolve_persist<{w['model']},7pt,{KERNEL_FORM[form]}>"
+    traffic = measured_traffic(w["name"], form)
+    common = {"traffic": traffic, "kernel": kname + " (one launch per time step)",
+              "algorithmic_bytes_per_launch": launch_bytes,
+              "traffic_over_algorithmic": (traffic / launch_bytes) if traffic else None}
+    if form == "fp64":
+        flops = S * (s * FP64_FLOPS_PER_SITE.get(w["model"], 40.0)
+                     + FP64_FLUSH_FLOPS_PER_SITE.get(w["model"], 35.0))
+        tf = flops / (ms_per_step / 1e3) / 1e12
+        out = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": tf / FP64_PEAK_TFLOPS,
+               "peak_kind": "float64 pipe: 2 DFMA/SM/clk x 152 SMs x 2.07 GHz (GB300 FP64 is "
+                            "1/64 of FP32; float64 arithmetic binds this form, not HBM)",
+               "flops_per_launch": flops, "achieved_gbs": gbs, "hbm_frac": gbs / hbm,
+               "hbm_peak_gbs": hbm}
+    else:
+        out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+               "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        if form == "split_dd":
+            out["note"] = ("double-float fluctuations: 8 bytes per value like FP64, arithmetic "
+                           "on the FP32 pipe (error-free transformations); the form is held to "
+                           "the FP64 parity tolerances")
+    out.update(common)
+    return out
+
+
 def _serving_configs(P, I, reqs, prec):
     mix = I.SERVING_MIX
     out = []
@@ -221,7 +286,7 @@ def _serve(P, items, arrivals, slots=64, budget=96 << 30):
                 time.sleep(dt)
         tickets.append(P.pycool_server_submit(srv, cfg, ic, r["seed"], r["steps"]))
         work += r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])
-    bad = sum(P.pycool_server_wait(srv, t, 600.0)[0] != P.OK for t in tickets)
+    bad = sum(P.pycool_server_wait(srv, t, 1800.0)[0] != P.OK for t in tickets)
     wall = time.perf_counter() - t0
     s = P.pycool_server_stats(srv)
     P.pycool_server_destroy(srv)
@@ -229,21 +294,24 @@ def _serve(P, items, arrivals, slots=64, budget=96 << 30):
                 completed=s["completed"], failed=int(bad), wall_s=wall)
 
 
-def serving_leg(P, I, count, steps_scale, load, other_loads=()):
+def serving_leg(P, I, count, steps_scale, load, other_loads=(), calib_count=100):
     """Serving mix (sizes 32..384^3, three models, orders 2..8): a closed-loop
-    calibration of the FP64 form's capacity, then the same Poisson arrival
-    stream at `load` x that capacity for each form (the headline), and at each
-    of `other_loads` x that capacity (reported under "by_load")."""
+    calibration of the FP64 form's capacity on the first `calib_count`
+    requests, then the Poisson arrival stream of all `count` requests at
+    `load` x that capacity for each form (the headline), and the split form at
+    each of `other_loads` x that capacity (reported under "by_load")."""
     reqs = I.serving_requests(count=count, steps_scale=steps_scale)
-    mean_work = sum(r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])
-                    for r in reqs) / len(reqs)
+    work_of = lambda r: r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])  # noqa
+    mean_work = sum(work_of(r) for r in reqs) / len(reqs)
     items64 = _serving_configs(P, I, reqs, "fp64")
-    calib = _serve(P, items64, None)
+    calib = _serve(P, items64[:calib_count], None)
     capacity = calib["site_updates_per_s"] / mean_work          # requests/s
     rate = load * capacity
     arr = I.poisson_arrivals(rate, len(reqs), I.SERVING_MIX["arrival_seed"])
     out = {"requests": len(reqs), "steps_scale": steps_scale, "offered_load": load,
            "arrival_rate_per_s": rate, "capacity_fp64_req_per_s": capacity,
+           "capacity_calibration": f"closed loop, first {min(calib_count, len(reqs))} requests, "
+                                   "FP64",
            "mean_site_stages_per_request": mean_work,
            "latency": "submit (Poisson arrival) -> observables read back on the host"}
     items32 = _serving_configs(P, I, reqs, "split_fp32")
@@ -252,33 +320,57 @@ def serving_leg(P, I, count, steps_scale, load, other_loads=()):
     by_load = {}
     for lo in other_loads:
         arr_lo = I.poisson_arrivals(lo * capacity, len(reqs), I.SERVING_MIX["arrival_seed"])
-        by_load[str(lo)] = {prec: {k: v for k, v in _serve(P, items, arr_lo).items()
-                                   if k in ("p50_s", "p99_s", "site_updates_per_s", "completed",
-                                            "failed")}
-                            for prec, items in (("fp64", items64), ("split_fp32", items32))}
+        by_load[str(lo)] = {"split_fp32": {k: v for k, v in _serve(P, items32, arr_lo).items()
+                                           if k in ("p50_s", "p99_s", "site_updates_per_s",
+                                                    "completed", "failed")}}
     if by_load:
         out["by_load"] = by_load
     return out
 
 
-def cpu_baseline(w, phi, pi, budget_s=15.0):
-    """The oracle as it stands, on the host cores: whole time steps of the workload."""
+def _oracle_stage_rate(args):
+    """Oracle stages on one host core for about `budget` seconds (one process)."""
+    name, n, budget = args
     from oracle import pycool_oracle as O
-    cfg = O.LatticeConfig(n=w["n"], L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+    from paper_1201_5029_gb300 import inputs as I
+    w = I.workload(name)
+    phi, pi = I.initial_fields(w, n=n)
+    cfg = O.LatticeConfig(n=n, L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
                           order=w["order"], mpl=w["mpl"])
     st = O.make_state(cfg, phi, pi)
-    s = len(O.stage_weights(w["order"]))
+    ws = O.stage_weights(w["order"])
     done, t0 = 0, time.perf_counter()
     while True:
-        O.step(cfg, st)
+        O.second_order_stage(cfg, st, ws[done % len(ws)] * cfg.dt)
         done += 1
         el = time.perf_counter() - t0
-        if el > budget_s or done >= 20:
+        if el > budget:
             break
-    rate = w["n"] ** 3 * s * done / el
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} full time step(s) of the {w['n']}^3 workload ({s} stages each), "
-                      f"{el:.1f} s, numpy FP64, single thread"}
+    return n ** 3 * done, el
+
+
+def cpu_baseline(w, budget_s=15.0, all_core_n=64):
+    """The oracle as it stands, on the host cores.  One thread on the
+    workload's own lattice (second-order stages of its time step), and every
+    host core running its own replica of the same model on an all_core_n^3
+    lattice (independent processes, as the GPU's replicas are independent)."""
+    import multiprocessing as mp
+    sites, el = _oracle_stage_rate((w["name"], w["n"], budget_s))
+    single = sites / el
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")        # no fork after the process has used the GPU
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_stage_rate, [(w["name"], all_core_n, budget_s)] * cores)
+        wall = time.perf_counter() - t0
+    agg = sum(s for s, _ in res) / max(e for _, e in res)
+    return {"value": agg, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, one per host core, each running second-order stages "
+                      f"of the {w['name']} model on its own {all_core_n}^3 lattice for "
+                      f"~{budget_s:.0f} s (numpy FP64; {wall:.1f} s wall)",
+            "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                              "sample": f"second-order stages of the {w['n']}^3 workload itself, "
+                                        f"{el:.1f} s, numpy FP64, one thread"}}
 
 
 def reference_arm(args, w):
@@ -291,28 +383,28 @@ def reference_arm(args, w):
     cfg = O.LatticeConfig(n=w["n"], L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
                           order=w["order"], mpl=w["mpl"])
     st = O.make_state(cfg, phi, pi)
-    s = len(O.stage_weights(w["order"]))
-    # one warm-up step at most: the oracle has no caches to warm
-    for _ in range(min(args.warmup, 1)):
-        O.step(cfg, st)
-    # each timed step is one full time step; stop early once the sample is
-    # bounded (~2 minutes) so the whole run ends within a few minutes
+    wts = O.stage_weights(w["order"])
+    # warm-up: at most one stage (the oracle has no caches to warm)
+    for i in range(min(args.warmup, 1)):
+        O.second_order_stage(cfg, st, wts[i % len(wts)] * cfg.dt)
+    # each timed step is one second-order stage of the workload (a bounded
+    # sample of its time step); stop once ~2 minutes are used
     done, t0 = 0, time.perf_counter()
     while done < args.steps:
-        O.step(cfg, st)
+        O.second_order_stage(cfg, st, wts[(done + 1) % len(wts)] * cfg.dt)
         done += 1
         if time.perf_counter() - t0 > 120.0:
             break
     el = time.perf_counter() - t0
-    value = w["n"] ** 3 * s * done / el
+    value = w["n"] ** 3 * done / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
         "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(w),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{done} full time step(s) of the {w['n']}^3 workload "
+                         "sample": f"{done} second-order stage(s) of the {w['n']}^3 workload "
                                    f"({el:.1f} s; numpy FP64, single thread)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -354,6 +446,7 @@ def linear_leg(P, w, steps):
 
 
 def _config(w):
+    state = 2 * len(w["background"]) * w["n"] ** 3 * 8
     return {"workload": f"{w['name']}: {w['model']} {len(w['background'])}-field, "
                         f"{w['n']}^3 periodic lattice, L={w['L']}, order {w['order']} "
                         f"(Yoshida), dt={w['dt']}, m_pl={w['mpl']}",
@@ -361,34 +454,66 @@ def _config(w):
             "stencil": "7pt", "ic": w.get("ic", "white"), "seed": w["seed"],
             "step": "evolve(1): one fused sweep per stage + synchronising flush",
             "l2": "flushed between timed steps (256 MiB write); FP64 state "
-                  + ("< L2" if 2 * len(w["background"]) * w["n"] ** 3 * 8 < 120e6 else "> L2"),
+                  + (f"{state / 1e6:.0f} MB < L2" if state < 120e6 else
+                     f"{state / 1e6:.0f} MB > L2"),
             "parallelism": "replicas (independent lattice per GPU)"}
+
+
+def time_workload(P, torch, I, name, forms, steps, warmup, flush_buf, stream, ws, hbm, peak_kind):
+    """Every form of one workload: CUDA-event timing of `steps` evolve(1) calls
+    after `warmup` untimed ones; the per-form results with their rooflines."""
+    w = I.workload(name)
+    w["name"] = name
+    phi, pi = I.initial_fields(w)
+    S = w["n"] ** 3
+    res = {prec: run_form(P, torch, w, prec, steps, warmup, flush_buf, phi, pi, stream)
+           for prec in forms}
+    tot = slowest_rank_ms({k: v["total_ms"] for k, v in res.items()}, forms, "cuda")
+    out = {"config": _config(w), "forms": {}}
+    for prec in forms:
+        r = res[prec]
+        rate = whole_job_rate(ws, S, r["stages"], steps, tot[prec])
+        msps = tot[prec] / steps
+        out["forms"][prec] = {"value": rate, "unit": UNIT, "ms_per_step": msps,
+                              "launches": r["launches"], "status": r["status"],
+                              "roofline": roofline(w, prec, r["stages"], msps, hbm, peak_kind)}
+    for f, dt in (("split_fp32", "f32 fluctuations + f64 background/sums"),
+                  ("split_dd", "f32 pairs (double-float fluctuations) + f64 background/sums")):
+        if f in forms:
+            out["forms"][f]["dtype"] = dt
+            if "fp64" in forms:
+                out["forms"][f]["speedup_vs_fp64"] = (out["forms"][f]["value"]
+                                                      / out["forms"]["fp64"]["value"])
+    return w, phi, pi, out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="preheat128")
+    ap.add_argument("--workload", default="qball256")
+    ap.add_argument("--extra", default="preheat128,oscillon256",
+                    help="further workloads timed in the same run (comma list)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--linear", action="store_true",
                     help="time the linearised evolution's growth functions instead")
     ap.add_argument("--no-linear", action="store_true",
                     help="leave the growth-function measurement out of the main line")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=60)
+    ap.add_argument("--serving-requests", type=int, default=500)
     ap.add_argument("--serving-steps-scale", type=float, default=0.02)
     ap.add_argument("--serving-load", type=float, default=0.7)
-    ap.add_argument("--serving-other-loads", default="0.5,0.9",
-                    help="further offered loads (comma list) reported beside the headline")
-    ap.add_argument("--forms", default="fp64,split_fp32",
+    ap.add_argument("--serving-other-loads", default="",
+                    help="further offered loads (comma list), split form, under by_load")
+    ap.add_argument("--forms", default="fp64,split_fp32,split_dd",
                     help="comma list of forms to time (profiling a single kernel)")
     args = ap.parse_args()
     forms = [f for f in args.forms.split(",") if f]
+    extras = [x for x in args.extra.split(",") if x and x != args.workload]
     args.warmup = max(args.warmup, 3)
 
     from paper_1201_5029_gb300 import inputs as I
@@ -401,7 +526,6 @@ def main():
         print(json.dumps(linear_leg(P, w, args.steps)), flush=True)
         return 0
 
-    import numpy as np
     import torch
     import paper_1201_5029_gb300 as P
 
@@ -411,76 +535,40 @@ def main():
         import torch.distributed as dist
         dist.init_process_group(backend="nccl")
     stream = torch.cuda.current_stream()
-    phi, pi = I.initial_fields(w)
-    nf = phi.shape[0]
-    S = w["n"] ** 3
     flush_buf = torch.zeros(256 << 20, dtype=torch.uint8, device="cuda")
     peaks, peak_kind = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
-    res = {}
     with ClockSampler(local) as clk:
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        for prec in forms:
-            res[prec] = run_form(P, torch, w, prec, args.steps, args.warmup, flush_buf, phi, pi,
-                                 stream)
+        w, phi, pi, head = time_workload(P, torch, I, args.workload, forms, args.steps,
+                                         args.warmup, flush_buf, stream, ws, hbm, peak_kind)
+        extra = {}
+        for name in extras:
+            extra[name] = time_workload(P, torch, I, name, forms, args.steps, args.warmup,
+                                        flush_buf, stream, ws, hbm, peak_kind)[3]
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
     clocks = clk.summary()
+    nf = phi.shape[0]
+    S = w["n"] ** 3
+    s = P.pycool_stages_per_step(w["order"])
 
-    # slowest rank decides
-    tot = slowest_rank_ms({k: v["total_ms"] for k, v in res.items()}, forms, "cuda")
-    if forms != ["fp64", "split_fp32"]:
-        if rank == 0:  # profiling run: a short line per form, no baselines
-            for f in forms:
-                r = res[f]
-                print(json.dumps({"form": f, "value": whole_job_rate(ws, S, r["stages"],
-                                                                      args.steps, tot[f]),
-                                  "unit": UNIT, "ms_per_step": tot[f] / args.steps,
-                                  "launches": r["launches"], "status": r["status"]}), flush=True)
+    if forms != list(FORMS):
+        if rank == 0:  # profiling run: a short line per workload and form, no baselines
+            for name, leg in [(args.workload, head)] + list(extra.items()):
+                for f in forms:
+                    r = leg["forms"][f]
+                    print(json.dumps({"workload": name, "form": f, "value": r["value"],
+                                      "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                                      "launches": r["launches"], "status": r["status"],
+                                      "roofline_frac": r["roofline"]["frac"]}), flush=True)
         return 0
 
-    def summarize(prec, word):
-        r = res[prec]
-        s = r["stages"]
-        total_s = tot[prec] / 1e3
-        rate = whole_job_rate(ws, S, s, args.steps, tot[prec])
-        # algorithmic bytes per launch (one launch = one time step: s sweeps
-        # that read and write phi and pi, then the flush that reads both and
-        # writes phi)
-        launch_bytes = (s * 4 + 3) * nf * word * S
-        gbs = launch_bytes * args.steps / total_s / 1e9
-        return rate, gbs, r["launches"], launch_bytes
-
-    r64, gbs64, l64, b64 = summarize("fp64", 8)
-    r32, gbs32, l32, b32 = summarize("split_fp32", 4)
-    s = res["fp64"]["stages"]
-    launch_flops = S * (s * FP64_FLOPS_PER_SITE.get(w["model"], 40.0)
-                        + FP64_FLUSH_FLOPS_PER_SITE.get(w["model"], 35.0))
-    fp64_tflops = launch_flops * args.steps / (tot["fp64"] / 1e3) / 1e12
-    kname = {"chaotic2": "chaotic2", "oscillon": "oscillon", "qball": "qball", "free": "free"}[w["model"]]
-    roof64 = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS,
-              "unit": "TFLOP/s", "frac": fp64_tflops / FP64_PEAK_TFLOPS,
-              "traffic": NCU_TRAFFIC_PER_LAUNCH.get((args.workload, "fp64")),
-              "kernel": f"evolve_persist<{kname},7pt,FP64> (one launch per time step)",
-              "peak_kind": "float64 pipe: 2 DFMA/SM/clk x 152 SMs x 2.07 GHz (GB300 FP64 is "
-                           "1/64 of FP32; float64 arithmetic binds this form, not HBM)",
-              "flops_per_launch": launch_flops, "algorithmic_bytes_per_launch": b64,
-              "achieved_gbs": gbs64, "hbm_frac": gbs64 / hbm}
-    roof32 = {"bound": "hbm", "achieved": gbs32, "peak": hbm, "unit": "GB/s",
-              "frac": gbs32 / hbm,
-              "traffic": NCU_TRAFFIC_PER_LAUNCH.get((args.workload, "split_fp32")),
-              "kernel": f"evolve_persist<{kname},7pt,split>",
-              "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-              "algorithmic_bytes_per_launch": b32,
-              "note": ("state fits in L2: the first stage of a step reads HBM (L2 flushed "
-                       "between steps), later stages of the step hit L2")
-              if S * nf * 4 * 4 < 120e6 else "state larger than L2"}
-
-    # e2e through the public API with host buffers (FP64 form)
+    # e2e through the public API with host buffers (FP64 form, headline workload)
     e2e = None
     if rank == 0 and not args.no_e2e:
         phi_pin = torch.from_numpy(phi).pin_memory().numpy()
@@ -506,7 +594,7 @@ def main():
     linear = None
     if rank == 0 and not args.no_linear:
         try:
-            lin = linear_leg(P, w, 100)
+            lin = linear_leg(P, w, 20)
             linear = {k: lin[k] for k in ("metric", "value", "unit", "distinct_k2", "lattice_modes",
                                           "steps", "seconds",
                                           "lattice_equivalent_site_updates_per_s", "finite")}
@@ -516,29 +604,25 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            cpu = cpu_baseline(w, phi, pi)
+            cpu = cpu_baseline(w)
+        f64 = head["forms"]["fp64"]
+        launches = sum(leg["forms"][f]["launches"] for leg in [head] + list(extra.values())
+                       for f in forms)
         line = {
-            "metric": METRIC, "value": r64, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot["fp64"] / args.steps,
+            "metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f64["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded spectral initial fluctuations, no dataset)",
-            "config": _config(w),
-            "roofline": roof64,
-            "forms": {
-                "fp64": {"value": r64, "unit": UNIT, "ms_per_step": tot["fp64"] / args.steps,
-                         "algorithmic_gbs": gbs64, "hbm_frac": gbs64 / hbm, "roofline": roof64,
-                         "status": res["fp64"]["status"]},
-                "split_fp32": {"value": r32, "unit": UNIT,
-                               "ms_per_step": tot["split_fp32"] / args.steps,
-                               "dtype": "f32 fluctuations + f64 background/sums",
-                               "roofline": roof32, "status": res["split_fp32"]["status"],
-                               "speedup_vs_fp64": r32 / r64},
-            },
+            "data": "synthetic (seeded white-noise / spectral initial fluctuations, no dataset)",
+            "config": head["config"],
+            "roofline": f64["roofline"],
+            "forms": head["forms"],
+            "extra": extra,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "serving": serving,
             "linear": linear,
-            "gpu_launches": int(l64 + l32),
+            "gpu_launches": int(launches),
+            "kernel_source_hash": kernel_source_hash(),
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -50,7 +50,8 @@ typedef enum {
   PYCOOL_E_TIMEOUT = 6,      /* a wait ran past its deadline                      */
   PYCOOL_E_STATE = 7,        /* call not valid in the current state               */
   PYCOOL_E_BUSY = 8,         /* server queue full                                 */
-  PYCOOL_E_NOT_FOUND = 9     /* unknown ticket                                    */
+  PYCOOL_E_NOT_FOUND = 9,    /* unknown ticket                                    */
+  PYCOOL_E_CANCELLED = 10    /* the request was cancelled before it finished      */
 } pycool_status;
 
 /* Potentials (Sec. 3).  params[] per model:
@@ -73,13 +74,27 @@ typedef enum {
  *                means phi0, pi0 in float64 and the fluctuations dphi, dpi
  *                stored and updated in float32; lattice sums, a and p_a in
  *                float64 (the homogeneous/perturbation split of Sec. 2.2,
- *                Eq. phi-lin, used here for precision, not linearisation). */
-typedef enum { PYCOOL_FP64 = 0, PYCOOL_SPLIT_FP32 = 1 } pycool_precision;
+ *                Eq. phi-lin, used here for precision, not linearisation).
+ *   SPLIT_DD   : the same split with the fluctuations stored and updated as
+ *                double-float pairs (hi + lo float32, ~48-bit significand,
+ *                8 bytes per value like FP64): float64-class accuracy with the
+ *                bulk arithmetic on the FP32 pipe (error-free transformations
+ *                TwoSum and the FMA-based TwoProduct).  Needs n a multiple of
+ *                32 (the persistent kernel); the server does not take it. */
+typedef enum { PYCOOL_FP64 = 0, PYCOOL_SPLIT_FP32 = 1, PYCOOL_SPLIT_DD = 2 } pycool_precision;
 
 /* Discrete Laplacian D of Sec. 2.1, Eq. D (its coefficients are not printed):
  *   7PT   : c = (-6, 1, 0, 0) for (centre, face, edge, corner) neighbours,
  *   ISO27 : c = (-128, 14, 3, 1)/30 (isotropic at O(k^4)). */
 typedef enum { PYCOOL_STENCIL_7PT = 7, PYCOOL_STENCIL_ISO27 = 27 } pycool_stencil;
+
+/* Time step rule.
+ *   CONFORMAL : every time step advances conformal time by dt (d-eta = dt).
+ *   PHYSICAL  : the adaptive conformal step of Sec. 3.1 -- each time step
+ *               advances physical time (dt_phys = a d-eta) by about dt:
+ *               d-eta = dt / a_n, a_n the scale factor of the synchronised
+ *               state that starts the step; all stages of the step use it. */
+typedef enum { PYCOOL_TIME_CONFORMAL = 0, PYCOOL_TIME_PHYSICAL = 1 } pycool_time_step;
 
 typedef struct {
   int32_t n;          /* lattice side, 1 <= n <= 1024; S = V_L = n^3 (Sec. 2.1)       */
@@ -87,9 +102,10 @@ typedef struct {
   int32_t order;      /* integrator order: 2, 4, 6 or 8                              */
   int32_t precision;  /* pycool_precision                                            */
   int32_t stencil;    /* pycool_stencil                                              */
-  int32_t reserved;   /* must be 0                                                   */
+  int32_t time_step;  /* pycool_time_step (0 = conformal)                            */
   double L;           /* comoving box side; dx = L/n                                 */
-  double dt;          /* conformal time step d-eta; may be negative (time reversal)  */
+  double dt;          /* time step (conformal d-eta, or physical dt: time_step);     */
+                      /* may be negative (time reversal)                             */
   double mpl;         /* reduced Planck mass in program units; +INF = static a       */
   double rho_rad0;    /* homogeneous radiation density today-units (Eq. H2)          */
   double rho_mat0;    /* homogeneous matter density (Eq. H2)                         */
@@ -175,6 +191,35 @@ pycool_status pycool_field_stats(pycool_sim* sim, int32_t field, double* mean,
  * set_initial; host copies synchronise first.  Either pointer may be NULL. */
 pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double* pi, int on_device);
 
+/* ---- output-interval observables (computed on the device) ------------------
+ * pycool_energy_fields: the energy density and pressure at every site of the
+ *   current synchronised state (synchronises first), Sec. 2.1 Eq. rho-pres
+ *   with the gradient terms from the stencil G of Eq. G and phi' = pi/a^2:
+ *     rho = sum_i [pi_i^2/(2 a^6) + G[phi_i]/(2 a^2 dx^2)] + V(phi)
+ *     P   = sum_i [pi_i^2/(2 a^6) - G[phi_i]/(6 a^2 dx^2)] - V(phi)
+ *     G[phi](x) = 1/2 sum_alpha c_d(alpha) (phi(alpha) - phi(x))^2
+ *   (c_d of the configured stencil).  Their lattice means are the rho and P
+ *   of pycool_energies (Stokes identity).  rho, P: n^3 float64 [z][y][x],
+ *   device pointers if on_device, else host (the call then allocates two
+ *   device arrays for the duration).
+ * pycool_spectrum_bins: number of shells of an n^3 lattice's spectrum,
+ *   floor(sqrt(3) n / 2) + 2 (-1 for a bad n).
+ * pycool_spectrum: the power spectrum of field `field` (which = 0) or of its
+ *   momentum (which = 1) at the current synchronised state (Sec. 2.4's field
+ *   spectra; the paper does not define them: this library's definition):
+ *     power[b] = sum over modes k with round(|m_k|) = b of |F_k|^2 / S^2,
+ *     count[b] = number of those modes (may be NULL),
+ *   F the unnormalised forward transform of the field, m_k the signed integer
+ *   wave vector; the shells add up to the lattice mean of the field squared.
+ *   power, count: host arrays of nbins = pycool_spectrum_bins(n).  The first
+ *   call makes an FFT plan and device buffers that the simulation keeps.
+ * Errors: E_INVALID (bad arguments), E_STATE (no synchronised state), E_NOMEM,
+ * E_CUDA, and the latched errors of pycool_sync. */
+pycool_status pycool_energy_fields(pycool_sim* sim, double* rho, double* P, int on_device);
+int32_t pycool_spectrum_bins(int32_t n);
+pycool_status pycool_spectrum(pycool_sim* sim, int32_t which, int32_t field, double* power,
+                              int64_t* count, int32_t nbins);
+
 /* Checkpoint of a synchronised state: the background record (eta, a, p_a,
  * step counters, split background phi0/pi0) and the current fields and
  * momenta in the sweep's own precision.  pycool_checkpoint_size gives the
@@ -237,12 +282,44 @@ pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int3
 /* The distinct k_eff^2 values of an n^3 lattice (host arithmetic only): the
  * symbol of -D (Eq. D, stencil PYCOOL_STENCIL_7PT or _ISO27) on every plane
  * wave exp(2 pi i m.x / n), m in numpy's FFT order ([z][y][x], x fastest);
- * values closer than 1e-12 (relative) count as one.
+ * values that follow their predecessor in the sorted list within 1e-12
+ * (relative to max(1, |v|)) count as one -- a chain of such values joins one
+ * group, so the tolerance is applied between neighbours, transitively.
  *   values (out, room for cap, may be NULL), ascending; count (out): how many;
  *   index (out, n^3 int32, may be NULL): each mode's position in values.
- * E_INVALID: bad n (1..1024) or stencil, count NULL, or cap too small. */
+ * The host work holds 2 n^3 doubles (the symbols and a sorted copy).
+ * E_INVALID: bad n (1..512) or stencil, count NULL, or cap too small. */
 pycool_status pycool_linear_modes(int32_t n, int32_t stencil, double* values, int64_t cap,
                                   int64_t* count, int32_t* index);
+
+/* The linearised evolution of lattice fields, end to end on the device
+ * (Sec. 2.2, Eqs. phi-lin, Phik-1, pert-evo; Sec. 2.4: growth functions per
+ * distinct k_eff^2, then a kernel that takes each Fourier position's matrix):
+ *   1. the background phi0, pi0 = lattice means (fixed-order device sums) and
+ *      the perturbations phi - phi0, pi - pi0 (Eq. phi-lin), written to
+ *      phi_out, pi_out as scratch;
+ *   2. forward real-to-complex FFTs of the perturbations (cuFFT), every
+ *      field, their k = 0 coefficients cleared;
+ *   3. the growth functions T of the distinct k_eff^2 values of the lattice's
+ *      stencil (pycool_linear_growth's kernel, background read on the device);
+ *   4. every mode (dPhi, dPi)_k <- T[k_eff^2(k)] (dPhi, dPi)_k / n^3, and the
+ *      k = 0 coefficient <- the evolved background;
+ *   5. inverse FFTs into phi_out, pi_out: background(eta) + perturbations(eta).
+ *   phi, pi (in) / phi_out, pi_out (out): device float64 [field][z][y][x],
+ *     N_f n^3 values each; the inputs are not modified; outputs must not
+ *     overlap the inputs.
+ *   a0 > 0, pa0 (finite): the initial scale factor and its momentum (e.g. the
+ *     p_a of pycool_energies for the same fields).
+ *   background (out, host, 2 + 2 N_f doubles): a, p_a, phi0[N_f], pi0[N_f] at
+ *     the end.
+ * The call allocates its device work space (spectra, tables, FFT plans),
+ * works on `cuda_stream` and synchronises it before returning.
+ * Errors: E_INVALID (bad config, n outside 2..512, bad pointers), E_NOMEM,
+ * E_CUDA.  The Q-ball's second derivatives need |Phi0| > 0 throughout. */
+pycool_status pycool_linear_evolve(const pycool_config* cfg, double a0, double pa0,
+                                   const double* phi, const double* pi, int64_t steps,
+                                   double* phi_out, double* pi_out, double* background,
+                                   void* cuda_stream);
 
 pycool_status pycool_linear_growth(const pycool_config* cfg, double a0, double pa0,
                                    const double* phi0, const double* pi0, const double* k2,
@@ -305,8 +382,35 @@ pycool_status pycool_server_wait(pycool_server* srv, uint64_t ticket, double tim
 pycool_status pycool_server_stats(pycool_server* srv, double* p50_s, double* p99_s,
                                   double* site_updates_per_s, int64_t* completed);
 
+/* Cancel a request.  A queued request is dropped at once; a resident one is
+ * retired at the server's next graph boundary (its launches complete first,
+ * its memory returns to the arena).  wait() then returns E_CANCELLED with the
+ * observables of the state it reached (all zero if it was never admitted).
+ * Returns OK, E_NOT_FOUND for an unknown or collected ticket, E_STATE if the
+ * request has finished already (collect it with wait).  Thread-safe. */
+pycool_status pycool_server_cancel(pycool_server* srv, uint64_t ticket);
+
 /* Stop the server thread and release every resident simulation and the arena. */
 void pycool_server_destroy(pycool_server* srv);
+
+/* ---- fault injection (tests of failure detection) ----------------------------
+ * Failures are made on the host or through a bounded device-side wait; nothing
+ * here traps or faults the GPU.  The paper has no counterpart.
+ *
+ * pycool_debug_fail_alloc: the next `count` device allocations the library
+ *   makes (pycool_create with NULL buffers, pycool_server_create's arena)
+ *   report failure as an exhausted cudaMalloc would: the call returns E_NOMEM
+ *   and leaves nothing allocated.  count = 0 clears it.  Process-wide.
+ * pycool_debug_barrier_stall: the simulation's next persistent launch (the
+ *   next pycool_evolve of a lattice with n a multiple of 32) waits at its
+ *   first grid barrier for one block more than the launch has -- an arrival
+ *   that never comes -- with every device-side wait limited to
+ *   wait_limit_clocks SM clocks.  Every block gives up at the limit, records
+ *   the fault and returns; pycool_sync then returns E_TIMEOUT and the
+ *   simulation is poisoned (E_STATE) while the CUDA context stays usable.
+ *   E_STATE if the simulation does not use the persistent kernel. */
+pycool_status pycool_debug_fail_alloc(int32_t count);
+pycool_status pycool_debug_barrier_stall(pycool_sim* sim, int64_t wait_limit_clocks);
 
 /* ---- allocation-free stage sweep ---------------------------------------------
  * The paper has no counterpart to this call; it is a deployment convenience.

@@ -29,23 +29,23 @@ MAX_PARAMS = 8
 
 # status codes (pycool_status)
 OK, E_INVALID, E_UNSTABLE_DT, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_BUSY, \
-    E_NOT_FOUND = range(10)
+    E_NOT_FOUND, E_CANCELLED = range(11)
 # models, precisions, stencils
 MODEL_FREE, MODEL_CHAOTIC2, MODEL_OSCILLON, MODEL_QBALL = range(4)
-FP64, SPLIT_FP32 = 0, 1
+FP64, SPLIT_FP32, SPLIT_DD = 0, 1, 2
 STENCIL_7PT, STENCIL_ISO27 = 7, 27
 IC_WHITE = 0
 
 MODELS = {"free": MODEL_FREE, "chaotic2": MODEL_CHAOTIC2, "oscillon": MODEL_OSCILLON,
           "qball": MODEL_QBALL}
 MODEL_NF = {MODEL_FREE: 1, MODEL_CHAOTIC2: 2, MODEL_OSCILLON: 1, MODEL_QBALL: 2}
-PRECISIONS = {"fp64": FP64, "split_fp32": SPLIT_FP32}
+PRECISIONS = {"fp64": FP64, "split_fp32": SPLIT_FP32, "split_dd": SPLIT_DD}
 STENCILS = {"7pt": STENCIL_7PT, "iso27": STENCIL_ISO27}
 
 
 class pycool_config(C.Structure):
     _fields_ = [("n", C.c_int32), ("model", C.c_int32), ("order", C.c_int32),
-                ("precision", C.c_int32), ("stencil", C.c_int32), ("reserved", C.c_int32),
+                ("precision", C.c_int32), ("stencil", C.c_int32), ("time_step", C.c_int32),
                 ("L", C.c_double), ("dt", C.c_double), ("mpl", C.c_double),
                 ("rho_rad0", C.c_double), ("rho_mat0", C.c_double),
                 ("params", C.c_double * MAX_PARAMS)]
@@ -113,6 +113,11 @@ def _load():
         "pycool_linear_modes": (S, [C.c_int32, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64), P]),
         "pycool_linear_growth": (S, [C.POINTER(pycool_config), C.c_double, C.c_double, P, P, P,
                                      C.c_int64, C.c_int64, P, P, P]),
+        "pycool_energy_fields": (S, [P, P, P, C.c_int]),
+        "pycool_spectrum_bins": (C.c_int32, [C.c_int32]),
+        "pycool_spectrum": (S, [P, C.c_int32, C.c_int32, P, P, C.c_int32]),
+        "pycool_linear_evolve": (S, [C.POINTER(pycool_config), C.c_double, C.c_double, P, P,
+                                     C.c_int64, P, P, P, P]),
         "pycool_persist_plan": (S, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                     C.POINTER(C.c_int32), P, C.c_int32, P, C.c_int32]),
         "pycool_destroy": (None, [P]),
@@ -124,6 +129,9 @@ def _load():
         "pycool_server_stats": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "pycool_server_destroy": (None, [P]),
+        "pycool_server_cancel": (S, [P, C.c_uint64]),
+        "pycool_debug_fail_alloc": (S, [C.c_int32]),
+        "pycool_debug_barrier_stall": (S, [P, C.c_int64]),
         "pycool_noalloc_max_blocks": (C.c_size_t, []),
         "pycool_sweep_noalloc": (S, [C.POINTER(pycool_config), P, P, P, P, C.c_int32,
                                      C.POINTER(pycool_stage_state), P]),
@@ -186,16 +194,19 @@ def _stream_ptr(stream) -> Optional[int]:
 
 # ---------------------------------------------------------------- config helpers
 
+TIME_STEPS = {"conformal": 0, "physical": 1}
+
+
 def make_config(n: int, L: float, model, params: Sequence[float], dt: float, order: int = 2,
                 precision="fp64", stencil="7pt", mpl: float = 1.0, rho_rad0: float = 0.0,
-                rho_mat0: float = 0.0) -> pycool_config:
+                rho_mat0: float = 0.0, time_step="conformal") -> pycool_config:
     c = pycool_config()
     c.n = int(n)
     c.model = MODELS[model] if isinstance(model, str) else int(model)
     c.order = int(order)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     c.stencil = STENCILS[stencil] if isinstance(stencil, str) else int(stencil)
-    c.reserved = 0
+    c.time_step = TIME_STEPS[time_step] if isinstance(time_step, str) else int(time_step)
     c.L, c.dt, c.mpl = float(L), float(dt), float(mpl)
     c.rho_rad0, c.rho_mat0 = float(rho_rad0), float(rho_mat0)
     for i, p in enumerate(params):
@@ -209,7 +220,8 @@ def config_from_workload(w: dict, **over) -> pycool_config:
     return make_config(n=w["n"], L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
                        order=w["order"], precision=w.get("precision", "fp64"),
                        stencil=w.get("stencil", "7pt"), mpl=w.get("mpl", 1.0),
-                       rho_rad0=w.get("rho_rad0", 0.0), rho_mat0=w.get("rho_mat0", 0.0))
+                       rho_rad0=w.get("rho_rad0", 0.0), rho_mat0=w.get("rho_mat0", 0.0),
+                       time_step=w.get("time_step", "conformal"))
 
 
 # ---------------------------------------------------------------- the C ABI, same names
@@ -354,6 +366,65 @@ def pycool_linear_growth(cfg: pycool_config, a0: float, pa0: float, phi0, pi0, k
     return T, (bg[0], bg[1], bg[2:2 + nf].copy(), bg[2 + nf:].copy())
 
 
+def pycool_linear_evolve(cfg: pycool_config, a0: float, pa0: float, phi, pi, steps: int,
+                         phi_out, pi_out, stream=None):
+    """The linearised evolution of lattice fields on the device: phi, pi,
+    phi_out, pi_out are contiguous float64 CUDA tensors of shape
+    (N_f, n, n, n).  Returns the final background (a, p_a, phi0, pi0)."""
+    import numpy as np
+    nf = MODEL_NF[int(cfg.model)]
+    need = nf * int(cfg.n) ** 3
+    for t in (phi, pi, phi_out, pi_out):
+        if not _is_field_tensor(t, need):
+            raise PycoolError(E_INVALID, "pycool_linear_evolve: arrays must be contiguous "
+                                         "float64 CUDA tensors of N_f n^3 elements")
+    bg = np.zeros(2 + 2 * nf)
+    _check(lib.pycool_linear_evolve(C.byref(cfg), float(a0), float(pa0), phi.data_ptr(),
+                                    pi.data_ptr(), int(steps), phi_out.data_ptr(),
+                                    pi_out.data_ptr(), bg.ctypes.data, _stream_ptr(stream)),
+           "pycool_linear_evolve")
+    return (bg[0], bg[1], bg[2:2 + nf].copy(), bg[2 + nf:].copy())
+
+
+def pycool_energy_fields(sim, shape_nnn, rho=None, P=None, on_device=False):
+    """rho(x), P(x) of the current synchronised state; host numpy arrays
+    (allocated here when not given) or CUDA float64 tensors (on_device)."""
+    import numpy as np
+    if on_device:
+        need = int(np.prod(shape_nnn))
+        for t in (rho, P):
+            if not _is_field_tensor(t, need):
+                raise PycoolError(E_INVALID, "pycool_energy_fields: rho and P must be "
+                                             "contiguous float64 CUDA tensors of n^3 elements")
+        _check(lib.pycool_energy_fields(sim, rho.data_ptr(), P.data_ptr(), 1),
+               "pycool_energy_fields")
+        return rho, P
+    rho = np.zeros(shape_nnn) if rho is None else rho
+    P = np.zeros(shape_nnn) if P is None else P
+    for a in (rho, P):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != np.prod(shape_nnn):
+            raise PycoolError(E_INVALID, "pycool_energy_fields: host arrays must be contiguous "
+                                         "float64 of n^3 elements")
+    _check(lib.pycool_energy_fields(sim, rho.ctypes.data, P.ctypes.data, 0),
+           "pycool_energy_fields")
+    return rho, P
+
+
+def pycool_spectrum_bins(n: int) -> int:
+    return int(lib.pycool_spectrum_bins(int(n)))
+
+
+def pycool_spectrum(sim, n: int, which: int, field: int):
+    """(power, count) of field `field` (which = 0) or its momentum (which = 1)."""
+    import numpy as np
+    nb = pycool_spectrum_bins(n)
+    power = np.zeros(nb)
+    count = np.zeros(nb, dtype=np.int64)
+    _check(lib.pycool_spectrum(sim, int(which), int(field), power.ctypes.data, count.ctypes.data,
+                               nb), "pycool_spectrum")
+    return power, count
+
+
 def pycool_persist_plan(n: int, nf: int, precision: int, sms: int, l2_bytes: int):
     """The persistent kernel's work plan (host only): (geo, units, uoff) with
     geo a dict, units an int32 array (units, 4) of (x0, y0, z0, planes + 2)
@@ -417,6 +488,22 @@ def pycool_server_stats(srv) -> dict:
 
 def pycool_server_destroy(srv) -> None:
     lib.pycool_server_destroy(srv)
+
+
+def pycool_server_cancel(srv, ticket: int) -> int:
+    """Cancel a request; returns the status code (OK, E_NOT_FOUND, E_STATE)."""
+    return lib.pycool_server_cancel(srv, int(ticket))
+
+
+def pycool_debug_fail_alloc(count: int) -> int:
+    """Fault injection: the next `count` device allocations of the library fail."""
+    return lib.pycool_debug_fail_alloc(int(count))
+
+
+def pycool_debug_barrier_stall(sim_handle, wait_limit_clocks: int) -> int:
+    """Fault injection: the next persistent launch waits at an unreachable grid
+    barrier with every wait limited to `wait_limit_clocks`; returns the status."""
+    return lib.pycool_debug_barrier_stall(sim_handle, int(wait_limit_clocks))
 
 
 def _is_field_tensor(t, numel: int) -> bool:
@@ -490,6 +577,12 @@ class Simulation:
 
     def kernel_launches(self) -> int:
         return pycool_kernel_launches(self.handle)
+
+    def energy_fields(self, rho=None, P=None, on_device=False):
+        return pycool_energy_fields(self.handle, self.shape[1:], rho, P, on_device)
+
+    def spectrum(self, which: int, field: int):
+        return pycool_spectrum(self.handle, self.n, which, field)
 
     def close(self):
         if self.handle:

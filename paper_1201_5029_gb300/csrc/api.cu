@@ -1,8 +1,10 @@
 // Host runtime behind include/pycool.h: simulation objects, device memory
 // layout, CUDA-graph replay of the sweep chain, observables, checkpoints.
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -134,8 +136,8 @@ PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
   // for a larger one.  The float64 form is bound by its arithmetic: h ~0.25.
   const double stage_bytes = 4.0 * nf * (double)n * n * n * word;   // phi, pi read and written
   const bool l2_resident = l2_bytes > 0 && stage_bytes <= 0.75 * (double)l2_bytes;
-  const double h = prec == PREC_FP64 ? 0.25 : (l2_resident ? 1.5 : 0.3);
-  const double pen = prec == PREC_FP64 ? 1.0 : 1.24;
+  const double h = prec != PREC_SPLIT ? 0.25 : (l2_resident ? 1.5 : 0.3);
+  const double pen = prec != PREC_SPLIT ? 1.0 : 1.24;
   constexpr int kMinPiece = 4;   // planes: no unit shorter than this is cut off a chunk
   const int cap = std::min(sms, kMaxPBlocks);
   auto is_wrap = [&](int t) {
@@ -285,12 +287,14 @@ PYCOOL_API pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t prec
                                              int32_t* units, int32_t cap_units, int32_t* uoff,
                                              int32_t cap_blocks) {
   if (n < 32 || n % 32 || (nf != 1 && nf != 2) || sms < 1 || l2_bytes < 0 || !geo ||
-      (precision != PYCOOL_FP64 && precision != PYCOOL_SPLIT_FP32))
+      (precision != PYCOOL_FP64 && precision != PYCOOL_SPLIT_FP32 &&
+       precision != PYCOOL_SPLIT_DD))
     return PYCOOL_E_INVALID;
-  const int prec = precision == PYCOOL_FP64 ? PREC_FP64 : PREC_SPLIT;
+  const int prec = precision == PYCOOL_FP64 ? PREC_FP64
+                   : (precision == PYCOOL_SPLIT_DD ? PREC_DD : PREC_SPLIT);
   std::vector<int4> u;
   std::vector<int> off;
-  const PGeo g = plan_units(n, prec == PREC_FP64 ? 8 : 4, nf, prec, sms, l2_bytes, &u, &off);
+  const PGeo g = plan_units(n, prec_word(prec), nf, prec, sms, l2_bytes, &u, &off);
   if (!check_plan(g, u, off)) return PYCOOL_E_INVALID;
   const int32_t vals[9] = {g.n, g.vx, g.tx, g.tiles_x, g.ntiles, g.rc, g.rw, g.nunits, g.G};
   for (int i = 0; i < 9; ++i) geo[i] = vals[i];
@@ -322,10 +326,13 @@ pycool_status validate(const pycool_config* c) {
   if (c->n < 1 || c->n > 1024) return PYCOOL_E_INVALID;
   if (model_nfields(c->model) < 0) return PYCOOL_E_INVALID;
   if (c->order != 2 && c->order != 4 && c->order != 6 && c->order != 8) return PYCOOL_E_INVALID;
-  if (c->precision != PYCOOL_FP64 && c->precision != PYCOOL_SPLIT_FP32) return PYCOOL_E_INVALID;
+  if (c->precision != PYCOOL_FP64 && c->precision != PYCOOL_SPLIT_FP32 &&
+      c->precision != PYCOOL_SPLIT_DD)
+    return PYCOOL_E_INVALID;
   if (c->stencil != PYCOOL_STENCIL_7PT && c->stencil != PYCOOL_STENCIL_ISO27)
     return PYCOOL_E_INVALID;
-  if (c->reserved != 0) return PYCOOL_E_INVALID;
+  if (c->time_step != PYCOOL_TIME_CONFORMAL && c->time_step != PYCOOL_TIME_PHYSICAL)
+    return PYCOOL_E_INVALID;
   if (!(c->L > 0.0) || !std::isfinite(c->L)) return PYCOOL_E_INVALID;
   if (!std::isfinite(c->dt) || c->dt == 0.0) return PYCOOL_E_INVALID;
   if (!(c->mpl > 0.0)) return PYCOOL_E_INVALID;
@@ -352,8 +359,10 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.nf = model_nfields(c.model);
   d.model = c.model;
   d.stencil = c.stencil;
-  d.prec = c.precision == PYCOOL_SPLIT_FP32 ? PREC_SPLIT : PREC_FP64;
+  d.prec = c.precision == PYCOOL_SPLIT_FP32 ? PREC_SPLIT
+           : (c.precision == PYCOOL_SPLIT_DD ? PREC_DD : PREC_FP64);
   d.nstages = stage_table(c.order, d.w);
+  d.physical = c.time_step == PYCOOL_TIME_PHYSICAL ? 1 : 0;
   d.tma = L.geo.tma; d.vx = L.geo.vx; d.txt = L.geo.txt;
   d.tx = L.geo.tx; d.ty = L.geo.ty; d.zc = L.geo.zc;
   d.tiles_x = L.geo.tiles_x; d.tiles_y = L.geo.tiles_y;
@@ -471,11 +480,14 @@ cudaError_t encode_persist_maps(const SimDesc& d, const PGeo& g, PParams& p) {
 
 cudaError_t launch_persist(const SimDesc& d, const PParams& p, int grid, cudaStream_t s, int* bps) {
   if (d.prec == PREC_SPLIT) return launch_persist_split(d.model, d.stencil, p.g.vx, p, grid, s, bps);
+  if (d.prec == PREC_DD) return launch_persist_dd(d.model, d.stencil, p.g.vx, p, grid, s, bps);
   return launch_persist_fp64(d.model, d.stencil, p.g.vx, p, grid, s, bps);
 }
 
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s) {
   if (d.prec == PREC_SPLIT) return launch_sweep_split(d.model, d.stencil, d.vx, d.tma, t, grid, s);
+  // the split-DD form runs on the persistent kernel only (no per-stage instance)
+  if (d.prec == PREC_DD) return grid == 0 ? cudaSuccess : cudaErrorInvalidValue;
   return launch_sweep_fp64(d.model, d.stencil, d.vx, d.tma, t, grid, s);
 }
 
@@ -491,6 +503,17 @@ __global__ void split_combine_kernel(const float* __restrict__ d, double base0, 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     out[i] = (i < S ? base0 : base1) + (double)d[i];
+  }
+}
+
+// split-DD: background + (hi + lo), evaluated in float64
+__global__ void dd_combine_kernel(const float2* __restrict__ d, double base0, double base1,
+                                  double* __restrict__ out, long long S, int nf) {
+  const long long total = S * nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = d[i];
+    out[i] = (i < S ? base0 : base1) + ((double)v.x + (double)v.y);
   }
 }
 
@@ -560,9 +583,46 @@ struct pycool_sim {
   // evolve(); otherwise a chain of per-stage launches replayed as a graph
   bool persist = false;
   PParams pp{};
+  long long stall_limit = 0;   // > 0: the next persistent launch is a fault test
+  // spectrum (made at the first pycool_spectrum call): FFT plan, buffers and
+  // the half-spectrum modes ordered by shell
+  bool spec_ready = false;
+  cufftHandle spec_plan = 0;
+  double* spec_tmp = nullptr;       // n^3 float64 field
+  void* spec_out = nullptr;         // n n (n/2 + 1) complex coefficients
+  int32_t* spec_order = nullptr;    // half-spectrum modes grouped by shell
+  int32_t* spec_start = nullptr;    // shell b: spec_order[spec_start[b] .. spec_start[b + 1])
+  double* spec_power = nullptr;     // per shell
+  std::vector<int64_t> spec_count;  // modes per shell over the full spectrum
 };
 
 static constexpr int kGraphLen = 16;
+
+// Host-side fault injection: the next `count` device allocations the library
+// makes report failure, as a cudaMalloc that ran out of memory would.
+static std::atomic<int> g_fail_allocs{0};
+
+namespace pycool {
+bool injected_alloc_failure() {
+  int c = g_fail_allocs.load();
+  while (c > 0)
+    if (g_fail_allocs.compare_exchange_weak(c, c - 1)) return true;
+  return false;
+}
+}  // namespace pycool
+
+PYCOOL_API pycool_status pycool_debug_fail_alloc(int32_t count) {
+  if (count < 0) return PYCOOL_E_INVALID;
+  g_fail_allocs.store(count);
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_debug_barrier_stall(pycool_sim* sim, int64_t wait_limit_clocks) {
+  if (!sim || wait_limit_clocks <= 0) return PYCOOL_E_INVALID;
+  if (!sim->persist) return PYCOOL_E_STATE;   // only the persistent kernel has a grid barrier
+  sim->stall_limit = (long long)wait_limit_clocks;
+  return PYCOOL_OK;
+}
 
 static pycool_status cuda_fail(pycool_sim* s, cudaError_t e, const char* what) {
   if (s) s->poisoned = true;
@@ -620,7 +680,7 @@ static pycool_status build_graph(pycool_sim* sim) {
 static pycool_status setup_persist(pycool_sim* sim) {
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
-  const int word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  const int word = prec_word(sim->hdesc.prec);
   std::vector<int4> units;
   std::vector<int> uoff;
   int l2 = 0;
@@ -646,6 +706,8 @@ static pycool_status setup_persist(pycool_sim* sim) {
   p.bar_base = 0;
   p.rows = sim->ws + sim->L.off_prows;
   p.fault = sim->hdesc.fault;
+  p.wait_limit = kWaitLimit;
+  p.bar_extra = 0;
   int bps = 0;
   CK(launch_persist(sim->hdesc, p, 0, sim->stream, &bps));
   sim->persist = bps >= 1 && g.G <= bps * sms;
@@ -657,7 +719,18 @@ static pycool_status setup_persist(pycool_sim* sim) {
 // tracks how many arrivals earlier launches made.
 static pycool_status launch_persist_sweeps(pycool_sim* sim, long long nsweeps) {
   sim->pp.nsweeps = nsweeps;
-  CK(launch_persist(sim->hdesc, sim->pp, sim->pp.g.G, sim->stream, nullptr));
+  if (sim->stall_limit > 0) {
+    // fault test (pycool_debug_barrier_stall): this launch's first grid
+    // barrier waits for one arrival more than there are blocks, with a short
+    // limit; every block gives up, records the fault and returns
+    PParams q = sim->pp;
+    q.wait_limit = sim->stall_limit;
+    q.bar_extra = 1;
+    sim->stall_limit = 0;
+    CK(launch_persist(sim->hdesc, q, q.g.G, sim->stream, nullptr));
+  } else {
+    CK(launch_persist(sim->hdesc, sim->pp, sim->pp.g.G, sim->stream, nullptr));
+  }
   sim->pp.bar_base += (unsigned long long)(nsweeps + 1) * (unsigned long long)sim->pp.g.G;
   sim->launches += 1;
   return PYCOOL_OK;
@@ -682,7 +755,8 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
   sim->state = (char*)dev_state;
   sim->ws = (char*)dev_workspace;
   if (!sim->state) {
-    if (cudaMalloc((void**)&sim->state, sim->L.state_bytes) != cudaSuccess) {
+    if (injected_alloc_failure() ||
+        cudaMalloc((void**)&sim->state, sim->L.state_bytes) != cudaSuccess) {
       cudaGetLastError();
       delete sim;
       return PYCOOL_E_NOMEM;
@@ -690,7 +764,7 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
     sim->own_state = true;
   }
   if (!sim->ws) {
-    if (cudaMalloc((void**)&sim->ws, sim->L.ws_bytes) != cudaSuccess) {
+    if (injected_alloc_failure() || cudaMalloc((void**)&sim->ws, sim->L.ws_bytes) != cudaSuccess) {
       cudaGetLastError();
       if (sim->own_state) cudaFree(sim->state);
       delete sim;
@@ -749,6 +823,11 @@ PYCOOL_API pycool_status pycool_create(const pycool_config* cfg, void* dev_state
       return st;
     }
   }
+  if (!sim->persist && sim->hdesc.prec == PREC_DD) {
+    // the split-DD form has only the persistent kernel (n a multiple of 32)
+    pycool_destroy(sim);
+    return PYCOOL_E_INVALID;
+  }
   if (!sim->persist) {
     st = build_graph(sim);
     if (st != PYCOOL_OK) {
@@ -805,7 +884,10 @@ PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, 
       sp = hphi.data();
       sq = hpi.data();
     }
-    std::vector<float> dphi(count), dpi(count);
+    // (split-DD: the fluctuation as a double-float pair hi + lo, 8 bytes)
+    const bool pair = sim->hdesc.prec == PREC_DD;
+    const size_t per = pair ? 2 : 1;
+    std::vector<float> dphi(count * per), dpi(count * per);
     for (int f = 0; f < nf; ++f) {
       for (int which = 0; which < 2; ++which) {
         const double* src = (which == 0 ? sp : sq) + (size_t)f * S;
@@ -816,13 +898,24 @@ PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, 
           s = t;
         }
         const double mean = (s + comp) / (double)S;
-        float* dst = (which == 0 ? dphi.data() : dpi.data()) + (size_t)f * S;
-        for (size_t i = 0; i < S; ++i) dst[i] = (float)(src[i] - mean);
+        float* dst = (which == 0 ? dphi.data() : dpi.data()) + (size_t)f * S * per;
+        for (size_t i = 0; i < S; ++i) {
+          const double x = src[i] - mean;
+          if (pair) {
+            const float hi = (float)x;
+            dst[2 * i] = hi;
+            dst[2 * i + 1] = (float)(x - (double)hi);
+          } else {
+            dst[i] = (float)x;
+          }
+        }
         if (which == 0) b.phi0[f] = mean; else b.pi0[f] = mean;
       }
     }
-    CK(cudaMemcpy(sim->hdesc.phi[0], dphi.data(), count * sizeof(float), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(sim->hdesc.pi[0], dpi.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sim->hdesc.phi[0], dphi.data(), dphi.size() * sizeof(float),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sim->hdesc.pi[0], dpi.data(), dpi.size() * sizeof(float),
+                  cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
   CK(cudaMemsetAsync(sim->ws, 0, sim->L.off_partials, sim->stream));
@@ -935,25 +1028,34 @@ PYCOOL_API pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double*
     CK(cudaStreamSynchronize(sim->stream));
     return b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK;
   }
-  // split: phi0 + dphi evaluated in float64
+  // split forms: phi0 + dphi evaluated in float64 (split-DD: dphi = hi + lo)
+  const bool pair = sim->hdesc.prec == PREC_DD;
   for (int which = 0; which < 2; ++which) {
     double* dst = which == 0 ? phi : pi;
     if (!dst) continue;
     const float* src = (const float*)(which == 0 ? src_phi : src_pi);
     const double* base = which == 0 ? b.phi0 : b.pi0;
     if (on_device) {
-      split_combine_kernel<<<1024, 256, 0, sim->stream>>>(src, base[0], base[1], dst,
-                                                          (long long)S, sim->nf);
+      if (pair)
+        dd_combine_kernel<<<1024, 256, 0, sim->stream>>>((const float2*)src, base[0], base[1],
+                                                         dst, (long long)S, sim->nf);
+      else
+        split_combine_kernel<<<1024, 256, 0, sim->stream>>>(src, base[0], base[1], dst,
+                                                            (long long)S, sim->nf);
       CK(cudaGetLastError());
       sim->launches += 1;
       CK(cudaStreamSynchronize(sim->stream));
     } else {
-      std::vector<float> tmp(count);
-      CK(cudaMemcpyAsync(tmp.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost,
+      std::vector<float> tmp(count * (pair ? 2 : 1));
+      CK(cudaMemcpyAsync(tmp.data(), src, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost,
                          sim->stream));
       CK(cudaStreamSynchronize(sim->stream));
       for (int f = 0; f < sim->nf; ++f)
-        for (size_t i = 0; i < S; ++i) dst[(size_t)f * S + i] = base[f] + (double)tmp[(size_t)f * S + i];
+        for (size_t i = 0; i < S; ++i) {
+          const size_t e = (size_t)f * S + i;
+          const double v = pair ? (double)tmp[2 * e] + (double)tmp[2 * e + 1] : (double)tmp[e];
+          dst[e] = base[f] + v;
+        }
     }
   }
   return b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK;
@@ -961,7 +1063,7 @@ PYCOOL_API pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double*
 
 PYCOOL_API pycool_status pycool_checkpoint_size(pycool_sim* sim, size_t* size) {
   if (!sim || !size) return PYCOOL_E_INVALID;
-  const size_t word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  const size_t word = prec_word(sim->hdesc.prec);
   *size = sizeof(Background) + 2 * (size_t)sim->nf * (size_t)sim->hdesc.S * word;
   return PYCOOL_OK;
 }
@@ -978,7 +1080,7 @@ PYCOOL_API pycool_status pycool_checkpoint_save(pycool_sim* sim, void* buf, size
   st = read_bg(sim, &b);
   if (st != PYCOOL_OK) return st;
   if (b.mode != MODE_IDLE) return PYCOOL_E_STATE;
-  const size_t word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  const size_t word = prec_word(sim->hdesc.prec);
   const size_t fb = (size_t)sim->nf * (size_t)sim->hdesc.S * word;
   char* p = (char*)buf;
   std::memcpy(p, &b, sizeof(b));
@@ -996,7 +1098,7 @@ PYCOOL_API pycool_status pycool_checkpoint_load(pycool_sim* sim, const void* buf
   Background b;
   std::memcpy(&b, buf, sizeof(b));
   if (b.mode != MODE_IDLE || b.error) return PYCOOL_E_INVALID;
-  const size_t word = sim->hdesc.prec == PREC_SPLIT ? 4 : 8;
+  const size_t word = prec_word(sim->hdesc.prec);
   const size_t fb = (size_t)sim->nf * (size_t)sim->hdesc.S * word;
   const char* p = (const char*)buf;
   CK(cudaStreamSynchronize(sim->stream));
@@ -1007,6 +1109,119 @@ PYCOOL_API pycool_status pycool_checkpoint_load(pycool_sim* sim, const void* buf
   sim->pp.bar_base = 0;
   CK(cudaEventRecord(sim->done, sim->stream));
   sim->initialised = true;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API int32_t pycool_spectrum_bins(int32_t n) {
+  if (n < 1 || n > 1024) return -1;
+  return (int32_t)std::floor(std::sqrt(3.0) * n / 2.0) + 2;
+}
+
+// The synchronised state that the observables read.
+static pycool_status observed_state(pycool_sim* sim, Background* b) {
+  if (!sim->initialised) return PYCOOL_E_STATE;
+  pycool_status st = pycool_sync(sim, -1.0);
+  if (st != PYCOOL_OK) return st;
+  st = read_bg(sim, b);
+  if (st != PYCOOL_OK) return st;
+  return b->mode == MODE_IDLE ? PYCOOL_OK : PYCOOL_E_STATE;
+}
+
+PYCOOL_API pycool_status pycool_energy_fields(pycool_sim* sim, double* rho, double* P,
+                                              int on_device) {
+  if (!sim || !rho || !P) return PYCOOL_E_INVALID;
+  if (sim->poisoned) return PYCOOL_E_STATE;
+  Background b;
+  pycool_status st = observed_state(sim, &b);
+  if (st != PYCOOL_OK) return st;
+  const size_t bytes = (size_t)sim->hdesc.S * sizeof(double);
+  if (on_device) {
+    CK(launch_energy_fields(sim->hdesc, b, rho, P, sim->stream));
+    sim->launches += 1;
+    CK(cudaStreamSynchronize(sim->stream));
+    return PYCOOL_OK;
+  }
+  double *dr = nullptr, *dp = nullptr;
+  if (injected_alloc_failure() || cudaMalloc((void**)&dr, bytes) != cudaSuccess ||
+      cudaMalloc((void**)&dp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dr);
+    return PYCOOL_E_NOMEM;
+  }
+  cudaError_t e = launch_energy_fields(sim->hdesc, b, dr, dp, sim->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, bytes, cudaMemcpyDeviceToHost, sim->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P, dp, bytes, cudaMemcpyDeviceToHost, sim->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+  cudaFree(dr);
+  cudaFree(dp);
+  if (e != cudaSuccess) return cuda_fail(sim, e, "pycool_energy_fields");
+  sim->launches += 1;
+  return PYCOOL_OK;
+}
+
+// Shell of each half-spectrum mode, the modes grouped by shell (counting
+// sort: ascending index within a shell), the FFT plan and the buffers.
+static pycool_status spectrum_setup(pycool_sim* sim) {
+  const int n = sim->cfg.n, nh = n / 2 + 1, nb = pycool_spectrum_bins(n);
+  const size_t half = (size_t)n * n * nh;
+  std::vector<int32_t> shell(half), start(nb + 1, 0), order(half);
+  sim->spec_count.assign(nb, 0);
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < nh; ++x) {
+        const long long mz = z <= n / 2 ? z : z - n, my = y <= n / 2 ? y : y - n;
+        const long long r2 = mz * mz + my * my + (long long)x * x;
+        const int b = (int)std::lround(std::sqrt((double)r2));
+        const size_t m = ((size_t)z * n + y) * nh + x;
+        shell[m] = b;
+        start[b + 1] += 1;
+        sim->spec_count[b] += (x > 0 && 2 * x != n) ? 2 : 1;
+      }
+  for (int b = 0; b < nb; ++b) start[b + 1] += start[b];
+  std::vector<int32_t> fill(start.begin(), start.end() - 1);
+  for (size_t m = 0; m < half; ++m) order[fill[shell[m]]++] = (int32_t)m;
+  if (injected_alloc_failure() ||
+      cudaMalloc((void**)&sim->spec_tmp, (size_t)sim->hdesc.S * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sim->spec_out, half * sizeof(cufftDoubleComplex)) != cudaSuccess ||
+      cudaMalloc((void**)&sim->spec_order, half * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc((void**)&sim->spec_start, (nb + 1) * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc((void**)&sim->spec_power, nb * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return PYCOOL_E_NOMEM;
+  }
+  CK(cudaMemcpy(sim->spec_order, order.data(), half * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->spec_start, start.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (cufftPlan3d(&sim->spec_plan, n, n, n, CUFFT_D2Z) != CUFFT_SUCCESS) return PYCOOL_E_CUDA;
+  sim->spec_ready = true;
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_spectrum(pycool_sim* sim, int32_t which, int32_t field,
+                                         double* power, int64_t* count, int32_t nbins) {
+  if (!sim || !power || (which != 0 && which != 1) || field < 0 || field >= sim->nf ||
+      nbins != pycool_spectrum_bins(sim->cfg.n))
+    return PYCOOL_E_INVALID;
+  if (sim->poisoned) return PYCOOL_E_STATE;
+  Background b;
+  pycool_status st = observed_state(sim, &b);
+  if (st != PYCOOL_OK) return st;
+  if (!sim->spec_ready) {
+    st = spectrum_setup(sim);
+    if (st != PYCOOL_OK) return st;
+  }
+  if (cufftSetStream(sim->spec_plan, sim->stream) != CUFFT_SUCCESS) return PYCOOL_E_CUDA;
+  CK(launch_field_values(sim->hdesc, b, which, field, sim->spec_tmp, sim->stream));
+  if (cufftExecD2Z(sim->spec_plan, sim->spec_tmp, (cufftDoubleComplex*)sim->spec_out) !=
+      CUFFT_SUCCESS)
+    return PYCOOL_E_CUDA;
+  CK(launch_spectrum_bins(sim->spec_out, sim->cfg.n, sim->spec_order, sim->spec_start, nbins,
+                          sim->spec_power, sim->stream));
+  CK(cudaMemcpyAsync(power, sim->spec_power, nbins * sizeof(double), cudaMemcpyDeviceToHost,
+                     sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  sim->launches += 2;
+  if (count)
+    for (int i = 0; i < nbins; ++i) count[i] = sim->spec_count[i];
   return PYCOOL_OK;
 }
 
@@ -1025,6 +1240,12 @@ PYCOOL_API pycool_status pycool_set_stream(pycool_sim* sim, void* cuda_stream) {
 PYCOOL_API void pycool_destroy(pycool_sim* sim) {
   if (!sim) return;
   cudaStreamSynchronize(sim->stream);
+  if (sim->spec_ready) cufftDestroy(sim->spec_plan);
+  cudaFree(sim->spec_tmp);
+  cudaFree(sim->spec_out);
+  cudaFree(sim->spec_order);
+  cudaFree(sim->spec_start);
+  cudaFree(sim->spec_power);
   if (sim->graph) cudaGraphExecDestroy(sim->graph);
   if (sim->done) cudaEventDestroy(sim->done);
   if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
@@ -1046,6 +1267,7 @@ PYCOOL_API const char* pycool_strerror(pycool_status s) {
     case PYCOOL_E_STATE: return "call not valid in the current state";
     case PYCOOL_E_BUSY: return "busy";
     case PYCOOL_E_NOT_FOUND: return "unknown ticket";
+    case PYCOOL_E_CANCELLED: return "request cancelled";
   }
   return "unknown status";
 }

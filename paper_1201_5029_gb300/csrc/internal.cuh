@@ -25,9 +25,15 @@ constexpr int kMaxTY = 8;          // tile height (y)
 constexpr int kNQ = 12;            // reduction slots per block
 constexpr int kMaxMembers = 64;    // simulations per batched launch
 constexpr int kGroup = 32;         // blocks per first-level fold group
+constexpr long long kWaitLimit = 1ll << 31;   // default limit of a device-side wait
+                                              // (SM clocks, about a second)
 
 enum Mode : int32_t { MODE_IDLE = 0, MODE_SWEEP = 1, MODE_FLUSH = 2 };
-enum Prec : int32_t { PREC_FP64 = 0, PREC_SPLIT = 1 };
+// PREC_DD: the split form with double-float fluctuations (float pairs, 8 bytes
+// per value) -- float64-class accuracy, arithmetic on the FP32 pipe.
+enum Prec : int32_t { PREC_FP64 = 0, PREC_SPLIT = 1, PREC_DD = 2 };
+// bytes per stored field value
+constexpr int prec_word(int prec) { return prec == PREC_SPLIT ? 4 : 8; }
 
 // Mutable background record.  a, p_a, eta and the pending half-stage are the
 // scalar part of the state (Sec. 2.3, Eq. split-Phi: Phi_H1 moves a, Phi_H2 and
@@ -53,7 +59,8 @@ struct alignas(16) Background {
   // Split form: lattice-mean background and pending re-centring shifts.
   double phi0[kMaxFields], pi0[kMaxFields];
   double mu_phi[kMaxFields], mu_pi[kMaxFields];
-  double pad[4];
+  double deta;               // conformal step of the running time step (physical-time steps)
+  double pad[3];
 };
 
 struct alignas(64) SimDesc {
@@ -62,6 +69,7 @@ struct alignas(64) SimDesc {
   // The tensor is the buffer viewed as x: n, y: n, z: N_f n (fields stacked in z).
   CUtensorMap tmap[4][2];
   int32_t n, nf, model, stencil, prec, nstages;
+  int32_t physical;           // 1: physical-time steps, d-eta = dt / a per step (Sec. 3.1)
   int32_t tma;                // 1: TMA-staged kernel (n % 32 == 0), 0: plain loads
   int32_t vx;                 // sites per thread along x (TMA kernel)
   int32_t txt;                // threads per tile row
@@ -168,6 +176,9 @@ struct PParams {
   int32_t* fault;
   PGeo g;
   long long nsweeps;       // stage sweeps of this launch (then one flush)
+  long long wait_limit;    // clocks after which a device-side wait gives up
+  unsigned long long bar_extra;  // added to every grid-barrier target: 0, or 1 to
+                                 // make the first barrier unreachable (fault test)
 };
 
 // The persistent geometry and its unit table (units grouped by block; off has
@@ -185,5 +196,7 @@ cudaError_t launch_persist_fp64(int model, int stencil, int vx, const PParams& p
                                 cudaStream_t s, int* bps);
 cudaError_t launch_persist_split(int model, int stencil, int vx, const PParams& p, int grid,
                                  cudaStream_t s, int* bps);
+cudaError_t launch_persist_dd(int model, int stencil, int vx, const PParams& p, int grid,
+                              cudaStream_t s, int* bps);
 
 }  // namespace pycool

@@ -14,6 +14,8 @@
 // thread evolves the (identical) background itself, so threads never wait on
 // one another; the work is FP64 scalar arithmetic, a few hundred operations
 // per stage and k_eff^2 value.
+#include <cufft.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -30,6 +32,7 @@ struct LinArgs {
   long long nk;
   double* T;              // out: nk x (2N_f)^2, row-major (rows dPhi_0.., dPi_0..)
   double* bg;             // out: a, p_a, phi0[N_f], pi0[N_f] (written by thread 0)
+  const double* bg_in;    // device: initial phi0[N_f], pi0[N_f] (NULL: the fields below)
   double a0, pa0, phi0[2], pi0[2];
   double w[kMaxStages];
   int nstages;
@@ -80,7 +83,10 @@ __global__ void __launch_bounds__(128) linear_growth(const LinArgs a) {
   const double q = a.k2[k] * a.dx2inv;   // k_eff^2 / dx^2
   double A = a.a0, PA = a.pa0, f0[NF], p0[NF], T[N2][N2];
 #pragma unroll
-  for (int i = 0; i < NF; ++i) { f0[i] = a.phi0[i]; p0[i] = a.pi0[i]; }
+  for (int i = 0; i < NF; ++i) {
+    f0[i] = a.bg_in ? a.bg_in[i] : a.phi0[i];
+    p0[i] = a.bg_in ? a.bg_in[NF + i] : a.pi0[i];
+  }
 #pragma unroll
   for (int r = 0; r < N2; ++r)
 #pragma unroll
@@ -153,19 +159,108 @@ cudaError_t launch_linear_growth(int model, const LinArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-}  // namespace pycool
+// The background of lattice fields (Eq. phi-lin): the lattice means of the
+// 2 N_f arrays phi_0..phi_{N-1}, pi_0.. (src[j] = array j, S values each),
+// summed in a fixed order -- per block a strided range and a fixed tree, then
+// the block sums in order by one block -- so the means are reproducible.
+constexpr int kMeanBlocks = 128;
+__global__ void __launch_bounds__(256) linear_means_partial(const double* const* src, long long S,
+                                                            double* part) {
+  __shared__ double red[256];
+  const int j = blockIdx.y;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < S; i += (long long)kMeanBlocks * 256)
+    acc += src[j][i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)j * kMeanBlocks + blockIdx.x] = red[0];
+}
+__global__ void linear_means_fold(const double* part, int narr, double invS, double* bg_in) {
+  const int j = threadIdx.x;   // one thread per array
+  if (j >= narr) return;
+  double s = 0.0;
+  for (int b = 0; b < kMeanBlocks; ++b) s += part[(size_t)j * kMeanBlocks + b];
+  bg_in[j] = s * invS;         // [phi0_0 .. phi0_{N_f-1}, pi0_0 ..]
+}
+// dst_f = src_f - mean_f (the perturbations, Eq. phi-lin), into the output
+// arrays that later receive the evolved fields
+__global__ void linear_subtract(const double* const* src, double* const* dst, long long S,
+                                int narr, const double* bg_in) {
+  const long long total = S * narr;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / S);
+    const long long e = i - (long long)j * S;
+    dst[j][e] = src[j][e] - bg_in[j];
+  }
+}
+// the k = 0 coefficients of the perturbations (zero up to rounding) cleared
+__global__ void linear_clear_mean(cufftDoubleComplex* spec, long long half, int nf) {
+  const int i = threadIdx.x;
+  if (i >= 2 * nf) return;
+  spec[(size_t)i * half].x = 0.0;
+  spec[(size_t)i * half].y = 0.0;
+}
 
-using namespace pycool;
+// Each Fourier mode of the perturbations at the later time from its initial
+// value (Sec. 2.2, after Eq. Phik-1): y(eta) = T[k_eff^2 of the mode] y(0),
+// y = (dPhi_1..dPhi_N, dPi_1..dPi_N), T real, scaled by 1/S for the
+// unnormalised inverse transform; the k = 0 coefficient becomes the evolved
+// background, so the inverse transform gives background + perturbations.
+template <int NF>
+__global__ void __launch_bounds__(256) linear_apply(cufftDoubleComplex* __restrict__ spec,
+                                                    long long half,
+                                                    const int32_t* __restrict__ index,
+                                                    const double* __restrict__ T,
+                                                    const double* __restrict__ bg_end, double invS) {
+  constexpr int N2 = 2 * NF;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < half;
+       m += (long long)gridDim.x * blockDim.x) {
+    cufftDoubleComplex y[N2], r[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) y[j] = spec[(size_t)j * half + m];
+    if (m == 0) {
+#pragma unroll
+      for (int j = 0; j < N2; ++j) { r[j].x = bg_end[2 + j]; r[j].y = 0.0; }
+    } else {
+      const double* t = T + (size_t)__ldg(&index[m]) * N2 * N2;
+#pragma unroll
+      for (int i = 0; i < N2; ++i) {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const double tij = __ldg(&t[i * N2 + j]);
+          re = fma(tij, y[j].x, re);
+          im = fma(tij, y[j].y, im);
+        }
+        r[i].x = re * invS;
+        r[i].y = im * invS;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < N2; ++j) spec[(size_t)j * half + m] = r[j];
+  }
+}
 
-// The distinct values of k_eff^2 (the symbol of -D on plane waves, Eq. D)
-// over the n^3 lattice modes, and each mode's index into them.  Values that
-// differ by less than 1e-12 (equal symbols reached through different cosines)
-// count as one.
-extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_modes(
-    int32_t n, int32_t stencil, double* values, int64_t cap, int64_t* count, int32_t* index) {
-  if (n < 1 || n > 1024 || !count || cap < 0 ||
-      (stencil != PYCOOL_STENCIL_7PT && stencil != PYCOOL_STENCIL_ISO27))
-    return PYCOOL_E_INVALID;
+cudaError_t launch_linear_apply(int nf, cufftDoubleComplex* spec, long long half,
+                                const int32_t* index, const double* T, const double* bg_end,
+                                double invS, cudaStream_t s) {
+  const long long want = (half + 255) / 256;
+  const unsigned grid = (unsigned)std::min<long long>(want, 152LL * 16);
+  if (nf == 1)
+    linear_apply<1><<<grid, 256, 0, s>>>(spec, half, index, T, bg_end, invS);
+  else
+    linear_apply<2><<<grid, 256, 0, s>>>(spec, half, index, T, bg_end, invS);
+  return cudaGetLastError();
+}
+
+// The distinct k_eff^2 values (ascending) of an n^3 lattice and each mode's
+// index into them (modes in numpy FFT order, [z][y][x]).
+bool linear_modes_host(int n, int stencil, std::vector<double>& vals, std::vector<int32_t>* index) {
   // coefficients by neighbour class (number of non-zero offsets), Eq. D
   const double c7[4] = {-6.0, 1.0, 0.0, 0.0};
   const double c27[4] = {-128.0 / 30.0, 14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0};
@@ -189,22 +284,43 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_mo
       }
   std::vector<double> sorted(k2);
   std::sort(sorted.begin(), sorted.end());
-  std::vector<double> vals;
+  vals.clear();
   for (double v : sorted)
     if (vals.empty() || v - vals.back() > 1e-12 * std::fmax(1.0, std::fabs(v))) vals.push_back(v);
+  if (index) {
+    index->resize(S);
+    for (size_t i = 0; i < S; ++i) {
+      // the last value not above k2[i] + tolerance
+      const double v = k2[i];
+      auto it = std::upper_bound(vals.begin(), vals.end(), v + 1e-12 * std::fmax(1.0, std::fabs(v)));
+      (*index)[i] = (int32_t)((it - vals.begin()) - 1);
+    }
+  }
+  return true;
+}
+
+}  // namespace pycool
+
+using namespace pycool;
+
+// The distinct values of k_eff^2 (the symbol of -D on plane waves, Eq. D)
+// over the n^3 lattice modes, and each mode's index into them.  Values that
+// differ by less than 1e-12 (equal symbols reached through different cosines)
+// count as one.
+extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_modes(
+    int32_t n, int32_t stencil, double* values, int64_t cap, int64_t* count, int32_t* index) {
+  if (n < 1 || n > 512 || !count || cap < 0 ||
+      (stencil != PYCOOL_STENCIL_7PT && stencil != PYCOOL_STENCIL_ISO27))
+    return PYCOOL_E_INVALID;
+  std::vector<double> vals;
+  std::vector<int32_t> idx;
+  linear_modes_host(n, stencil, vals, index ? &idx : nullptr);
   *count = (int64_t)vals.size();
   if (values) {
     if (cap < (int64_t)vals.size()) return PYCOOL_E_INVALID;
     for (size_t i = 0; i < vals.size(); ++i) values[i] = vals[i];
   }
-  if (index) {
-    for (size_t i = 0; i < S; ++i) {
-      // the last value not above k2[i] + tolerance
-      const double v = k2[i];
-      auto it = std::upper_bound(vals.begin(), vals.end(), v + 1e-12 * std::fmax(1.0, std::fabs(v)));
-      index[i] = (int32_t)((it - vals.begin()) - 1);
-    }
-  }
+  if (index) std::memcpy(index, idx.data(), idx.size() * sizeof(int32_t));
   return PYCOOL_OK;
 }
 
@@ -215,7 +331,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_gr
   const pycool_status v = validate(cfg);
   if (v != PYCOOL_OK) return v;
   if (!phi0 || !pi0 || !k2 || !T || !background || nk < 1 || steps < 0 || !(a0 > 0.0) ||
-      !std::isfinite(pa0))
+      !std::isfinite(pa0) || cfg->time_step != PYCOOL_TIME_CONFORMAL)
     return PYCOOL_E_INVALID;
   const int nf = model_nfields(cfg->model);
   LinArgs a;
@@ -259,5 +375,154 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_gr
   cudaFree(dk);
   cudaFree(dT);
   cudaFree(dbg);
+  return st;
+}
+
+// The whole linearised evolution of lattice fields on the device.
+extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_evolve(
+    const pycool_config* cfg, double a0, double pa0, const double* phi, const double* pi,
+    int64_t steps, double* phi_out, double* pi_out, double* background, void* cuda_stream) {
+  const pycool_status v = validate(cfg);
+  if (v != PYCOOL_OK) return v;
+  if (!phi || !pi || !phi_out || !pi_out || !background || steps < 0 || !(a0 > 0.0) ||
+      !std::isfinite(pa0) || cfg->n < 2 || cfg->n > 512 ||
+      cfg->time_step != PYCOOL_TIME_CONFORMAL)
+    return PYCOOL_E_INVALID;
+  {  // the outputs serve as scratch while the inputs are read: no overlap
+    const size_t bytes = (size_t)model_nfields(cfg->model) * cfg->n * cfg->n * cfg->n * 8;
+    const uintptr_t in[2] = {(uintptr_t)phi, (uintptr_t)pi};
+    const uintptr_t out[2] = {(uintptr_t)phi_out, (uintptr_t)pi_out};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (out[i] < in[j] + bytes && in[j] < out[i] + bytes) return PYCOOL_E_INVALID;
+    if (out[0] < out[1] + bytes && out[1] < out[0] + bytes) return PYCOOL_E_INVALID;
+  }
+  const int nf = model_nfields(cfg->model);
+  const int n = cfg->n;
+  const long long S = (long long)n * n * n;
+  const long long half = (long long)n * n * (n / 2 + 1);   // coefficients of a real transform
+  std::vector<double> vals;
+  std::vector<int32_t> full;
+  linear_modes_host(n, cfg->stencil, vals, &full);
+  std::vector<int32_t> hidx((size_t)half);
+  const int nh = n / 2 + 1;
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < nh; ++x)
+        hidx[((size_t)z * n + y) * nh + x] = full[((size_t)z * n + y) * n + x];
+  const long long nk = (long long)vals.size();
+  const size_t N2 = (size_t)(2 * nf) * (2 * nf);
+
+  LinArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nk = nk;
+  a.a0 = a0;
+  a.pa0 = pa0;
+  a.nstages = stage_table(cfg->order, a.w);
+  a.steps = steps;
+  a.dt = cfg->dt;
+  const double dx = cfg->L / n;
+  a.dx2inv = 1.0 / (dx * dx);
+  a.VL = (double)S;
+  a.inv6VLm2 = std::isinf(cfg->mpl) ? 0.0 : 1.0 / (6.0 * a.VL * cfg->mpl * cfg->mpl);
+  a.rho_m0 = cfg->rho_mat0;
+  for (int i = 0; i < 8; ++i) a.params[i] = cfg->params[i];
+  if (cfg->model == PYCOOL_MODEL_QBALL) a.derived[0] = std::log(cfg->params[2] * cfg->params[2]);
+
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cufftDoubleComplex* spec = nullptr;   // [phi, pi][N_f][half]
+  double *dk = nullptr, *dT = nullptr, *dbg = nullptr, *dpart = nullptr;
+  double** dptrs = nullptr;             // [2][2 N_f]: source and destination arrays
+  int32_t* didx = nullptr;
+  cufftHandle fwd = 0, inv = 0;
+  bool have_fwd = false, have_inv = false;
+  pycool_status st = PYCOOL_OK;
+  do {
+    if (injected_alloc_failure() ||
+        cudaMalloc((void**)&spec, (size_t)2 * nf * half * sizeof(cufftDoubleComplex)) !=
+            cudaSuccess ||
+        cudaMalloc((void**)&dk, (size_t)nk * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&dT, (size_t)nk * N2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&dbg, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&didx, (size_t)half * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc((void**)&dpart, (size_t)2 * nf * kMeanBlocks * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&dptrs, 8 * sizeof(double*)) != cudaSuccess) {
+      cudaGetLastError();
+      st = PYCOOL_E_NOMEM;
+      break;
+    }
+    int dims[3] = {n, n, n};
+    if (cufftPlanMany(&fwd, 3, dims, nullptr, 1, (int)S, nullptr, 1, (int)half, CUFFT_D2Z, nf) !=
+        CUFFT_SUCCESS) { st = PYCOOL_E_CUDA; break; }
+    have_fwd = true;
+    if (cufftPlanMany(&inv, 3, dims, nullptr, 1, (int)half, nullptr, 1, (int)S, CUFFT_Z2D, nf) !=
+        CUFFT_SUCCESS) { st = PYCOOL_E_CUDA; break; }
+    have_inv = true;
+    if (cufftSetStream(fwd, s) != CUFFT_SUCCESS || cufftSetStream(inv, s) != CUFFT_SUCCESS) {
+      st = PYCOOL_E_CUDA;
+      break;
+    }
+    a.k2 = dk;
+    a.T = dT;
+    a.bg = dbg;
+    a.bg_in = dbg + 8;
+    cufftDoubleComplex* sphi = spec;
+    cufftDoubleComplex* spi = spec + (size_t)nf * half;
+    if (cudaMemcpyAsync(dk, vals.data(), (size_t)nk * sizeof(double), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(didx, hidx.data(), (size_t)half * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess) { st = PYCOOL_E_CUDA; break; }
+    // 1. background: the lattice means (fixed-order sums); the perturbations
+    //    (fields minus means) go to the output arrays, which serve as the
+    //    transforms' real input (the background never enters a transform)
+    double* hptrs[8];
+    for (int f = 0; f < nf; ++f) {
+      hptrs[f] = const_cast<double*>(phi) + (size_t)f * S;
+      hptrs[nf + f] = const_cast<double*>(pi) + (size_t)f * S;
+      hptrs[4 + f] = phi_out + (size_t)f * S;
+      hptrs[4 + nf + f] = pi_out + (size_t)f * S;
+    }
+    if (cudaMemcpyAsync(dptrs, hptrs, sizeof(hptrs), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = PYCOOL_E_CUDA;
+      break;
+    }
+    linear_means_partial<<<dim3(kMeanBlocks, 2 * nf), 256, 0, s>>>(dptrs, S, dpart);
+    linear_means_fold<<<1, 32, 0, s>>>(dpart, 2 * nf, 1.0 / (double)S, dbg + 8);
+    linear_subtract<<<152 * 8, 256, 0, s>>>(dptrs, dptrs + 4, S, 2 * nf, dbg + 8);
+    // 2. forward transforms of the perturbations (every field), k = 0 cleared
+    if (cudaGetLastError() != cudaSuccess ||
+        cufftExecD2Z(fwd, phi_out, sphi) != CUFFT_SUCCESS ||
+        cufftExecD2Z(fwd, pi_out, spi) != CUFFT_SUCCESS) {
+      st = PYCOOL_E_CUDA;
+      break;
+    }
+    linear_clear_mean<<<1, 32, 0, s>>>(spec, half, nf);
+    // 3. growth functions of the distinct k_eff^2 (background evolved per thread)
+    // 4. every mode: T y(0) / S, k = 0 -> the evolved background
+    if (cudaGetLastError() != cudaSuccess || launch_linear_growth(cfg->model, a, s) != cudaSuccess ||
+        launch_linear_apply(nf, spec, half, didx, dT, dbg, 1.0 / (double)S, s) != cudaSuccess) {
+      st = PYCOOL_E_CUDA;
+      break;
+    }
+    // 5. inverse transforms into the caller's arrays
+    if (cufftExecZ2D(inv, sphi, phi_out) != CUFFT_SUCCESS ||
+        cufftExecZ2D(inv, spi, pi_out) != CUFFT_SUCCESS) {
+      st = PYCOOL_E_CUDA;
+      break;
+    }
+    if (cudaMemcpyAsync(background, dbg, (size_t)(2 + 2 * nf) * sizeof(double),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = PYCOOL_E_CUDA;
+  } while (0);
+  if (have_fwd) cufftDestroy(fwd);
+  if (have_inv) cufftDestroy(inv);
+  cudaFree(spec);
+  cudaFree(dk);
+  cudaFree(dT);
+  cudaFree(dbg);
+  cudaFree(didx);
+  cudaFree(dpart);
+  cudaFree(dptrs);
   return st;
 }

@@ -85,25 +85,27 @@ struct PLayout {
 //   split extra: the compensated sums [NQ][threads / 4] float pairs, or every
 //               block's row of the stage sums (the fold reads them there),
 //               whichever is larger.
+// The FP64 and split-DD forms (bound by arithmetic: ALU) share the FP64 ring.
 template <int PREC, int NF, int VX, int NQ>
 struct PRing {
-  using LY = PLayout<NF, VX, PREC == PREC_FP64 ? 8 : 4>;
+  static constexpr bool ALU = PREC != PREC_SPLIT;
+  using LY = PLayout<NF, VX, prec_word(PREC)>;
   static constexpr int DRIFT_ELEMS = NF * (kPTY + 2) * LY::TX;
   static constexpr int KAHAN_BYTES = NQ * kKahanGroups * 8;
   static constexpr int ROWS_BYTES = kMaxPBlocks * kNQ * 8;
   static constexpr int EXTRA_BYTES =
-      PREC == PREC_FP64 ? 2 * DRIFT_ELEMS * 8 + NQ * kPThreads * 8
-                        : (KAHAN_BYTES > ROWS_BYTES ? KAHAN_BYTES : ROWS_BYTES);
+      ALU ? 2 * DRIFT_ELEMS * 8 + NQ * kPThreads * 8
+          : (KAHAN_BYTES > ROWS_BYTES ? KAHAN_BYTES : ROWS_BYTES);
   static constexpr int FIT = (kPSmemBudget - EXTRA_BYTES) / LY::SLOT_BYTES;
-  static constexpr int NSLOT = PREC == PREC_FP64 ? 3 : (FIT < 10 ? FIT : 10);
-  static constexpr int LEAD = PREC == PREC_FP64 ? 2
+  static constexpr int NSLOT = ALU ? 3 : (FIT < 10 ? FIT : 10);
+  static constexpr int LEAD = ALU ? 2
                               : (NSLOT - kSplitSlack < kSplitLead ? NSLOT - kSplitSlack : kSplitLead);
   // warps that issue a stage's first LEAD planes at a stage boundary (the
   // others fold the block sums), each every PRE-th plane
   static constexpr int PRE = LEAD < kPWarps - NQ ? LEAD : kPWarps - NQ;
   static constexpr int RING_BYTES = NSLOT * LY::SLOT_BYTES;
   static constexpr int SMEM_BYTES = RING_BYTES + EXTRA_BYTES;
-  static_assert(NSLOT >= 5 || PREC == PREC_FP64, "split ring too shallow");
+  static_assert(NSLOT >= 5 || ALU, "split ring too shallow");
   static_assert(PRE >= 1, "a warp to issue the first planes beside the folds");
 };
 
@@ -124,6 +126,7 @@ struct PShared {
   const int4* units;      // (x0, y0, z0, Q): tile origin, first output plane, planes incl. halos
   int nunits;
   uint32_t* issued;       // per slot: 1 + ring index of the last plane issued
+  long long limit;        // clocks after which a wait gives up
 };
 
 // Vector store to global memory (st.global: the output arrays are global, and
@@ -159,9 +162,11 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 // Thread 0 adds its arrival with release semantics (publishing the block's
 // global writes, ordered before it by the block barrier) and polls the
 // counter with acquire loads until every block of this barrier has arrived
-// (target = arrivals before it + G).  The poll is bounded by ~2^31 clocks
-// (about a second); on timeout it reports false instead of waiting on.
-__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long target) {
+// (target = arrivals before it + G).  The poll is bounded by `limit` clocks
+// (~2^31, about a second, unless a test asks for less); on timeout it reports
+// false instead of waiting on.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long target,
+                                             long long limit) {
   bool ok = true;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -169,7 +174,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned
     if (ld_acquire_u64(count) < target) {
       const long long t0 = clock64();
       for (uint32_t i = 1; ld_acquire_u64(count) < target; ++i)
-        if ((i & 63u) == 0u && clock64() - t0 > (1ll << 31)) { ok = false; break; }
+        if ((i & 63u) == 0u && clock64() - t0 > limit) { ok = false; break; }
     }
   }
   return ok;
@@ -277,24 +282,33 @@ __device__ __forceinline__ void plane_parts(const T (&ctr)[VX], const T (&dn)[VX
   }
 }
 
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ dd shfl_up1(dd v) { return dd_shfl_up(v, 1); }
+__device__ __forceinline__ float shfl_down1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_down1(double v) {
+  return __shfl_down_sync(0xffffffffu, v, 1);
+}
+__device__ __forceinline__ dd shfl_down1(dd v) { return dd_shfl_down(v, 1); }
+
 // x-neighbours of a lane's VX sites (shuffles; lanes 0 and 31 take the halo
 // column) and the four diagonal neighbours (27-point stencil), then the parts.
 template <typename T, int VX, bool CORNERS, bool MID, int CR>
 __device__ __forceinline__ void lane_parts(const T (&ctr)[VX], const T (&dn)[VX], const T (&up)[VX],
                                            const T (&el)[CR], T (&smid)[VX], T (&so)[VX]) {
   const int lane = threadIdx.x & 31;
-  T left = 0, right = 0, dl = 0, dr = 0, ul = 0, ur = 0;
+  T left = T(0.0), right = T(0.0), dl = T(0.0), dr = T(0.0), ul = T(0.0), ur = T(0.0);
   if (MID || CORNERS) {
-    left = __shfl_up_sync(0xffffffffu, ctr[VX - 1], 1);
-    right = __shfl_down_sync(0xffffffffu, ctr[0], 1);
+    left = shfl_up1(ctr[VX - 1]);
+    right = shfl_down1(ctr[0]);
     if (lane == 0) left = el[(CR - 1) / 2];
     if (lane == 31) right = el[(CR - 1) / 2];
   }
   if constexpr (CORNERS) {
-    dl = __shfl_up_sync(0xffffffffu, dn[VX - 1], 1);
-    dr = __shfl_down_sync(0xffffffffu, dn[0], 1);
-    ul = __shfl_up_sync(0xffffffffu, up[VX - 1], 1);
-    ur = __shfl_down_sync(0xffffffffu, up[0], 1);
+    dl = shfl_up1(dn[VX - 1]);
+    dr = shfl_down1(dn[0]);
+    ul = shfl_up1(up[VX - 1]);
+    ur = shfl_down1(up[0]);
     if (lane == 0) { dl = el[0]; ul = el[CR - 1]; }
     if (lane == 31) { dr = el[0]; ur = el[CR - 1]; }
   }
@@ -348,7 +362,7 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
       const int s = g % NSLOT;
       const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
       T* dp = sm.drift + (g & 1) * RG::DRIFT_ELEMS;   // this plane's drifted phi
-      const bool ok = mbar_wait(&sm.full[s], (g / NSLOT) & 1);
+      const bool ok = mbar_wait(&sm.full[s], (g / NSLOT) & 1, sm.limit);
       // drift the own row and the two halo rows (warps 0 and 1) into the
       // drift buffer, and the halo-column values this lane needs (registers)
       T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
@@ -452,6 +466,188 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
 }
 
 // ---------------------------------------------------------------------------
+// Split-DD form: phi = phi0 + d with the background phi0 in float64 (advanced
+// by the scalar chain) and the fluctuation d stored and updated as a
+// double-float (two float32 per value, 8 bytes: the traffic of the FP64
+// form).  The structure is the FP64 form's (each plane drifted once into a
+// shared-memory buffer, one block barrier per plane); the arithmetic is that
+// of the split-FP32 form (stencil on phi + c pi, re-centred output, difference
+// forms of V') in double-float on the FP32 pipe.
+// ---------------------------------------------------------------------------
+// One stage over this block's units.  tot: this thread's stage sums (NQ
+// double-floats, the running accumulators folded in every KGROUP planes).
+// Returns false (in every thread) if a wait gave up.
+template <int MODEL, int STENCIL, int VX, int MODE>
+__device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC_DD>& cx,
+                                         const PShared& sm, uint32_t gq, int ib, dd* tot) {
+  using C = Ctx<MODEL, PREC_DD>;
+  using T = dd;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int CR = CORNERS ? 3 : 1;
+  using LY = PLayout<NF, VX, 8>;
+  using RG = PRing<PREC_DD, NF, VX, NQ>;
+  constexpr int TX = LY::TX, CW = LY::CW;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  constexpr int KGROUP = 8;   // output planes per running accumulator before it is folded
+  const SimDesc& d = *sm.d;
+  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+  const int n = p.g.n;
+  const size_t S = (size_t)d.S, nn = (size_t)n * n;
+  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
+  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
+  const T cd = cx.cdrift;
+  // re-centring: phi* = phi + c pi - (mu_phi + c mu_pi); the stencil works on
+  // phi + c pi (D of a constant is zero)
+  T Mf[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Mf[f] = cx.mu_phi[f] + cd * cx.mu_pi[f];
+  const int side = lane == 31 ? 1 : 0;
+  const bool edge = lane == 0 || lane == 31;          // lanes that read a halo column
+  const int own = (ly + 1) * TX + lane * VX;          // this lane's sites in a slot row
+  DDAcc acc[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) acc[i].zero();
+  int kg = 0;
+
+  int pui = 0, puq = 0;                                 // producer position, LEAD ahead
+  for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  uint32_t g = gq;
+  for (int i = 0; i < sm.nunits; ++i) {
+    const int4 u = sm.units[i];
+    const int Q = u.w;
+    const bool clear = yclear(u, n);
+    const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
+    T part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int jj = 0; jj < VX; ++jj)
+        part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = T(0.0);
+    for (int q = 0; q < Q; ++q, ++g) {
+      const int s = g % NSLOT;
+      const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
+      T* dp = reinterpret_cast<T*>(sm.drift) + (g & 1) * RG::DRIFT_ELEMS;   // drifted plane
+      const bool ok = mbar_wait(&sm.full[s], (g / NSLOT) & 1, sm.limit);
+      // drift the own row and the two halo rows (warps 0 and 1) into the drift
+      // buffer, and the halo-column values lanes 0 and 31 need (registers)
+      T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* mph = sl + LY::main_off(0, f);
+        const T* mpi = sl + LY::main_off(1, f);
+        T* dph = dp + f * (kPTY + 2) * TX;
+        T a[VX], b[VX];
+        vload<T, VX>(&mph[own], a);
+        vload<T, VX>(&mpi[own], b);
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          cur_pi[f][jj] = b[jj] - cx.mu_pi[f];
+          cur_ph[f][jj] = a[jj] + cd * b[jj];
+        }
+        vstore<T, VX>(&dph[own], cur_ph[f]);
+        if (ly < 2) {
+          const int r = (ly == 0 ? 0 : kPTY + 1) * TX + lane * VX;
+          vload<T, VX>(&mph[r], a);
+          vload<T, VX>(&mpi[r], b);
+#pragma unroll
+          for (int jj = 0; jj < VX; ++jj) a[jj] = a[jj] + cd * b[jj];
+          vstore<T, VX>(&dph[r], a);
+        }
+#pragma unroll
+        for (int rr = 0; rr < CR; ++rr) el[f][rr] = T(0.0);
+        if (edge) {
+          const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
+          const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
+#pragma unroll
+          for (int rr = 0; rr < CR; ++rr) {
+            const int r = ly + 1 + rr - (CR - 1) / 2;
+            const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+            el[f][rr] = cph[row] + cd * cpi[row];
+          }
+        }
+      }
+      if (__syncthreads_or(!ok)) return false;   // one decision for the whole block
+      if (tid == 0 && pui < sm.nunits) {
+        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift
+        const uint32_t gp = g + LEAD;
+        pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
+                                     sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                     &sm.full[gp % NSLOT]);
+        sm.issued[gp % NSLOT] = gp + 1;
+      }
+      padvance(sm, pui, puq);
+
+      const bool mid = q > 0 && q < Q - 1;   // the z-halo planes need S_off only
+      T so_new[NF][VX], smid_new[NF][VX];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* dph = dp + f * (kPTY + 2) * TX;
+        T dn[VX], up[VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) dn[jj] = up[jj] = T(0.0);
+        if (mid || CORNERS) {
+          vload<T, VX>(&dph[own - TX], dn);
+          vload<T, VX>(&dph[own + TX], up);
+        }
+        if (mid)
+          lane_parts<T, VX, CORNERS, true, CR>(cur_ph[f], dn, up, el[f], smid_new[f], so_new[f]);
+        else
+          lane_parts<T, VX, CORNERS, false, CR>(cur_ph[f], dn, up, el[f], smid_new[f], so_new[f]);
+      }
+      if (q >= 2) {  // output plane z0 + q - 2
+        const size_t o = o0 + (size_t)(q - 2) * nn;
+        T pin[NF][VX], phs[NF][VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          T phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            phs[f][jj] = ph_m[f][jj] - Mf[f];   // the re-centred drifted field
+            phj[f] = phs[f][jj];
+            Dj[f] = part_m[f][jj] + so_new[f][jj];
+            pmj[f] = pi_m[f][jj];
+          }
+          site_dd<MODEL>(cx, MODE, phj, Dj, pmj, pnj, acc);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pin[f][jj] = pnj[f];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          gstore<T, VX>(phi_out + f * S + o, phs[f]);
+          if (MODE == MODE_SWEEP) gstore<T, VX>(pi_out + f * S + o, pin[f]);
+        }
+        if (++kg == KGROUP) {
+          kg = 0;
+#pragma unroll
+          for (int i2 = 0; i2 < NQ; ++i2) acc[i2].fold(tot[i2]);
+        }
+      }
+      if (mid) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int jj = 0; jj < VX; ++jj)
+            part_m[f][jj] = (CORNERS ? so_m[f][jj] : ph_m[f][jj]) + smid_new[f][jj];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          if constexpr (CORNERS) so_m[f][jj] = so_new[f][jj];
+          ph_m[f][jj] = cur_ph[f][jj];
+          pi_m[f][jj] = cur_pi[f][jj];
+        }
+    }
+  }
+#pragma unroll
+  for (int i2 = 0; i2 < NQ; ++i2) acc[i2].fold(tot[i2]);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Split-FP32 form.
 // ---------------------------------------------------------------------------
 // Producer of ring plane gp (one warp): waits until every warp has released
@@ -463,7 +659,7 @@ __device__ __noinline__ bool produce_split(const PParams& p, const PShared& sm, 
   bool ok = true;
   if (gp >= (uint32_t)NSLOT) {
     const uint32_t rr = gp - NSLOT;
-    ok = mbar_wait(&sm.empty[rr % NSLOT], (rr / NSLOT) & 1);
+    ok = mbar_wait(&sm.empty[rr % NSLOT], (rr / NSLOT) & 1, sm.limit);
   }
   if (!__all_sync(0xffffffffu, ok)) return false;
   if ((threadIdx.x & 31) == 0) {
@@ -585,7 +781,7 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
           pQ = pui < sm.nunits ? sm.units[pui].w : 0;
         }
       }
-      ok = ok && mbar_wait(&sm.full[s], par);
+      ok = ok && mbar_wait(&sm.full[s], par, sm.limit);
       if (!__all_sync(0xffffffffu, ok)) return false;
       const float* sl = (const float*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
       // the three rows this warp needs and the halo-column values, drifted in registers
@@ -685,7 +881,7 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
 template <int PREC, int NF, int VX, bool CORNERS, int NSLOT>
 __device__ __forceinline__ void prefetch_plane(const PParams& p, const PShared& sm, int ib,
                                                uint32_t gq, int l) {
-  constexpr int WORD = PREC == PREC_FP64 ? 8 : 4;
+  constexpr int WORD = prec_word(PREC);
   using LY = PLayout<NF, VX, WORD>;
   int ui = 0, uq = 0;
   for (int j = 0; j < l; ++j) padvance(sm, ui, uq);
@@ -748,6 +944,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   __shared__ int4 s_units[kMaxPUnits];
   __shared__ uint32_t s_issued[NSLOT];
   __shared__ int s_bad;
+  __shared__ int s_fold;   // parity of a rows copy issued and not yet folded; -1: none
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SimDesc& d = s_desc;
@@ -766,6 +963,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   sm.empty = empty;
   sm.units = s_units;
   sm.issued = s_issued;
+  sm.limit = p.wait_limit;
   const int ubeg = __ldg(&p.uoff[blockIdx.x]);
   sm.nunits = min(__ldg(&p.uoff[blockIdx.x + 1]) - ubeg, kMaxPUnits);   // host: <= kMaxPUnits
 
@@ -777,6 +975,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     mbar_init(&foldbar, 1);
     fence_mbar_init();
     s_bad = 0;
+    s_fold = -1;
   }
   if (tid < NSLOT) s_issued[tid] = 0;
   if (tid < 6) {   // bring the tensor maps into the descriptor cache
@@ -824,6 +1023,15 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       ok = (mode == MODE_SWEEP)
                ? stage_fp64<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib, accd)
                : stage_fp64<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib, accd);
+    } else if constexpr (PREC == PREC_DD) {
+      dd tot[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) tot[q] = dd(0.f, 0.f);
+      ok = (mode == MODE_SWEEP)
+               ? stage_dd<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib, tot)
+               : stage_dd<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib, tot);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) accd[q] = (double)tot[q];
     } else {
       // the Q-ball's difference forms have a branch for a background at the
       // origin; a stage whose background is away from it runs without the test
@@ -850,7 +1058,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     if (s_bad) { fault = true; break; }
 
     // ---- block sums: one warp per quantity over the 512 threads' values, fixed order ----
-    if constexpr (PREC == PREC_FP64) {
+    if constexpr (PREC != PREC_SPLIT) {
       double* red = sm.red;
 #pragma unroll
       for (int q = 0; q < NQ; ++q) red[q * kPThreads + tid] = accd[q];
@@ -895,7 +1103,9 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     }
     // the reduction scratch is overwritten by the rows' bulk copy below
     fence_proxy_async();
-    if (!grid_barrier(p.bar, p.bar_base + (unsigned long long)(k + 1) * G)) s_bad = 1;
+    if (!grid_barrier(p.bar, p.bar_base + (unsigned long long)(k + 1) * G + p.bar_extra,
+                      p.wait_limit))
+      s_bad = 1;
     // while thread 0 waits for the other blocks, warp 14 forms what the scalar
     // chain needs that does not depend on the sums: this stage's SumCoef and
     // the next stage's PreCoef (it starts from a = k.a, h_prev = k.h)
@@ -904,9 +1114,10 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       if (k < K) {
         const int mn = k + 1 < K ? MODE_SWEEP : MODE_FLUSH;
         const int sn = sbv[cb].stage + 1 < d.nstages ? sbv[cb].stage + 1 : 0;
-        const double hn = (mn == MODE_SWEEP) ? d.w[sn] * d.dt : 0.0;
         const Coef& kc = sctxv[cb].k;
-        s_qn = prestage_a(kc.a, __drcp_rn(kc.a), kc.h, hn, d, mn);
+        const double hn = stage_step(d, sn, kc.deta, mn);
+        s_qn = prestage_a(kc.a, __drcp_rn(kc.a), kc.h, hn, d, mn, d.physical ? kc.deta : d.dt,
+                          d.physical && sn == 0, d.w[sn]);
       }
     }
     __syncthreads();
@@ -924,24 +1135,25 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     const int ib_next = ib ^ (mode == MODE_SWEEP ? 3 : 1);
     const bool pre = k < K;
     constexpr int kPreThreads = (1 + PRE) * 32;
-    using FT = typename std::conditional<PREC == PREC_FP64, double, float2>::type;
+    using FT = typename std::conditional<PREC != PREC_SPLIT, double, float2>::type;
     // every block's row arrives by one bulk copy into the (now free) reduction
     // scratch: one request stream per block instead of 8-byte loads of the
     // same lines by every block
-    FT* srows = reinterpret_cast<FT*>(PREC == PREC_FP64 ? (void*)sm.red : (void*)sm.kahan);
+    FT* srows = reinterpret_cast<FT*>(PREC != PREC_SPLIT ? (void*)sm.red : (void*)sm.kahan);
     if (warp == 0) {
       if (lane == 0) {
         const uint32_t bytes = (uint32_t)(G * kNQ * sizeof(FT));
         mbar_expect_tx(&foldbar, bytes);
         bulk_load(srows, reinterpret_cast<const FT*>(p.rows) + (size_t)(k & 1) * G * kNQ, bytes,
                   &foldbar);
+        s_fold = (int)(k & 1);
       }
       __syncwarp();
       if (pre) named_arrive(1, kPreThreads);   // the next stage's copies queue behind it
     }
     if (warp < NQ) {
-      if (!mbar_wait(&foldbar, (uint32_t)(k & 1))) atomicOr(&s_bad, 1);
-      if constexpr (PREC == PREC_FP64) {
+      if (!mbar_wait(&foldbar, (uint32_t)(k & 1), p.wait_limit)) atomicOr(&s_bad, 1);
+      if constexpr (PREC != PREC_SPLIT) {
         double v = 0.0;
         for (int r = lane; r < G; r += 32) v += srows[(size_t)r * kNQ + warp];   // row order
 #pragma unroll
@@ -973,6 +1185,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     }
     __syncthreads();
     // @folded
+    if (tid == 0 && !s_bad) s_fold = -1;   // every folding warp saw the copy land
     // ---- in parallel, on warps of different schedulers, identically in
     //      every block: the next stage's coefficients (warp 14: sums -> p_a
     //      kick -> scalar half-steps -> split background), the split form's
@@ -993,7 +1206,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
               nx.shiftK[f] = (mn == MODE_FLUSH) ? flush_shift(d, ib_next, f, nx.k.c) : 0.0;
           }
         }
-        if constexpr (PREC == PREC_SPLIT) {
+        if constexpr (PREC != PREC_FP64) {
           __syncwarp();
           named_sync(2, 64);
           if (lane == 0) nx.split_tail(d, mn, s_p0);
@@ -1001,7 +1214,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       }
       // @chain-done
     } else if (warp == kPWarps - 4) {
-      if constexpr (PREC == PREC_SPLIT) {
+      if constexpr (PREC != PREC_FP64) {
         if (pre) {
           if (lane == 0) {
             double mphi[NF], mpi[NF];
@@ -1031,7 +1244,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     if (fault) atomicOr(p.fault, 1);
     for (int s = 0; s < NSLOT; ++s)
       if (s_issued[s]) mbar_wait(&full[s], ((s_issued[s] - 1u) / NSLOT) & 1u);
-    if (fault) mbar_wait(&foldbar, 0u), mbar_wait(&foldbar, 1u);   // a pending rows copy, if any
+    if (s_fold >= 0) mbar_wait(&foldbar, (uint32_t)s_fold);   // a rows copy still in flight
   }
   if (fault) return;   // the state is not trusted any more (the host poisons the simulation)
   if (blockIdx.x == 0 && tid < (int)(sizeof(Background) / 8))
@@ -1045,7 +1258,7 @@ template <int PREC>
 cudaError_t launch_persist_impl(int model, int stencil, int vx, const PParams& p, int grid,
                                 cudaStream_t s, int* bps) {
 #define PYCOOL_P(M, ST, V)                                                                  \
-  if constexpr (V * Pot<M>::NF * (PREC == PREC_FP64 ? 8 : 4) <= 16) {                       \
+  if constexpr (V * Pot<M>::NF * prec_word(PREC) <= 16) {                                  \
     if (model == M && stencil == ST && vx == V) {                                           \
       constexpr size_t smem = persist_smem_bytes<M, PREC, V>();                             \
       auto kern = evolve_persist<M, ST, PREC, V>;                                           \

@@ -40,6 +40,13 @@ cudaError_t encode_tensor_maps(SimDesc& d);
 cudaError_t launch_arm(Background* bg, long long nsweeps, cudaStream_t s);
 void observables(const Background& b, const SimDesc& d, double mpl, double rho_r0,
                  double rho_m0, pycool_observables* out);
+// Output-interval observables (observe.cu), at a synchronised state b.
+cudaError_t launch_energy_fields(const SimDesc& d, const Background& b, double* rho, double* P,
+                                 cudaStream_t s);
+cudaError_t launch_field_values(const SimDesc& d, const Background& b, int which, int f,
+                                double* out, cudaStream_t s);
+cudaError_t launch_spectrum_bins(const void* spec, int n, const int32_t* order,
+                                 const int32_t* start, int nbins, double* power, cudaStream_t s);
 // Fault injection (pycool_debug_fail_alloc): true if this device allocation
 // is to report failure (consumes one of the requested failures).
 bool injected_alloc_failure();

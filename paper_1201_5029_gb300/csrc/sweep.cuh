@@ -49,6 +49,7 @@
 
 #include "internal.cuh"
 #include "models.cuh"
+#include "models_dd.cuh"
 
 namespace pycool {
 
@@ -62,6 +63,7 @@ struct Coef {
   double a;      // a after the leading Phi_H1's
   double pa;     // p_a after the leading Phi_H2 (before this stage's Phi_H3)
   double h;      // this stage's step (0 for a flush)
+  double deta;   // the conformal step of this stage's time step (h = w_i deta)
 };
 
 // The boundary between two stages splits into the part that needs only a,
@@ -77,11 +79,23 @@ struct PreCoef {
   double hn;     // h/2
   double hdx;    // h / dx^2
   double h;      // this stage's step (0 for a flush)
+  double deta;   // the time step's conformal step (physical steps: found in prestage_p)
+  // physical-time steps (Sec. 3.1), a stage that starts a time step: h is
+  // w0 dt / a_n with a_n the scale factor of the synchronised state, known
+  // only after the trailing Phi_H2 has moved p_a
+  int adapt;
+  double w0;     // the stage weight
+  double g0;     // -(h_prev/2) / (6 V_L m^2): the trailing Phi_H1's da/dp_a
+  double gm;     // -(1/2) / (6 V_L m^2): the leading Phi_H1's da/dp_a per unit h
+  double dt, dx2inv;
 };
 
 // ia: 1/a (the caller's reciprocal, so that it can be formed early).
+// h: this stage's step; deta: its time step's conformal step; adapt != 0: a
+// physical-time step starts here and h is derived in prestage_p (h ignored).
 __device__ __forceinline__ PreCoef prestage_a(double a, double ia, double hp, double h,
-                                              const SimDesc& d, int mode) {
+                                              const SimDesc& d, int mode, double deta = 0.0,
+                                              int adapt = 0, double w0 = 0.0) {
   PreCoef q;
   const double ia2 = ia * ia;
   q.a = a;
@@ -89,6 +103,13 @@ __device__ __forceinline__ PreCoef prestage_a(double a, double ia, double hp, do
   q.hh = 0.5 * hp;
   q.c0 = q.hh * ia2;
   q.nVLrm = -(d.VL * d.rho_m0);
+  q.deta = deta;
+  q.adapt = (mode == MODE_SWEEP) ? adapt : 0;
+  q.w0 = w0;
+  q.g0 = -(d.inv6VLm2 * q.hh);
+  q.gm = -(d.inv6VLm2 * 0.5);
+  q.dt = d.dt;
+  q.dx2inv = d.dx2inv;
   if (mode == MODE_SWEEP) {
     q.g1 = -(d.inv6VLm2 * (0.5 * (hp + h)));
     q.hn = 0.5 * h;
@@ -107,8 +128,22 @@ __device__ __forceinline__ Coef prestage_p(const PreCoef& q, double pa, double s
   Coef k;
   // trailing Phi_H2(h_prev/2) of the previous stage: p_a += [sum pi^2/a^3 - V_L rho_m] h_prev/2
   pa = fma(fma(s2, q.ia3, q.nVLrm), q.hh, pa);
-  // Phi_H1(h_prev/2) [Phi_H1(h/2)] merged (p_a is constant under H1): a -= p_a dt' / (12 V_L m^2)
-  const double a = fma(pa, q.g1, q.a);
+  double a, hn = q.hn, hdx = q.hdx, h = q.h;
+  k.deta = q.deta;
+  if (q.adapt) {
+    // a physical-time step starts: the trailing Phi_H1(h_prev/2) gives the
+    // synchronised a_n, the step is d-eta = dt / a_n (Sec. 3.1), then the
+    // leading Phi_H1(h/2) of its first stage, h = w_0 d-eta
+    const double an = fma(pa, q.g0, q.a);
+    k.deta = q.dt / an;
+    h = q.w0 * k.deta;
+    hn = 0.5 * h;
+    hdx = h * q.dx2inv;
+    a = fma(pa, q.gm * h, an);
+  } else {
+    // Phi_H1(h_prev/2) [Phi_H1(h/2)] merged (p_a is constant under H1): a -= p_a dt' / (12 V_L m^2)
+    a = fma(pa, q.g1, q.a);
+  }
   k.a = a;
   if (mode != MODE_SWEEP) {
     k.c = q.c0; k.kD = 0.0; k.kV = 0.0; k.pa = pa; k.h = 0.0;
@@ -118,21 +153,31 @@ __device__ __forceinline__ Coef prestage_p(const PreCoef& q, double pa, double s
   // ~450 cycles of a single thread on GB300
   const double ia = __drcp_rn(a), ia2 = ia * ia;
   // leading Phi_H2(h/2)
-  k.pa = fma(fma(s2, ia2 * ia, q.nVLrm), q.hn, pa);
-  k.c = fma(q.hn, ia2, q.c0);
+  k.pa = fma(fma(s2, ia2 * ia, q.nVLrm), hn, pa);
+  k.c = fma(hn, ia2, q.c0);
   const double a2 = a * a;
-  k.kD = a2 * q.hdx;
-  k.kV = (a2 * a2) * q.h;
-  k.h = q.h;
+  k.kD = a2 * hdx;
+  k.kV = (a2 * a2) * h;
+  k.h = h;
   return k;
 }
 
 // ia_a: 1/b.a if the caller already has it (a negative value means "compute it").
+// The step of the stage a Background is about to run: w_i dt (conformal), or
+// w_i d-eta of the running time step (physical; d-eta found at its first stage).
+__device__ __forceinline__ double stage_step(const SimDesc& d, int stage, double deta, int mode) {
+  if (mode != MODE_SWEEP) return 0.0;
+  return d.w[stage] * (d.physical ? deta : d.dt);
+}
+
 __device__ __forceinline__ Coef prestage(const Background& b, const SimDesc& d, int mode,
                                          double ia_a = -1.0) {
-  const double h = (mode == MODE_SWEEP) ? d.w[b.stage] * d.dt : 0.0;
+  const double h = stage_step(d, (int)b.stage, b.deta, mode);
+  const int adapt = d.physical && b.stage == 0;
   const double ia = ia_a > 0.0 ? ia_a : __drcp_rn(b.a);
-  return prestage_p(prestage_a(b.a, ia, b.h_prev, h, d, mode), b.pa, b.sum_pi2, mode);
+  return prestage_p(prestage_a(b.a, ia, b.h_prev, h, d, mode, d.physical ? b.deta : d.dt, adapt,
+                               d.w[b.stage]),
+                    b.pa, b.sum_pi2, mode);
 }
 
 // Explicitly typed fused multiply-add: float arithmetic must stay on the FP32
@@ -182,6 +227,15 @@ template <int NF> struct Slots<NF, PREC_SPLIT> {
                        DPHI2 = 4 * NF + 1;
   static constexpr int NQ = 5 * NF + 1;
 };
+template <int NF> struct Slots<NF, PREC_DD> : Slots<NF, PREC_SPLIT> {};
+
+// The working type of a form: float64, float, or a double-float pair.
+template <int PREC> struct WorkT { using type = float; };
+template <> struct WorkT<PREC_FP64> { using type = double; };
+template <> struct WorkT<PREC_DD> { using type = dd; };
+// The constants of a split form's difference forms.
+template <int MODEL, int PREC> struct SplitKOf { using type = typename Pot<MODEL>::SplitK; };
+template <int MODEL> struct SplitKOf<MODEL, PREC_DD> { using type = typename PotDD<MODEL>::SplitK; };
 
 template <typename T, int V> struct Vec;
 template <> struct Vec<float, 1> { using type = float; };
@@ -189,6 +243,8 @@ template <> struct Vec<float, 2> { using type = float2; };
 template <> struct Vec<float, 4> { using type = float4; };
 template <> struct Vec<double, 1> { using type = double; };
 template <> struct Vec<double, 2> { using type = double2; };
+template <> struct Vec<dd, 1> { using type = float2; };
+template <> struct Vec<dd, 2> { using type = float4; };
 
 // Load / store VX consecutive elements (aligned to VX * sizeof(T)).
 template <typename T, int VX>
@@ -247,7 +303,7 @@ template <int MODEL, int PREC>
 struct Ctx {
   using P = Pot<MODEL>;
   static constexpr int NF = P::NF;
-  using T = typename std::conditional<PREC == PREC_FP64, double, float>::type;
+  using T = typename WorkT<PREC>::type;
   using SL = Slots<NF, PREC>;
   Coef k;
   typename P::K pk;
@@ -255,13 +311,13 @@ struct Ctx {
   T nkVg;                          // FP64 chaotic model: -kV g2 (folded into the chi kick)
   T mu_phi[NF], mu_pi[NF];
   T shiftK[NF];
-  double phi0s[NF], pi0s[NF], V0;  // split form: background after drift / kick
-  typename P::SplitK sk;
+  double phi0s[NF], pi0s[NF], V0;  // split forms: background after drift / kick
+  typename SplitKOf<MODEL, PREC>::type sk;
 
   __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode,
                                        double ia_a = -1.0) {
     set_coef(prestage(bg, d, mode, ia_a), d, mode, P::prep(d.params, d.derived));
-    if constexpr (PREC == PREC_SPLIT) {
+    if constexpr (PREC != PREC_FP64) {
       double p0[2 * NF];
       recenter(bg.mu_phi, bg.mu_pi, bg.phi0, bg.pi0, p0);
       split_tail(d, mode, p0);
@@ -296,7 +352,7 @@ struct Ctx {
       mu_pi[f] = (T)mpi[f];
       p0[f] = phi0[f] + (double)mu_phi[f];
       p0[NF + f] = pi0[f] + (double)mu_pi[f];
-      shiftK[f] = 0;
+      shiftK[f] = T(0.0);
     }
   }
   //   split_tail (split form): the background's own drift and kick, and the
@@ -305,7 +361,10 @@ struct Ctx {
     double dV0[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) phi0s[f] = fma(k.c, p0[NF + f], p0[f]);   // background drift
-    sk = P::split_prep(pk, d.params, d.derived, d.fparams, phi0s, dV0, V0);
+    if constexpr (PREC == PREC_DD)
+      sk = PotDD<MODEL>::prep(pk, d.params, d.derived, phi0s, dV0, V0);
+    else
+      sk = P::split_prep(pk, d.params, d.derived, d.fparams, phi0s, dV0, V0);
 #pragma unroll
     for (int f = 0; f < NF; ++f)  // background kick (D[phi0] = 0)
       pi0s[f] = (mode == MODE_SWEEP) ? fma(-k.kV, dV0[f], p0[NF + f]) : p0[NF + f];
@@ -376,6 +435,30 @@ struct Ctx {
     }
   }
 };
+
+// The kick and the per-site sums of the split-DD form (double-float
+// fluctuations; the sums gather in running double-float accumulators).
+template <int MODEL>
+__device__ __forceinline__ void site_dd(const Ctx<MODEL, PREC_DD>& cx, int mode,
+                                        const dd (&phj)[Pot<MODEL>::NF],
+                                        const dd (&D)[Pot<MODEL>::NF],
+                                        const dd (&pim)[Pot<MODEL>::NF],
+                                        dd (&pin)[Pot<MODEL>::NF], DDAcc* acc) {
+  constexpr int NF = Pot<MODEL>::NF;
+  using SL = Slots<NF, PREC_DD>;
+  dd dVd[NF], dVv;
+  PotDD<MODEL>::diff(cx.sk, phj, dVd, dVv);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    pin[f] = (mode == MODE_SWEEP) ? pim[f] + cx.kD * D[f] - cx.kV * dVd[f] : pim[f];
+    acc[SL::DPI + f].add(pin[f]);
+    acc[SL::DPI2 + f].add_sqr(pin[f]);
+    acc[SL::PHID + f].add_prod(phj[f], D[f]);
+    acc[SL::DPHI + f].add(phj[f]);
+    if (mode != MODE_SWEEP) acc[SL::DPHI2 + f].add_sqr(phj[f]);
+  }
+  acc[SL::V].add(dVv);
+}
 
 // Error-free addition of float pairs (hi, lo): TwoSum on the high parts.
 __device__ __forceinline__ void pair_add(float& hi, float& lo, float bh, float bl) {
@@ -482,8 +565,8 @@ __device__ __forceinline__ SumCoef<C::NF> sum_coef(const C& cx, const SimDesc& d
   q.pa = cx.k.pa;
 #pragma unroll
   for (int f = 0; f < C::NF; ++f) {
-    q.spi[f] = (PREC == PREC_SPLIT) ? (double)d.S * cx.pi0s[f] : 0.0;
-    q.tpi[f] = (PREC == PREC_SPLIT) ? 2.0 * cx.pi0s[f] : 0.0;
+    q.spi[f] = (PREC != PREC_FP64) ? (double)d.S * cx.pi0s[f] : 0.0;
+    q.tpi[f] = (PREC != PREC_FP64) ? 2.0 * cx.pi0s[f] : 0.0;
   }
   return q;
 }
@@ -556,6 +639,7 @@ __device__ __forceinline__ void post_stage(const C& cx, const SumCoef<C::NF>& q,
     pa = pa_kick(q, sum_phiD, sum_V);
     nb.eta = bg.eta + k.h;
     nb.h_prev = k.h;
+    nb.deta = k.deta;
     nb.stage = bg.stage + 1;
     if (nb.stage >= d.nstages) { nb.stage = 0; nb.steps_done = bg.steps_done + 1; }
     nb.sweeps_done = bg.sweeps_done + 1;
@@ -590,7 +674,7 @@ __device__ __forceinline__ void post_stage(const C& cx, const SumCoef<C::NF>& q,
   nb.a = a;
   nb.pa = pa;
   nb.sum_pi2 = sum_pi2;
-  if constexpr (PREC == PREC_SPLIT) {
+  if constexpr (PREC != PREC_FP64) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       nb.phi0[f] = cx.phi0s[f];
@@ -742,15 +826,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait: gives up after ~2^31 clocks (about a second) and reports it.
+// Bounded wait: gives up after `limit` clocks and reports it.
 // (try_wait itself suspends the thread for a while; the clock is read only
 // every 32 polls so that a waiting warp issues few instructions.)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitLimit) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try(bar, parity)) return true;
-    if ((i & 31u) == 0u && clock64() - t0 > (1ll << 31)) return false;
+    if ((i & 31u) == 0u && clock64() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void fence_proxy_async() {

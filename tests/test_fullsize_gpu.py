@@ -73,3 +73,21 @@ def test_split_full_size(case):
     assert ea < 1e-9 and epa < 1e-7
     assert erho < 1e-7
     assert max(evar) < 1e-4
+
+
+def test_split_dd_full_size(case):
+    """The split-DD form in the bench's launch configuration, at the FP64 tolerances."""
+    w, st = case["w"], case["st"]
+    gphi, gpi, ge = G.run_gpu(P, G.gpu_cfg(P, w, order=case["order"], precision="split_dd"),
+                              case["phi"], case["pi"], case["steps"])
+    ef = G.field_errors(gphi, st.phi)
+    ep = G.field_errors(gpi, st.pi)
+    ea, epa = G.rel(ge["a"], st.a), G.rel(ge["pa"], st.pa)
+    stages = int(ge["sweeps_done"]) + 1
+    ff = G.fluct_errors(gphi, st.phi) + G.fluct_errors(gpi, st.pi)
+    ft = G.fluct_tolerances(st.phi, stages, TOL64) + G.fluct_tolerances(st.pi, stages, TOL64)
+    print(f"\n{case['name']} n={w['n']} split-DD: phi {ef} pi {ep} a {ea:.1e} pa {epa:.1e} "
+          f"fluct {['%.2e' % x for x in ff]} bound {['%.2e' % x for x in ft]}")
+    assert max(ef) < TOL64 and max(ep) < TOL64
+    assert ea < TOL64 and epa < TOL64
+    assert all(e < t for e, t in zip(ff, ft)), (ff, ft)

@@ -67,3 +67,48 @@ def test_growth_rejects_bad_arguments():
     with pytest.raises(P.PycoolError) as ei:
         P.pycool_linear_growth(gcfg, -1.0, 0.0, (1.0, 0.0), (0.0, 0.0), [1.0], 3)
     assert ei.value.status == P.E_INVALID
+
+
+LATTICE_CASES = [  # workload-like model, n, order, steps, mpl
+    ("preheat128", 64, 4, 20, 1.0),
+    ("oscillon256", 64, 6, 10, 100.0),
+    ("qball256", 32, 8, 5, 100.0),
+]
+
+
+@pytest.mark.parametrize("name,n,order,steps,mpl", LATTICE_CASES, ids=[c[0] for c in LATTICE_CASES])
+def test_linear_evolve_on_device_matches_oracle(name, n, order, steps, mpl):
+    """pycool_linear_evolve (background, FFT, growth functions, per-mode
+    apply, inverse FFT, all on the device) against the oracle's direct
+    evolution of every mode, element by element on the lattice: the background
+    to 1e-11, and the fields at the scale of their perturbations within
+    gpu_helpers.fluct_tolerances for 3 log2(n) roundings (the transforms'
+    levels; the output adds the perturbations to a float64 background, whose
+    last bit is already 1e-16 / 1e-5 of a 1e-5 perturbation)."""
+    torch = pytest.importorskip("torch")
+    from paper_1201_5029_gb300 import inputs as I
+    w = I.workload(name)
+    phi, pi = I.initial_fields(w, n=n)
+    cfg = O.LatticeConfig(n=n, L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+                          order=order, mpl=mpl)
+    pa0 = O.initial_pa(cfg, 1.0, phi, pi)
+    ls = L.from_lattice(cfg, phi, pi, 1.0, pa0)
+    L.evolve(cfg, ls, steps)
+    ophi, opi = L.to_lattice(ls)
+
+    gcfg = P.make_config(n=n, L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+                         order=order, mpl=mpl)
+    dphi, dpi = torch.from_numpy(phi).cuda(), torch.from_numpy(pi).cuda()
+    outp, outq = torch.empty_like(dphi), torch.empty_like(dpi)
+    a, pa, f0, p0 = P.pycool_linear_evolve(gcfg, 1.0, pa0, dphi, dpi, steps, outp, outq)
+    gphi, gpi = outp.cpu().numpy(), outq.cpu().numpy()
+    assert np.array_equal(dphi.cpu().numpy(), phi)          # inputs untouched
+    assert abs(a - ls.a) <= TOL * ls.a and abs(pa - ls.pa) <= TOL * abs(ls.pa)
+    assert np.max(np.abs(f0 - ls.phi0)) <= TOL * max(1.0, np.max(np.abs(ls.phi0)))
+    import gpu_helpers as G
+    levels = 3 * int(np.log2(n))
+    for g, o in ((gphi, ophi), (gpi, opi)):
+        fe, ft = G.fluct_errors(g, o), G.fluct_tolerances(o, levels, TOL)
+        print(f"\n{name} n={n}: perturbation errors {['%.1e' % x for x in fe]} "
+              f"bounds {['%.1e' % x for x in ft]}")
+        assert all(e < t for e, t in zip(fe, ft)), (fe, ft)
