@@ -48,6 +48,10 @@ Readings of the paper taken here (the paper is silent or garbled):
    initial p_a is 0 (the constraint cannot be imposed).
 8. The complex Q-ball field is Phi = (phi_1 + i phi_2)/sqrt(2), so
    |Phi|^2 = (phi_1^2 + phi_2^2)/2 and V = dV = 0 at |Phi| = 0.
+10. The fourth-order stencil (Sec. 2.1 names HLATTICE's without printing it):
+   '4th' is the 13-point form that is fourth-order accurate on each axis,
+   D[f](x) = sum_axes [-f(x-2e) + 16 f(x-e) - 30 f(x) + 16 f(x+e) - f(x+2e)] / 12,
+   with G of Eq. G taken over the same 12 neighbours and coefficients.
 9. The adaptive conformal step of Sec. 3.1 ("constant increases in physical
    time", dt_phys = a d-eta): with time_step = "physical" each time step
    takes d-eta = dt / a, a being the scale factor of the synchronised state at
@@ -144,12 +148,29 @@ def _neighbour(f: np.ndarray, dz: int, dy: int, dx: int) -> np.ndarray:
     return np.roll(f, shift=(-dz, -dy, -dx), axis=(-3, -2, -1))
 
 
+# The fourth-order stencil: (offset along one axis, coefficient) pairs.
+_FOURTH = ((1, 16.0 / 12.0), (2, -1.0 / 12.0))
+_FOURTH_CENTRE = -90.0 / 12.0
+
+
+def _axis_neighbour(f: np.ndarray, axis: int, k: int) -> np.ndarray:
+    """f at x + k e_axis (axis 0 = z, 1 = y, 2 = x of the last three)."""
+    return np.roll(f, shift=-k, axis=-3 + axis)
+
+
 def laplacian(f: np.ndarray, stencil: str = "7pt") -> np.ndarray:
-    """Eq. D: D[f](x) = sum over the 27 sites alpha around x of c_{d(alpha)} f(alpha).
+    """Eq. D: D[f](x) = sum over the 27 sites alpha around x of c_{d(alpha)} f(alpha)
+    (for '4th': over the centre and the 12 sites up to two steps along an axis).
 
     Works on a single field [z][y][x] or a stack [field][z][y][x].
     D carries no 1/dx^2; the flows divide by dx^2 themselves.
     """
+    if stencil == "4th":
+        out = _FOURTH_CENTRE * f
+        for axis in range(3):
+            for k, c in _FOURTH:
+                out = out + c * (_axis_neighbour(f, axis, k) + _axis_neighbour(f, axis, -k))
+        return out
     c = stencil_coefficients(stencil)
     out = np.zeros_like(f)
     for dz, dy, dx in _offsets():
@@ -161,6 +182,14 @@ def laplacian(f: np.ndarray, stencil: str = "7pt") -> np.ndarray:
 
 def gradient_G(f: np.ndarray, stencil: str = "7pt") -> np.ndarray:
     """Eq. G: G[f](x) = 1/2 sum_alpha c_{d(alpha)} (f(alpha) - f(x))^2."""
+    if stencil == "4th":
+        out = np.zeros_like(f)
+        for axis in range(3):
+            for k, c in _FOURTH:
+                for sgn in (1, -1):
+                    diff = _axis_neighbour(f, axis, sgn * k) - f
+                    out = out + 0.5 * c * diff * diff
+        return out
     c = stencil_coefficients(stencil)
     out = np.zeros_like(f)
     for dz, dy, dx in _offsets():

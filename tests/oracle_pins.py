@@ -69,7 +69,11 @@ def composition_error_pendulum(order: int, nsteps: int, T: float = 2.0) -> float
 
 def stencil_symbol(stencil: str, theta) -> float:
     """Fourier symbol of Eq. D for the coefficient classes c_0..c_3:
-    c0 + 2 c1 sum cos + 4 c2 sum_{d<e} cos cos + 8 c3 prod cos."""
+    c0 + 2 c1 sum cos + 4 c2 sum_{d<e} cos cos + 8 c3 prod cos;
+    for the fourth-order stencil, per axis (4 sin^2 t - 64 sin^2(t/2)) / 12
+    (from 1 - cos t = 2 sin^2(t/2) applied to (-2 cos 2t + 32 cos t - 30)/12)."""
+    if stencil == "4th":
+        return sum((4 * math.sin(t) ** 2 - 64 * math.sin(t / 2) ** 2) / 12.0 for t in theta)
     c = O.stencil_coefficients(stencil)
     cs = [math.cos(t) for t in theta]
     pair = cs[0] * cs[1] + cs[0] * cs[2] + cs[1] * cs[2]
@@ -453,3 +457,20 @@ def radiation_physical_recurrence(order: int, rho_r0: float = 3.0, a0: float = 1
         want = a_n + C * dt / a_n
         worst = max(worst, abs(st.a - want) / want)
     return worst
+
+
+# --- the fourth-order stencil -------------------------------------------------
+
+def fourth_order_accuracy_slope(mode=(1, 0, 0)) -> float:
+    """The symbol of the fourth-order stencil on a plane wave, lambda(theta),
+    against -|theta|^2: the difference must fall as theta^6 (fourth order in
+    dx relative to theta^2).  Log2 ratio of |lambda + theta^2| at n = 32 and
+    n = 64 (theta halves)."""
+    errs = []
+    for n in (32, 64):
+        f = plane_wave(n, mode)
+        D = O.laplacian(f, "4th")
+        lam = float(np.sum(D * f) / np.sum(f * f))     # the eigenvalue on this wave
+        th2 = sum((2 * math.pi * m / n) ** 2 for m in mode)
+        errs.append(abs(lam + th2))
+    return math.log2(errs[0] / errs[1])

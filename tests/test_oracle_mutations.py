@@ -132,11 +132,18 @@ def _checks():
         "dV": P.potential_derivative_error("chaotic2", (1.0, 1e4), (1.0, 0.3)) < 1e-8,
         "composition8": 7.7 < slope(P.composition_error_harmonic, (8, 10), (8, 20)) < 8.8,
         "field_stats": P.field_stats_error() < 1e-12,
+        "fourth_symbol": P.plane_wave_symbol_error("4th", 8, (1, 2, 3)) < 1e-13,
+        "fourth_order": abs(P.fourth_order_accuracy_slope() - 6.0) < 0.1,
         "physical_radiation": P.radiation_physical_recurrence(4) < 1e-14,
         "physical_static": P.static_physical_equivalence() == 0.0,
     }
     return out
 
+
+MUTATIONS_FOURTH = {
+    "fourth-order far weight +1/12": ((1, 16.0 / 12.0), (2, 1.0 / 12.0)),
+    "fourth-order near weight 15/12": ((1, 15.0 / 12.0), (2, -1.0 / 12.0)),
+}
 
 MUTATIONS = {
     "H1 sign": ("flow_H1", _mut_H1_sign),
@@ -174,5 +181,14 @@ def test_each_planted_mistake_fails_some_pin(name, monkeypatch):
             res = _checks()
         except (ValueError, FloatingPointError, OverflowError, ZeroDivisionError):
             return  # the mistake broke the oracle outright
+    failed = [k for k, ok in res.items() if not ok]
+    assert failed, f"planted mistake '{name}' passed every pin"
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_FOURTH))
+def test_each_planted_fourth_order_mistake_fails_some_pin(name, monkeypatch):
+    monkeypatch.setattr(O, "_FOURTH", MUTATIONS_FOURTH[name])
+    with np.errstate(all="ignore"):
+        res = _checks()
     failed = [k for k, ok in res.items() if not ok]
     assert failed, f"planted mistake '{name}' passed every pin"

@@ -201,3 +201,24 @@ def test_physical_steps_on_static_background_are_conformal_steps_of_dt_over_a():
 @pytest.mark.parametrize("order", [2, 4, 8])
 def test_physical_steps_radiation_recurrence(order):
     assert P.radiation_physical_recurrence(order) < 1e-14
+
+
+# --- the fourth-order stencil (Sec. 2.1: HLATTICE's, not printed) --------------
+
+@pytest.mark.parametrize("n,mode", [(8, (1, 2, 3)), (12, (5, 0, 2)), (9, (4, 4, 1))])
+def test_fourth_order_stencil_plane_wave_symbol(n, mode):
+    assert P.plane_wave_symbol_error("4th", n, mode) < 1e-13
+
+
+def test_fourth_order_stencil_is_fourth_order():
+    assert abs(P.fourth_order_accuracy_slope() - 6.0) < 0.1
+
+
+def test_fourth_order_stencil_stokes_identity():
+    assert P.stokes_error("4th") < 1e-13
+
+
+def test_fourth_order_stencil_free_mode_and_constraint_slope():
+    assert P.free_mode_transfer_error(4, stencil="4th") < 1e-12
+    e1, e2 = (P.constraint_error(4, dt, stencil="4th") for dt in (0.04, 0.02))
+    assert abs(math.log2(e1 / e2) - 4.0) < 0.4, (e1, e2)
