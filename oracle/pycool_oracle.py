@@ -205,7 +205,7 @@ def gradient_G(f: np.ndarray, stencil: str = "7pt") -> np.ndarray:
 # massive field used by the closed-form tests)
 # ---------------------------------------------------------------------------
 
-_MODEL_NF = {"free": 1, "free2": 2, "chaotic2": 2, "oscillon": 1, "qball": 2}
+_MODEL_NF = {"free": 1, "free2": 2, "chaotic2": 2, "oscillon": 1, "qball": 2, "phi4": 1}
 
 
 def model_nfields(model: str) -> int:
@@ -220,7 +220,13 @@ def potential(model: str, p: Sequence[float], phi: np.ndarray) -> np.ndarray:
     oscillon : V = m^2 phi^2/2 - lam phi^4/4 + g phi^6/6 p = (m2, lam, g)   (Sec. 3.2)
     qball    : V = m^2 |Phi|^2 (1 + K ln(|Phi|^2/M^2)),
                |Phi|^2 = (phi_1^2 + phi_2^2)/2           p = (m2, K, M)     (Sec. 3.3)
+    phi4     : V = m^2 phi^2/2 + lam phi^4/4               p = (m2, lam)
+               (a model outside Sec. 3, for potentials given at run time)
     """
+    if model == "phi4":
+        m2, lam = p[0], p[1]
+        ph = phi[0]
+        return 0.5 * m2 * ph ** 2 + 0.25 * lam * ph ** 4
     if model in ("free", "free2"):
         m2 = p[0]
         return 0.5 * m2 * np.sum(phi * phi, axis=0)
@@ -243,6 +249,8 @@ def potential(model: str, p: Sequence[float], phi: np.ndarray) -> np.ndarray:
 
 def potential_derivative(model: str, p: Sequence[float], phi: np.ndarray) -> np.ndarray:
     """dV/dphi_i at every site, shape (N_f, ...), derived by hand from V above."""
+    if model == "phi4":
+        return np.stack([p[0] * phi[0] + p[1] * phi[0] ** 3])
     if model in ("free", "free2"):
         return p[0] * phi
     if model == "chaotic2":

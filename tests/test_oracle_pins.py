@@ -96,6 +96,7 @@ def test_potential_values_golden():
     ("oscillon", (1.0, 1.0, 0.5), (-1.7,)),
     ("qball", (1.0, -0.1, 1.0), (1.3, 0.4)),
     ("qball", (1.0, -0.1, 1.0), (0.01, -0.02)),
+    ("phi4", (2.0, 3.0), (0.7,)),
 ])
 def test_potential_derivative_matches_difference_quotient(model, params, point):
     assert P.potential_derivative_error(model, params, point) < 1e-8
