@@ -85,8 +85,17 @@ typedef enum { PYCOOL_FP64 = 0, PYCOOL_SPLIT_FP32 = 1, PYCOOL_SPLIT_DD = 2 } pyc
 
 /* Discrete Laplacian D of Sec. 2.1, Eq. D (its coefficients are not printed):
  *   7PT   : c = (-6, 1, 0, 0) for (centre, face, edge, corner) neighbours,
- *   ISO27 : c = (-128, 14, 3, 1)/30 (isotropic at O(k^4)). */
-typedef enum { PYCOOL_STENCIL_7PT = 7, PYCOOL_STENCIL_ISO27 = 27 } pycool_stencil;
+ *   ISO27 : c = (-128, 14, 3, 1)/30 (isotropic at O(k^4)),
+ *   4TH   : the fourth-order stencil Sec. 2.1 mentions (HLATTICE's, not
+ *           printed): per axis (-1, 16, -30, 16, -1)/12 over two sites each
+ *           way, 13 points; symbol -k^2 + O(k^6).  FP64 and SPLIT_FP32 forms,
+ *           per-stage kernel (no persistent kernel, no linearised path);
+ *           n >= 4. */
+typedef enum {
+  PYCOOL_STENCIL_7PT = 7,
+  PYCOOL_STENCIL_4TH = 13,
+  PYCOOL_STENCIL_ISO27 = 27
+} pycool_stencil;
 
 /* Time step rule.
  *   CONFORMAL : every time step advances conformal time by dt (d-eta = dt).
@@ -190,6 +199,28 @@ pycool_status pycool_field_stats(pycool_sim* sim, int32_t field, double* mean,
  * (SPLIT_FP32: phi0 + dphi evaluated in float64).  on_device as for
  * set_initial; host copies synchronise first.  Either pointer may be NULL. */
 pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double* pi, int on_device);
+
+/* ---- potentials given at run time --------------------------------------------
+ * The analogue of the paper's model files (Sec. 2.4: the potential strings of
+ * a model are turned into CUDA code at run time): the caller gives V and
+ * dV/dphi_i as C expressions in the fields f0 (and f1) and the parameters
+ * p[0..7] (the config's params), e.g. "0.5*p[0]*f0*f0 + 0.25*p[1]*f0*f0*f0*f0";
+ * the library compiles them with NVRTC into one kernel for this device and
+ * returns a model id (>= 16) to put in pycool_config.model.  Such a model
+ * runs in the FP64 form with the 7-point or 27-point stencil, one stage as
+ * three launches (the library's drift, the compiled potential, the library's
+ * stencil, kick and sums); params[0] is taken as the mass scale m^2 of the
+ * stability check.  Not available with such models: the split forms, the
+ * server, the allocation-free sweep, the linearised evolution and
+ * pycool_energy_fields (E_INVALID).  The expressions are compiled into the
+ * caller's own process; a compile error returns E_INVALID and prints the
+ * compiler's log to stderr.  E_CUDA: the compiled kernel could not be
+ * loaded (no GPU); E_NOMEM: 64 models already defined in this process.
+ * pycool_model_source gives the generated kernel source (len: its length
+ * without the terminating zero; buf may be NULL). */
+pycool_status pycool_model_define(int32_t nf, const char* V, const char* const* dV,
+                                  int32_t* model_id);
+pycool_status pycool_model_source(int32_t model_id, char* buf, size_t cap, size_t* len);
 
 /* ---- output-interval observables (computed on the device) ------------------
  * pycool_energy_fields: the energy density and pressure at every site of the

@@ -33,14 +33,14 @@ OK, E_INVALID, E_UNSTABLE_DT, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, 
 # models, precisions, stencils
 MODEL_FREE, MODEL_CHAOTIC2, MODEL_OSCILLON, MODEL_QBALL = range(4)
 FP64, SPLIT_FP32, SPLIT_DD = 0, 1, 2
-STENCIL_7PT, STENCIL_ISO27 = 7, 27
+STENCIL_7PT, STENCIL_4TH, STENCIL_ISO27 = 7, 13, 27
 IC_WHITE = 0
 
 MODELS = {"free": MODEL_FREE, "chaotic2": MODEL_CHAOTIC2, "oscillon": MODEL_OSCILLON,
           "qball": MODEL_QBALL}
 MODEL_NF = {MODEL_FREE: 1, MODEL_CHAOTIC2: 2, MODEL_OSCILLON: 1, MODEL_QBALL: 2}
 PRECISIONS = {"fp64": FP64, "split_fp32": SPLIT_FP32, "split_dd": SPLIT_DD}
-STENCILS = {"7pt": STENCIL_7PT, "iso27": STENCIL_ISO27}
+STENCILS = {"7pt": STENCIL_7PT, "4th": STENCIL_4TH, "iso27": STENCIL_ISO27}
 
 
 class pycool_config(C.Structure):
@@ -113,6 +113,9 @@ def _load():
         "pycool_linear_modes": (S, [C.c_int32, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64), P]),
         "pycool_linear_growth": (S, [C.POINTER(pycool_config), C.c_double, C.c_double, P, P, P,
                                      C.c_int64, C.c_int64, P, P, P]),
+        "pycool_model_define": (S, [C.c_int32, C.c_char_p, C.POINTER(C.c_char_p),
+                                    C.POINTER(C.c_int32)]),
+        "pycool_model_source": (S, [C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
         "pycool_energy_fields": (S, [P, P, P, C.c_int]),
         "pycool_spectrum_bins": (C.c_int32, [C.c_int32]),
         "pycool_spectrum": (S, [P, C.c_int32, C.c_int32, P, P, C.c_int32]),
@@ -384,6 +387,25 @@ def pycool_linear_evolve(cfg: pycool_config, a0: float, pa0: float, phi, pi, ste
                                     pi_out.data_ptr(), bg.ctypes.data, _stream_ptr(stream)),
            "pycool_linear_evolve")
     return (bg[0], bg[1], bg[2:2 + nf].copy(), bg[2 + nf:].copy())
+
+
+def pycool_model_define(V: str, dV: Sequence[str]) -> int:
+    """Compile a potential given as C expressions (fields f0, f1; parameters
+    p[0..7]) and return its model id for make_config(model=...)."""
+    nf = len(dV)
+    arr = (C.c_char_p * nf)(*[e.encode() for e in dV])
+    mid = C.c_int32()
+    _check(lib.pycool_model_define(nf, V.encode(), arr, C.byref(mid)), "pycool_model_define")
+    MODEL_NF[mid.value] = nf
+    return mid.value
+
+
+def pycool_model_source(model_id: int) -> str:
+    n = C.c_size_t()
+    _check(lib.pycool_model_source(int(model_id), None, 0, C.byref(n)), "pycool_model_source")
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib.pycool_model_source(int(model_id), buf, n.value + 1, None), "pycool_model_source")
+    return buf.value.decode()
 
 
 def pycool_energy_fields(sim, shape_nnn, rho=None, P=None, on_device=False):

@@ -22,7 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpycool.so")
 SOURCES = ("api.cu", "sweep_fp64.cu", "sweep_split.cu", "persist_fp64.cu", "persist_split.cu",
-           "persist_dd.cu", "linear.cu", "observe.cu",
+           "persist_dd.cu", "linear.cu", "observe.cu", "runtime_model.cu",
            "server.cu", "noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -76,7 +76,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
         objs = list(ex.map(compile_one, srcs))
     libdir = os.path.join(cuda_home(), "lib64")
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcufft",
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcufft", "-lnvrtc",
            "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/pycool.h"
+#include "models.cuh"
 #include "internal.cuh"
 #include "runtime.h"
 
@@ -63,6 +64,7 @@ int stage_table(int order, double* w) {
 }
 
 int model_nfields(int model) {
+  if (model >= kRuntimeModelBase) return runtime_model_nfields(model);
   switch (model) {
     case PYCOOL_MODEL_FREE: return 1;
     case PYCOOL_MODEL_CHAOTIC2: return 2;
@@ -79,7 +81,8 @@ Layout layout_for(const pycool_config& c) {
   const int nf = model_nfields(c.model);
   const size_t S = (size_t)c.n * c.n * c.n;
   const size_t word = c.precision == PYCOOL_SPLIT_FP32 ? 4 : 8;
-  L.geo = choose_geometry(c.n, (int)word, nf);
+  const bool runtime = c.model >= kRuntimeModelBase;
+  L.geo = choose_geometry(c.n, (int)word, nf, c.stencil == PYCOOL_STENCIL_4TH || runtime);
   L.field_bytes = align256((size_t)nf * S * word);
   L.off_bg = 0;
   L.off_desc = align256(sizeof(Background));
@@ -88,6 +91,11 @@ Layout layout_for(const pycool_config& c) {
   workspace_layout(L.geo.ncta, L);
   L.off_prows = 0;
   L.off_punits = 0;
+  L.off_rt = 0;
+  if (runtime) {   // drifted fields, V' (N_f n^3 each) and V (n^3)
+    L.off_rt = align256(L.ws_bytes);
+    L.ws_bytes = L.off_rt + 2 * align256((size_t)nf * S * 8) + align256(S * 8);
+  }
   return L;
 }
 
@@ -329,8 +337,17 @@ pycool_status validate(const pycool_config* c) {
   if (c->precision != PYCOOL_FP64 && c->precision != PYCOOL_SPLIT_FP32 &&
       c->precision != PYCOOL_SPLIT_DD)
     return PYCOOL_E_INVALID;
-  if (c->stencil != PYCOOL_STENCIL_7PT && c->stencil != PYCOOL_STENCIL_ISO27)
+  if (c->stencil != PYCOOL_STENCIL_7PT && c->stencil != PYCOOL_STENCIL_ISO27 &&
+      c->stencil != PYCOOL_STENCIL_4TH)
     return PYCOOL_E_INVALID;
+  // the fourth-order stencil has a per-stage kernel in the FP64 and split-FP32 forms
+  if (c->stencil == PYCOOL_STENCIL_4TH && c->precision == PYCOOL_SPLIT_DD) return PYCOOL_E_INVALID;
+  // a potential given at run time: FP64 form, 7-point or 27-point stencil
+  if (c->model >= kRuntimeModelBase &&
+      (c->precision != PYCOOL_FP64 || c->stencil == PYCOOL_STENCIL_4TH))
+    return PYCOOL_E_INVALID;
+  // its +-2 neighbours wrap once around the lattice at most: n >= 4
+  if (c->stencil == PYCOOL_STENCIL_4TH && c->n < 4) return PYCOOL_E_INVALID;
   if (c->time_step != PYCOOL_TIME_CONFORMAL && c->time_step != PYCOOL_TIME_PHYSICAL)
     return PYCOOL_E_INVALID;
   if (!(c->L > 0.0) || !std::isfinite(c->L)) return PYCOOL_E_INVALID;
@@ -341,13 +358,14 @@ pycool_status validate(const pycool_config* c) {
     if (!std::isfinite(c->params[i])) return PYCOOL_E_INVALID;
   if (c->model == PYCOOL_MODEL_QBALL && !(c->params[2] > 0.0)) return PYCOOL_E_INVALID;
   // linear stability of every stage at a = 1: |h| omega_max < 2,
-  // omega_max^2 = max|symbol of D| / dx^2 + |m2|  (7pt: 12, iso27: 92/15)
+  // omega_max^2 = max|symbol of D| / dx^2 + |m2|  (7pt: 12, iso27: 92/15, 4th: 16)
   double w[kMaxStages];
   const int s = stage_table(c->order, w);
   double wmax = 0.0;
   for (int i = 0; i < s; ++i) wmax = std::fmax(wmax, std::fabs(w[i]));
   const double dx = c->L / c->n;
-  const double sym = c->stencil == PYCOOL_STENCIL_7PT ? 12.0 : 92.0 / 15.0;
+  const double sym = c->stencil == PYCOOL_STENCIL_7PT ? 12.0
+                    : (c->stencil == PYCOOL_STENCIL_4TH ? 16.0 : 92.0 / 15.0);
   const double om = std::sqrt(sym / (dx * dx) + std::fabs(c->params[0]));
   if (std::fabs(c->dt) * wmax * om >= 2.0) return PYCOOL_E_UNSTABLE_DT;
   return PYCOOL_OK;
@@ -357,7 +375,8 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   std::memset(&d, 0, sizeof(d));
   d.n = c.n;
   d.nf = model_nfields(c.model);
-  d.model = c.model;
+  d.model = c.model >= kRuntimeModelBase ? (d.nf == 1 ? M_RUNTIME1 : M_RUNTIME2) : c.model;
+  d.rt_index = c.model >= kRuntimeModelBase ? c.model - kRuntimeModelBase : -1;
   d.stencil = c.stencil;
   d.prec = c.precision == PYCOOL_SPLIT_FP32 ? PREC_SPLIT
            : (c.precision == PYCOOL_SPLIT_DD ? PREC_DD : PREC_FP64);
@@ -394,6 +413,12 @@ void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state,
   d.gticket = (unsigned int*)(ws + L.off_gticket);
   d.gpartials = (double*)(ws + L.off_gpartials);
   d.ngroups = (L.geo.ncta + kGroup - 1) / kGroup;
+  if (L.off_rt) {
+    const size_t fb = align256((size_t)d.nf * (size_t)d.S * 8);
+    d.rt_phis = (double*)(ws + L.off_rt);
+    d.rt_dV = (double*)(ws + L.off_rt + fb);
+    d.rt_V = (double*)(ws + L.off_rt + 2 * fb);
+  }
 }
 
 // TMA descriptors for the four field buffers (see SimDesc::tmap).  The driver
@@ -485,6 +510,7 @@ cudaError_t launch_persist(const SimDesc& d, const PParams& p, int grid, cudaStr
 }
 
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s) {
+  if (d.model == M_RUNTIME1 || d.model == M_RUNTIME2) return launch_runtime_stage(d, t, grid, s);
   if (d.prec == PREC_SPLIT) return launch_sweep_split(d.model, d.stencil, d.vx, d.tma, t, grid, s);
   // the split-DD form runs on the persistent kernel only (no per-stage instance)
   if (d.prec == PREC_DD) return grid == 0 ? cudaSuccess : cudaErrorInvalidValue;
@@ -1130,6 +1156,7 @@ static pycool_status observed_state(pycool_sim* sim, Background* b) {
 PYCOOL_API pycool_status pycool_energy_fields(pycool_sim* sim, double* rho, double* P,
                                               int on_device) {
   if (!sim || !rho || !P) return PYCOOL_E_INVALID;
+  if (sim->cfg.model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // V is not on the device
   if (sim->poisoned) return PYCOOL_E_STATE;
   Background b;
   pycool_status st = observed_state(sim, &b);

@@ -25,6 +25,8 @@ constexpr int kMaxTY = 8;          // tile height (y)
 constexpr int kNQ = 12;            // reduction slots per block
 constexpr int kMaxMembers = 64;    // simulations per batched launch
 constexpr int kGroup = 32;         // blocks per first-level fold group
+constexpr int kRuntimeModelBase = 16;         // first id of a potential given at run time
+constexpr int kRuntimeModelMax = 64;          // such potentials per process
 constexpr long long kWaitLimit = 1ll << 31;   // default limit of a device-side wait
                                               // (SM clocks, about a second)
 
@@ -90,6 +92,11 @@ struct alignas(64) SimDesc {
   int32_t ngroups;
   int32_t* fault;             // set when a device-side wait gave up
   Background* bg;
+  // potentials compiled at run time: the drifted fields, V' and V of a stage
+  double* rt_phis;            // N_f n^3
+  double* rt_dV;              // N_f n^3
+  double* rt_V;               // n^3
+  int32_t rt_index;           // the registry entry of the potential (-1: none)
 };
 
 struct LaunchTable {
@@ -108,9 +115,10 @@ struct Geometry {
   int tma, vx, txt, tx, ty, zc, tiles_x, tiles_y, zchunks, ncta;
 };
 
-inline Geometry choose_geometry(int n, int word, int nf) {
+// plain: the plain-load geometry whatever n (the fourth-order stencil's kernel).
+inline Geometry choose_geometry(int n, int word, int nf, bool plain = false) {
   Geometry g;
-  g.tma = (n % 32 == 0) ? 1 : 0;
+  g.tma = (n % 32 == 0 && !plain) ? 1 : 0;
   g.vx = 1;
   if (g.tma) {
     for (int v = 16 / (word * nf); v >= 2; v /= 2)

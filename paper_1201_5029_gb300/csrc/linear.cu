@@ -330,6 +330,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_gr
     void* cuda_stream) {
   const pycool_status v = validate(cfg);
   if (v != PYCOOL_OK) return v;
+  if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // no second derivatives
   if (!phi0 || !pi0 || !k2 || !T || !background || nk < 1 || steps < 0 || !(a0 > 0.0) ||
       !std::isfinite(pa0) || cfg->time_step != PYCOOL_TIME_CONFORMAL)
     return PYCOOL_E_INVALID;
@@ -384,9 +385,10 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
     int64_t steps, double* phi_out, double* pi_out, double* background, void* cuda_stream) {
   const pycool_status v = validate(cfg);
   if (v != PYCOOL_OK) return v;
+  if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // no second derivatives
   if (!phi || !pi || !phi_out || !pi_out || !background || steps < 0 || !(a0 > 0.0) ||
       !std::isfinite(pa0) || cfg->n < 2 || cfg->n > 512 ||
-      cfg->time_step != PYCOOL_TIME_CONFORMAL)
+      cfg->time_step != PYCOOL_TIME_CONFORMAL || cfg->stencil == PYCOOL_STENCIL_4TH)
     return PYCOOL_E_INVALID;
   {  // the outputs serve as scratch while the inputs are read: no overlap
     const size_t bytes = (size_t)model_nfields(cfg->model) * cfg->n * cfg->n * cfg->n * 8;

@@ -25,7 +25,10 @@
 
 namespace pycool {
 
-enum ModelId { M_FREE = 0, M_CHAOTIC2 = 1, M_OSCILLON = 2, M_QBALL = 3 };
+enum ModelId { M_FREE = 0, M_CHAOTIC2 = 1, M_OSCILLON = 2, M_QBALL = 3,
+               // potentials compiled at run time (pycool_model_define), 1 or 2 fields:
+               // their V and V' come from arrays the compiled kernel fills
+               M_RUNTIME1 = 4, M_RUNTIME2 = 5 };
 
 template <int M> struct Pot;
 
@@ -227,5 +230,17 @@ template <> struct Pot<M_QBALL> {
     }
   }
 };
+
+// ---------------------------------------------------------------- RUNTIME
+// A potential given at run time: its values reach the sweep through arrays
+// (rt_kick), so these records carry nothing.
+template <int NFIELDS> struct PotRuntime {
+  static constexpr int NF = NFIELDS;
+  struct K {};
+  struct SplitK {};
+  __device__ static K prep(const double*, const double*) { return K{}; }
+};
+template <> struct Pot<M_RUNTIME1> : PotRuntime<1> {};
+template <> struct Pot<M_RUNTIME2> : PotRuntime<2> {};
 
 }  // namespace pycool

@@ -86,7 +86,8 @@ PYCOOL_API pycool_status pycool_sweep_noalloc(const pycool_config* cfg, const do
   pycool_status st = validate(cfg);
   if (st != PYCOOL_OK) return st;
   // FP64 form, conformal steps (the state record carries no physical-time step)
-  if (cfg->precision != PYCOOL_FP64 || cfg->time_step != PYCOOL_TIME_CONFORMAL)
+  if (cfg->precision != PYCOOL_FP64 || cfg->time_step != PYCOOL_TIME_CONFORMAL ||
+      cfg->model >= kRuntimeModelBase)
     return PYCOOL_E_INVALID;
   if (!state || !phi_in || !pi_in || !phi_out || (!flush && !pi_out)) return PYCOOL_E_INVALID;
   if (!aligned16(phi_in) || !aligned16(pi_in) || !aligned16(phi_out) ||

@@ -13,6 +13,11 @@ namespace pycool {
 //   workspace : [ticket, fault word (256 B)][group tickets][block partials: ncta * kNQ
 //               doubles][group partials: ngroups * kNQ doubles]; the counters
 //               [0, off_partials) must be zero before a launch.
+// Potentials given at run time (runtime_model.cu): fields of a registered
+// model id (-1 if unknown), and one stage of such a simulation.
+int runtime_model_nfields(int id);
+cudaError_t launch_runtime_stage(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s);
+
 struct Layout {
   Geometry geo;
   size_t field_bytes;
@@ -20,6 +25,7 @@ struct Layout {
   size_t off_ticket, off_gticket, off_partials, off_gpartials, ws_bytes;
   size_t off_prows;   // single-simulation API: rows of the persistent kernel (0 = none)
   size_t off_punits;  // single-simulation API: the persistent kernel's unit table
+  size_t off_rt;      // runtime potentials: drifted fields, V', V (0 = none)
 };
 
 // Workspace layout of a launch of `ncta` blocks (fills the off_* / ws_bytes fields).

@@ -500,6 +500,7 @@ PYCOOL_API pycool_status pycool_server_submit(pycool_server* s, const pycool_con
   const pycool_status st = validate(cfg);
   if (st != PYCOOL_OK) return st;
   if (cfg->precision == PYCOOL_SPLIT_DD) return PYCOOL_E_INVALID;   // no per-stage DD kernel
+  if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;     // one launch per group only
   if (!std::isfinite(ic->noise) || ic->noise < 0.0) return PYCOOL_E_INVALID;
   if (footprint(*cfg) > s->arena.capacity()) return PYCOOL_E_NOMEM;  // could never fit
   Request r;

@@ -1625,6 +1625,236 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_plain(const LaunchTable tab
   finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sout, &s_last);
 }
 
+// ---------------------------------------------------------------------------
+// Fourth-order stencil (13 points: the centre and two sites each way along
+// every axis), per-axis weights (-1, 16, -30, 16, -1)/12: a plain-load sweep.
+// Each thread owns one (x, y) column of a tile and marches z with a register
+// queue of its column's drifted values at z-2 .. z+2; the eight in-plane
+// neighbours are read (and drifted) from global memory (L1/L2), the column's
+// own momenta from its queue.  The kick, sums and block finish are those of
+// the other kernels (Ctx::site, block_partials, finish_block).
+// ---------------------------------------------------------------------------
+template <int MODEL, int PREC>
+__global__ void __launch_bounds__(kThreads, 2) sweep_wide(const LaunchTable tab) {
+  using C = Ctx<MODEL, PREC>;
+  using T = typename C::T;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  __shared__ double sred[(kThreads / 32) * NQ];
+  __shared__ double sout[NQ];
+  __shared__ int s_last;
+  __shared__ C s_ctx;
+
+  const int mem = member_of(tab, blockIdx.x);
+  const SimDesc& d = *tab.desc[mem];
+  const int cta = blockIdx.x - tab.cta_offset[mem];
+  const Background& bgr = *d.bg;
+  const int mode = bgr.mode;
+  if (mode == MODE_IDLE) return;
+
+  const int n = d.n;
+  const int TX = d.txt, TY = d.ty;
+  const int tile = cta % (d.tiles_x * d.tiles_y);
+  const int zch = cta / (d.tiles_x * d.tiles_y);
+  const int x0 = (tile % d.tiles_x) * TX;
+  const int y0 = (tile / d.tiles_x) * TY;
+  const int z0 = zch * d.zc;
+  const int zend = min(n, z0 + d.zc);
+  const int tid = threadIdx.x;
+  const bool active = tid < TX * TY;
+  const int gx = x0 + (active ? tid % TX : 0), gy = y0 + (active ? tid / TX : 0);
+  const bool valid = active && gx < n && gy < n;
+  const size_t S = (size_t)d.S, nn = (size_t)n * n;
+
+  if (tid == 0) s_ctx.init(bgr, d, mode);
+  __syncthreads();
+  const C cx = s_ctx;
+  const int ib = bgr.cur;
+  const T* __restrict__ phi_in = (const T*)d.phi[ib & 1];
+  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
+  const T* __restrict__ pi_in = (const T*)d.pi[(ib >> 1) & 1];
+  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
+  const T w1 = (T)(16.0 / 12.0), w2 = (T)(-1.0 / 12.0), w0 = (T)(-90.0 / 12.0);
+  T Mf[NF];   // split form: re-centring of the drifted field
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Mf[f] = madd(cx.cdrift, cx.mu_pi[f], cx.mu_phi[f]);
+
+  // drifted field value (re-centred momenta in the split form: the stencil
+  // works on phi + c pi, D of a constant being zero)
+  auto drifted = [&](int f, int z, int y, int x) -> T {
+    const size_t o = (size_t)f * S + (size_t)wrapi(z, n) * nn + (size_t)wrapi(y, n) * n + wrapi(x, n);
+    return madd(cx.cdrift, pi_in[o], phi_in[o]);
+  };
+  Acc<T> acc[NQ];
+  T accd_s[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { acc[q].zero(); accd_s[q] = (T)0; }
+
+  if (valid) {
+    T qz[NF][5], qp[NF];   // column queue z-2 .. z+2; momentum at z
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) qz[f][k] = drifted(f, z0 - 2 + k, gy, gx);
+    for (int z = z0; z < zend; ++z) {
+      T phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        qz[f][4] = drifted(f, z + 2, gy, gx);
+        const size_t own = (size_t)f * S + (size_t)z * nn + (size_t)gy * n + gx;
+        qp[f] = pi_in[own];
+        if constexpr (PREC == PREC_SPLIT) qp[f] -= cx.mu_pi[f];
+        const T near = (qz[f][1] + qz[f][3]) +
+                       ((drifted(f, z, gy - 1, gx) + drifted(f, z, gy + 1, gx)) +
+                        (drifted(f, z, gy, gx - 1) + drifted(f, z, gy, gx + 1)));
+        const T far = (qz[f][0] + qz[f][4]) +
+                      ((drifted(f, z, gy - 2, gx) + drifted(f, z, gy + 2, gx)) +
+                       (drifted(f, z, gy, gx - 2) + drifted(f, z, gy, gx + 2)));
+        Dj[f] = madd(w0, qz[f][2], madd(w2, far, w1 * near));
+        phj[f] = qz[f][2];
+        if constexpr (PREC == PREC_SPLIT) phj[f] -= Mf[f];
+        pmj[f] = qp[f];
+      }
+      T ps_local[NQ];
+      T* ps = ps_local;
+      if constexpr (PREC == PREC_FP64) {
+        ps = accd_s;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) ps_local[i] = (T)0;
+      }
+      cx.site(mode, phj, Dj, pmj, pnj, ps);
+      const size_t o = (size_t)z * nn + (size_t)gy * n + gx;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        phi_out[f * S + o] = phj[f];
+        if (mode == MODE_SWEEP) pi_out[f * S + o] = pnj[f];
+      }
+      if constexpr (PREC == PREC_SPLIT) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i].add(ps_local[i]);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qz[f][k] = qz[f][k + 1];
+    }
+  }
+  block_partials<PREC, NQ, T>(acc, accd_s, sred, sout);
+  finish_block<MODEL, PREC>(s_ctx, d, mode, cta, sout, &s_last);
+}
+
+// ---------------------------------------------------------------------------
+// Potentials compiled at run time (FP64 form, per-stage, plain loads).  A
+// stage is three launches: rt_drift (phi* = phi + c pi into d.rt_phis), the
+// compiled kernel (V'(phi*) and V(phi*) into d.rt_dV, d.rt_V), and rt_kick
+// (the Laplacian of phi*, the kick, the sums and the block finish, which
+// advances the Background).  Both library kernels derive the stage's
+// coefficients from the same Background record, which only the last block of
+// rt_kick changes.
+// ---------------------------------------------------------------------------
+template <int MODEL>
+__global__ void __launch_bounds__(kThreads) rt_drift(const LaunchTable tab) {
+  using C = Ctx<MODEL, PREC_FP64>;
+  constexpr int NF = C::NF;
+  __shared__ C s_ctx;
+  const SimDesc& d = *tab.desc[0];
+  const Background& bgr = *d.bg;
+  const int mode = bgr.mode;
+  if (mode == MODE_IDLE) return;
+  if (threadIdx.x == 0) s_ctx.init(bgr, d, mode);
+  __syncthreads();
+  const double c = s_ctx.cdrift;
+  const int ib = bgr.cur;
+  const double* __restrict__ phi = (const double*)d.phi[ib & 1];
+  const double* __restrict__ pi = (const double*)d.pi[(ib >> 1) & 1];
+  const size_t total = (size_t)NF * (size_t)d.S;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x)
+    d.rt_phis[i] = fma(c, pi[i], phi[i]);
+}
+
+template <int MODEL, int STENCIL>
+__global__ void __launch_bounds__(kThreads, 2) rt_kick(const LaunchTable tab) {
+  using C = Ctx<MODEL, PREC_FP64>;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  __shared__ double sred[(kThreads / 32) * NQ];
+  __shared__ double sout[NQ];
+  __shared__ int s_last;
+  __shared__ C s_ctx;
+  const SimDesc& d = *tab.desc[0];
+  const int cta = blockIdx.x;
+  const Background& bgr = *d.bg;
+  const int mode = bgr.mode;
+  if (mode == MODE_IDLE) return;
+  const int n = d.n;
+  const int TX = d.txt, TY = d.ty;
+  const int tile = cta % (d.tiles_x * d.tiles_y);
+  const int zch = cta / (d.tiles_x * d.tiles_y);
+  const int x0 = (tile % d.tiles_x) * TX, y0 = (tile / d.tiles_x) * TY;
+  const int z0 = zch * d.zc, zend = min(n, z0 + d.zc);
+  const int tid = threadIdx.x;
+  const bool active = tid < TX * TY;
+  const int gx = x0 + (active ? tid % TX : 0), gy = y0 + (active ? tid / TX : 0);
+  const bool valid = active && gx < n && gy < n;
+  const size_t S = (size_t)d.S, nn = (size_t)n * n;
+  if (tid == 0) s_ctx.init(bgr, d, mode);
+  __syncthreads();
+  const C cx = s_ctx;
+  const int ib = bgr.cur;
+  double* __restrict__ phi_out = (double*)d.phi[(ib & 1) ^ 1];
+  const double* __restrict__ pi_in = (const double*)d.pi[(ib >> 1) & 1];
+  double* __restrict__ pi_out = (double*)d.pi[((ib >> 1) & 1) ^ 1];
+  const double c0 = CORNERS ? -128.0 / 30.0 : -6.0, c1 = CORNERS ? 14.0 / 30.0 : 1.0;
+  const double c2 = CORNERS ? 3.0 / 30.0 : 0.0, c3 = CORNERS ? 1.0 / 30.0 : 0.0;
+  double ps[NQ];
+  Acc<double> acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) ps[q] = 0.0;
+  if (valid) {
+    for (int z = z0; z < zend; ++z) {
+      const size_t o = (size_t)z * nn + (size_t)gy * n + gx;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const double* ph = d.rt_phis + (size_t)f * S;
+        double faces = 0.0, edges = 0.0, corners = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int cls = (dz != 0) + (dy != 0) + (dx != 0);
+              if (cls == 0 || (!CORNERS && cls > 1)) continue;
+              const double v = ph[(size_t)wrapi(z + dz, n) * nn + (size_t)wrapi(gy + dy, n) * n +
+                                  wrapi(gx + dx, n)];
+              if (cls == 1) faces += v; else if (cls == 2) edges += v; else corners += v;
+            }
+        const double ctr = ph[o];
+        const double D = fma(c3, corners, fma(c2, edges, fma(c1, faces, c0 * ctr)));
+        const double pim = pi_in[(size_t)f * S + o];
+        double pin = pim;
+        if (mode == MODE_SWEEP) {
+          pin = fma(cx.kD, D, fma(-cx.kV, d.rt_dV[(size_t)f * S + o], pim));
+          pi_out[(size_t)f * S + o] = pin;
+        }
+        phi_out[(size_t)f * S + o] = ctr;
+        ps[SL::PI2 + f] = fma(pin, pin, ps[SL::PI2 + f]);
+        ps[SL::PHID + f] = fma(ctr, D, ps[SL::PHID + f]);
+        if (mode != MODE_SWEEP) {
+          const double dd = ctr - cx.shiftK[f];
+          ps[SL::DPHI + f] += dd;
+          ps[SL::DPHI2 + f] = fma(dd, dd, ps[SL::DPHI2 + f]);
+        }
+      }
+      ps[SL::V] += d.rt_V[o];
+    }
+  }
+  block_partials<PREC_FP64, NQ, double>(acc, ps, sred, sout);
+  finish_block<MODEL, PREC_FP64>(s_ctx, d, mode, cta, sout, &s_last);
+}
+
 // Launch helper: dispatch (model, stencil, path/vx) at runtime to an instance.
 // grid == 0 only prepares the instance (its shared-memory attribute), so that
 // callers can do it before a stream capture.
@@ -1638,6 +1868,14 @@ cudaError_t launch_sweep_impl(int model, int stencil, int vx, int tma, const Lau
     sweep_plain<M, ST, PREC><<<g, b, 0, s>>>(t);                         \
     return cudaGetLastError();                                           \
   }
+#define PYCOOL_WIDE(M)                                                   \
+  if (model == M && stencil == 13) {                                     \
+    if (grid == 0) return cudaSuccess;                                   \
+    sweep_wide<M, PREC><<<g, b, 0, s>>>(t);                              \
+    return cudaGetLastError();                                           \
+  }
+  PYCOOL_WIDE(M_FREE) PYCOOL_WIDE(M_CHAOTIC2) PYCOOL_WIDE(M_OSCILLON) PYCOOL_WIDE(M_QBALL)
+#undef PYCOOL_WIDE
 #define PYCOOL_TMA(M, ST, V)                                             \
   if constexpr (V * Pot<M>::NF * (PREC == PREC_FP64 ? 8 : 4) <= 16) {    \
     if (tma && model == M && stencil == ST && vx == V) {                 \

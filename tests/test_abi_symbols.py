@@ -58,3 +58,10 @@ def test_fault_injection_calls_check_their_arguments_without_gpu():
     assert P.pycool_debug_barrier_stall(None, 1000) == P.E_INVALID
     assert P.pycool_server_cancel(None, 1) == P.E_INVALID
     assert P.pycool_strerror(P.E_CANCELLED) == "request cancelled"
+
+
+def test_fourth_order_stencil_needs_four_sites_per_axis():
+    import paper_1201_5029_gb300 as P
+    for n, want in ((3, P.E_INVALID), (4, P.OK)):
+        cfg = P.make_config(n, 4.0, "chaotic2", (1.0, 1.0), 0.01, order=2, stencil="4th")
+        assert P.lib.pycool_query_bytes(ctypes.byref(cfg), None, None) == want

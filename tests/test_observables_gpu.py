@@ -3,9 +3,13 @@
 pycool_energy_fields (rho(x), P(x) of Eq. rho-pres with the stencil G of Eq.
 G) and pycool_spectrum (shell-binned power spectrum, Sec. 2.4) at the state a
 few steps into the preheating, oscillon and Q-ball workloads, for each form.
-The FP64 and split-DD forms agree with the oracle (on the oracle's evolved
-state) to 1e-10 relative per site and per shell; the split-FP32 form at its
-float32 fluctuation accuracy (1e-4 of the gradient and spectrum scales)."""
+Each side evaluates the observables on its own evolved state, so the
+difference carries the states' difference: for the FP64 and split-DD forms the
+per-site fields agree at the scale of their fluctuations within the state
+parity bound (gpu_helpers.fluct_tolerances for the stages run, never below
+1e-10) and the shells (relative to the total power, which is the lattice mean
+of the field squared) to 1e-10; the split-FP32 form at its float32
+fluctuation accuracy, 1e-4 of the same scales."""
 import numpy as np
 import pytest
 
@@ -43,23 +47,31 @@ def test_energy_fields_and_spectra(case, precision, tol):
     sim.evolve(case["steps"])
     rho, Pg = sim.energy_fields()
     # the fluctuating parts (rho - <rho>) at their own scale, and the means
+    stages = int(sim.energies()["sweeps_done"]) + 1
     for g, o in ((rho, case["rho"]), (Pg, case["P"])):
         scale = np.max(np.abs(o - o.mean()))
         err = np.max(np.abs(g - o)) / scale
-        print(f"\n{w['model']} {precision}: field error {err:.1e} of fluctuation scale {scale:.1e}")
-        assert err < tol
+        bound = max(tol, G.fluct_tolerances(o[None], stages, tol)[0]) if tol < 1e-6 else tol
+        print(f"\n{w['model']} {precision}: field error {err:.1e} of fluctuation scale "
+              f"{scale:.1e} (bound {bound:.1e})")
+        assert err < bound
     e = sim.energies()
     assert abs(rho.mean() - e["rho"]) <= 1e-12 * abs(e["rho"]) + 1e-14 * np.max(np.abs(rho))
     for which in (0, 1):
         for f in range(case["phi"].shape[0]):
             pw, cnt = sim.spectrum(which, f)
             po, co = case["spec"][which][f]
+            # a spectrum is quadratic in the field: twice the field's bound
+            arr = (case["st"].phi, case["st"].pi)[which][f][None]
+            sb = max(tol, 2 * G.fluct_tolerances(arr, stages, tol)[0]) if tol < 1e-6 else tol
             assert np.array_equal(cnt, co)
-            # shell 0 carries the mean squared; the others the fluctuations
-            e0 = abs(pw[0] - po[0]) / max(po[0], 1e-300)
+            # shell 0 (the mean squared) against the total power; the other
+            # shells (the fluctuations) against their largest
+            e0 = abs(pw[0] - po[0]) / po.sum()
             e1 = np.max(np.abs(pw[1:] - po[1:])) / np.max(po[1:])
-            print(f"  spectrum which={which} f={f}: shell0 {e0:.1e} shells {e1:.1e}")
-            assert e0 < tol and e1 < tol
+            print(f"  spectrum which={which} f={f}: shell0 {e0:.1e} shells {e1:.1e} "
+                  f"(bound {sb:.1e})")
+            assert e0 < sb and e1 < sb
     sim.close()
 
 
