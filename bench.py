@@ -445,6 +445,97 @@ def linear_leg(P, w, steps):
             "finite": ok, "a_end": bg[0], "config": _config(w)}
 
 
+# C expressions of the compiled-in potentials, for the runtime-compiled leg
+RUNTIME_EXPRESSIONS = {
+    "chaotic2": ("0.5*p[0]*f0*f0 + 0.5*p[1]*f0*f0*f1*f1",
+                 ("p[0]*f0 + p[1]*f0*f1*f1", "p[1]*f0*f0*f1")),
+    "oscillon": ("0.5*p[0]*f0*f0 - 0.25*p[1]*f0*f0*f0*f0 + p[2]/6.0*f0*f0*f0*f0*f0*f0",
+                 ("p[0]*f0 - p[1]*f0*f0*f0 + p[2]*f0*f0*f0*f0*f0",)),
+}
+
+
+def _event_ms(torch, stream, fn, reps):
+    """Mean CUDA-event time (ms) of fn() over reps calls on `stream`, after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def next_rows_leg(P, torch, I, w, stream, steps=3):
+    """The paths beyond the fused step, each timed on the workload's lattice:
+      linear_evolve : the linearised evolution end to end on the device
+                      (means, FFTs, growth functions of every distinct
+                      k_eff^2 for `steps` steps, per-mode apply, inverse FFTs);
+      observables   : per-site energy density and pressure, and the spectra of
+                      every field (FP64 state of the workload);
+      fourth_order  : `steps` time steps with the 13-point stencil (per-stage
+                      kernel), FP64;
+      runtime_model : `steps` time steps of a potential compiled at run time
+                      (the workload's own potential as C expressions), FP64.
+    Each figure is site-updates/s (n^3 x stages x steps / time) or, for the
+    observables, sites/s and GB/s of their algorithmic bytes."""
+    import numpy as np
+    out = {}
+    n = w["n"]
+    S = n ** 3
+    nf = len(w["background"])
+    stages = P.pycool_stages_per_step(w["order"])
+    phi, pi = I.initial_fields(w)
+    dphi = torch.from_numpy(phi).cuda()
+    dpi = torch.from_numpy(pi).cuda()
+    try:
+        cfg = P.config_from_workload(w)
+        with P.Simulation(P.config_from_workload(w)) as sim:
+            sim.set_initial(phi, pi)
+            pa0 = sim.energies()["pa"]
+            # observables of the initial FP64 state
+            r = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+            q = torch.empty_like(r)
+            ms_e = _event_ms(torch, stream, lambda: sim.energy_fields(r, q, on_device=True), 3)
+            sim.spectrum(0, 0)                     # the first call makes the plan and tables
+            t0 = time.perf_counter()
+            for f in range(nf):
+                sim.spectrum(0, f)
+            ms_s = (time.perf_counter() - t0) * 1e3 / nf
+        e_bytes = S * (2 * nf * 8 + 2 * 8)      # read phi, pi of every field; write rho, P
+        out["observables"] = {"energy_fields_ms": ms_e, "energy_fields_gbs": e_bytes / ms_e / 1e6,
+                              "spectrum_ms_per_field": ms_s,
+                              "note": "energy fields: CUDA events; spectrum: wall time of one "
+                                      "pycool_spectrum call (FFT, shell sums, copy back)"}
+        outp, outq = torch.empty_like(dphi), torch.empty_like(dpi)
+        ms_l = _event_ms(torch, stream,
+                         lambda: P.pycool_linear_evolve(cfg, 1.0, pa0, dphi, dpi, steps, outp,
+                                                        outq, stream), 2)
+        out["linear_evolve"] = {"value": S * stages * steps / (ms_l / 1e3), "unit": UNIT,
+                                "ms_per_call": ms_l, "steps": steps,
+                                "note": "whole call incl. its device allocations, after one "
+                                        "call that made the lattice's tables and FFT plans"}
+    except Exception as e:  # noqa: BLE001
+        out["error"] = f"{type(e).__name__}: {e}"
+    for name, make in (("fourth_order", lambda: P.config_from_workload(w, stencil="4th")),
+                       ("runtime_model", lambda: P.make_config(
+                           n, w["L"], P.pycool_model_define(*RUNTIME_EXPRESSIONS[w["model"]]),
+                           w["params"], w["dt"], order=w["order"], mpl=w["mpl"]))):
+        if name == "runtime_model" and w["model"] not in RUNTIME_EXPRESSIONS:
+            continue
+        try:
+            with P.Simulation(make(), stream=stream) as sim:
+                sim.set_initial(phi, pi)
+                ms = _event_ms(torch, stream, lambda: sim.evolve(1), steps)
+                st = sim.sync()
+            out[name] = {"value": S * stages / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "status": st, "form": "fp64"}
+        except Exception as e:  # noqa: BLE001
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
 def _config(w):
     state = 2 * len(w["background"]) * w["n"] ** 3 * 8
     return {"workload": f"{w['name']}: {w['model']} {len(w['background'])}-field, "
@@ -501,6 +592,11 @@ def main():
                     help="time the linearised evolution's growth functions instead")
     ap.add_argument("--no-linear", action="store_true",
                     help="leave the growth-function measurement out of the main line")
+    ap.add_argument("--next-rows", default="preheat128",
+                    help="workload of the linearised / observables / fourth-order / runtime-model "
+                         "timings (empty: leave them out)")
+    ap.add_argument("--only-next-rows", action="store_true",
+                    help="time only those paths (profiling them)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -524,6 +620,13 @@ def main():
     if args.linear:
         import paper_1201_5029_gb300 as P
         print(json.dumps(linear_leg(P, w, args.steps)), flush=True)
+        return 0
+    if args.only_next_rows:
+        import torch
+        import paper_1201_5029_gb300 as P
+        wn = I.workload(args.next_rows)
+        wn["name"] = args.next_rows
+        print(json.dumps(next_rows_leg(P, torch, I, wn, torch.cuda.current_stream())), flush=True)
         return 0
 
     import torch
@@ -601,6 +704,13 @@ def main():
         except Exception as e:  # noqa: BLE001
             linear = {"error": f"{type(e).__name__}: {e}"}
 
+    next_rows = None
+    if rank == 0 and args.next_rows:
+        wn = I.workload(args.next_rows)
+        wn["name"] = args.next_rows
+        next_rows = next_rows_leg(P, torch, I, wn, stream)
+        next_rows["workload"] = _config(wn)["workload"]
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -621,6 +731,7 @@ def main():
             "e2e": e2e,
             "serving": serving,
             "linear": linear,
+            "next_rows": next_rows,
             "gpu_launches": int(launches),
             "kernel_source_hash": kernel_source_hash(),
             "clocks": clocks,

@@ -343,8 +343,11 @@ pycool_status pycool_linear_modes(int32_t n, int32_t stencil, double* values, in
  *     p_a of pycool_energies for the same fields).
  *   background (out, host, 2 + 2 N_f doubles): a, p_a, phi0[N_f], pi0[N_f] at
  *     the end.
- * The call allocates its device work space (spectra, tables, FFT plans),
- * works on `cuda_stream` and synchronises it before returning.
+ * The call allocates its device work space (spectra, tables), works on
+ * `cuda_stream` and synchronises it before returning.  The host tables of a
+ * lattice size and the FFT plans of a (size, N_f, device) are kept for the
+ * process's lifetime: the first call for a size pays for them, and calls that
+ * share a plan run one at a time.
  * Errors: E_INVALID (bad config, n outside 2..512, bad pointers), E_NOMEM,
  * E_CUDA.  The Q-ball's second derivatives need |Phi0| > 0 throughout. */
 pycool_status pycool_linear_evolve(const pycool_config* cfg, double a0, double pa0,

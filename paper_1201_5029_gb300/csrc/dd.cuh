@@ -102,7 +102,45 @@ __device__ __forceinline__ dd dd_sqr(dd x) {
   e = ffma(fadd(x.hi, x.hi), x.lo, e);
   return dd_norm(p, e);
 }
-__device__ __forceinline__ dd madd(dd a, dd b, dd c) { return a * b + c; }
+// a b + c in one pass: the product's pieces (TwoProduct and the cross terms)
+// go into the sum unnormalised, so only the result is renormalised.
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) {
+  float p, e, s, t;
+  two_prod(a.hi, b.hi, p, e);
+  e = ffma(a.hi, b.lo, e);
+  e = ffma(a.lo, b.hi, e);
+  two_sum(c.hi, p, s, t);
+  t = fadd(t, fadd(c.lo, e));
+  return dd_norm(s, t);
+}
+__device__ __forceinline__ dd dd_fma(float a, dd b, dd c) {
+  float p, e, s, t;
+  two_prod(a, b.hi, p, e);
+  e = ffma(a, b.lo, e);
+  two_sum(c.hi, p, s, t);
+  t = fadd(t, fadd(c.lo, e));
+  return dd_norm(s, t);
+}
+__device__ __forceinline__ dd madd(dd a, dd b, dd c) { return dd_fma(a, b, c); }
+
+// (a + b) + (c + e) + w x: the high parts added exactly in one chain of
+// TwoSums, the low parts and the rounding errors gathered in one float, a
+// single renormalisation (the in-plane part of the 7-point Laplacian).
+__device__ __forceinline__ dd dd_sum4_axpy(dd a, dd b, dd c, dd e, float w, dd x) {
+  float s0, s1, s2, s3, s4, r, t = a.lo, p, pe;
+  two_sum(a.hi, b.hi, s1, r);
+  t = fadd(t, fadd(r, b.lo));
+  two_sum(s1, c.hi, s2, r);
+  t = fadd(t, fadd(r, c.lo));
+  two_sum(s2, e.hi, s3, r);
+  t = fadd(t, fadd(r, e.lo));
+  two_prod(w, x.hi, p, pe);
+  pe = ffma(w, x.lo, pe);
+  two_sum(s3, p, s4, r);
+  t = fadd(t, fadd(r, pe));
+  s0 = s4;
+  return dd_norm(s0, t);
+}
 
 __device__ __forceinline__ dd dd_shfl_up(dd v, int d) {
   return dd(__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d));

@@ -19,6 +19,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
@@ -299,6 +303,61 @@ bool linear_modes_host(int n, int stencil, std::vector<double>& vals, std::vecto
   return true;
 }
 
+// Per-process caches of pycool_linear_evolve: the host tables of a lattice
+// (distinct k_eff^2 values, each half-spectrum mode's index) per (n, stencil),
+// and the forward/inverse FFT plans per (n, N_f, device).  A plan is used
+// under its own lock (its stream is set per call).
+struct LinTables {
+  std::vector<double> vals;
+  std::vector<int32_t> hidx;
+};
+struct LinPlans {
+  cufftHandle fwd = 0, inv = 0;
+  std::mutex mu;
+};
+std::mutex g_lin_mu;
+std::map<std::pair<int, int>, std::shared_ptr<const LinTables>> g_lin_tables;
+std::map<std::tuple<int, int, int>, std::shared_ptr<LinPlans>> g_lin_plans;
+
+std::shared_ptr<const LinTables> linear_tables(int n, int stencil) {
+  {
+    std::lock_guard<std::mutex> lk(g_lin_mu);
+    auto it = g_lin_tables.find({n, stencil});
+    if (it != g_lin_tables.end()) return it->second;
+  }
+  auto t = std::make_shared<LinTables>();
+  std::vector<int32_t> full;
+  linear_modes_host(n, stencil, t->vals, &full);
+  const int nh = n / 2 + 1;
+  t->hidx.resize((size_t)n * n * nh);
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < nh; ++x)
+        t->hidx[((size_t)z * n + y) * nh + x] = full[((size_t)z * n + y) * n + x];
+  std::lock_guard<std::mutex> lk(g_lin_mu);
+  return g_lin_tables.emplace(std::make_pair(n, stencil), t).first->second;
+}
+
+std::shared_ptr<LinPlans> linear_plans(int n, int nf, int device) {
+  std::lock_guard<std::mutex> lk(g_lin_mu);
+  auto key = std::make_tuple(n, nf, device);
+  auto it = g_lin_plans.find(key);
+  if (it != g_lin_plans.end()) return it->second;
+  auto p = std::make_shared<LinPlans>();
+  int dims[3] = {n, n, n};
+  const int S = n * n * n, half = n * n * (n / 2 + 1);
+  if (cufftPlanMany(&p->fwd, 3, dims, nullptr, 1, S, nullptr, 1, half, CUFFT_D2Z, nf) !=
+      CUFFT_SUCCESS)
+    return nullptr;
+  if (cufftPlanMany(&p->inv, 3, dims, nullptr, 1, half, nullptr, 1, S, CUFFT_Z2D, nf) !=
+      CUFFT_SUCCESS) {
+    cufftDestroy(p->fwd);
+    return nullptr;
+  }
+  g_lin_plans.emplace(key, p);
+  return p;
+}
+
 }  // namespace pycool
 
 using namespace pycool;
@@ -403,15 +462,14 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
   const int n = cfg->n;
   const long long S = (long long)n * n * n;
   const long long half = (long long)n * n * (n / 2 + 1);   // coefficients of a real transform
-  std::vector<double> vals;
-  std::vector<int32_t> full;
-  linear_modes_host(n, cfg->stencil, vals, &full);
-  std::vector<int32_t> hidx((size_t)half);
-  const int nh = n / 2 + 1;
-  for (int z = 0; z < n; ++z)
-    for (int y = 0; y < n; ++y)
-      for (int x = 0; x < nh; ++x)
-        hidx[((size_t)z * n + y) * nh + x] = full[((size_t)z * n + y) * n + x];
+  const std::shared_ptr<const LinTables> tab = linear_tables(n, cfg->stencil);
+  const std::vector<double>& vals = tab->vals;
+  const std::vector<int32_t>& hidx = tab->hidx;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return PYCOOL_E_CUDA;
+  const std::shared_ptr<LinPlans> plans = linear_plans(n, nf, device);
+  if (!plans) return PYCOOL_E_CUDA;
+  std::lock_guard<std::mutex> plan_lock(plans->mu);
   const long long nk = (long long)vals.size();
   const size_t N2 = (size_t)(2 * nf) * (2 * nf);
 
@@ -436,8 +494,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
   double *dk = nullptr, *dT = nullptr, *dbg = nullptr, *dpart = nullptr;
   double** dptrs = nullptr;             // [2][2 N_f]: source and destination arrays
   int32_t* didx = nullptr;
-  cufftHandle fwd = 0, inv = 0;
-  bool have_fwd = false, have_inv = false;
+  const cufftHandle fwd = plans->fwd, inv = plans->inv;
   pycool_status st = PYCOOL_OK;
   do {
     if (injected_alloc_failure() ||
@@ -453,13 +510,6 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
       st = PYCOOL_E_NOMEM;
       break;
     }
-    int dims[3] = {n, n, n};
-    if (cufftPlanMany(&fwd, 3, dims, nullptr, 1, (int)S, nullptr, 1, (int)half, CUFFT_D2Z, nf) !=
-        CUFFT_SUCCESS) { st = PYCOOL_E_CUDA; break; }
-    have_fwd = true;
-    if (cufftPlanMany(&inv, 3, dims, nullptr, 1, (int)half, nullptr, 1, (int)S, CUFFT_Z2D, nf) !=
-        CUFFT_SUCCESS) { st = PYCOOL_E_CUDA; break; }
-    have_inv = true;
     if (cufftSetStream(fwd, s) != CUFFT_SUCCESS || cufftSetStream(inv, s) != CUFFT_SUCCESS) {
       st = PYCOOL_E_CUDA;
       break;
@@ -517,8 +567,6 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
         cudaStreamSynchronize(s) != cudaSuccess)
       st = PYCOOL_E_CUDA;
   } while (0);
-  if (have_fwd) cufftDestroy(fwd);
-  if (have_inv) cufftDestroy(inv);
   cudaFree(spec);
   cudaFree(dk);
   cudaFree(dT);

@@ -32,7 +32,7 @@ template <> struct PotDD<M_FREE> {
   }
   __device__ static void diff(const SplitK& k, const dd* d, dd* dVd, dd& dVv) {
     dVd[0] = k.m2 * d[0];
-    dVv = k.hm2 * (d[0] * (k.two_p0 + d[0]));
+    dVv = k.hm2 * (d[0] * (k.two_p0 + d[0]));   // (free field: a few operations)
   }
 };
 
@@ -59,10 +59,10 @@ template <> struct PotDD<M_CHAOTIC2> {
     const dd dQ = dc * (k.two_c0 + dc);
     const dd Q = k.c0sq + dQ;
     const dd ch = k.c0 + dc;
-    const dd mix = dp * Q + k.p0 * dQ;
-    dVd[0] = k.m2 * dp + k.g2 * mix;
-    dVd[1] = k.g2 * (dP * ch + k.p0sq * dc);
-    dVv = k.hm2 * dP + k.hg2 * (dP * Q + k.p0sq * dQ);
+    const dd mix = dd_fma(dp, Q, k.p0 * dQ);
+    dVd[0] = dd_fma(k.m2, dp, k.g2 * mix);
+    dVd[1] = k.g2 * dd_fma(dP, ch, k.p0sq * dc);
+    dVv = dd_fma(k.hm2, dP, k.hg2 * dd_fma(dP, Q, k.p0sq * dQ));
   }
 };
 
@@ -93,16 +93,16 @@ template <> struct PotDD<M_OSCILLON> {
   }
   __device__ static void diff(const SplitK& k, const dd* dd_, dd* dVd, dd& dVv) {
     const dd d = dd_[0];
-    dd t = k.c[3] + d * k.c[4];
-    t = k.c[2] + d * t;
-    t = k.c[1] + d * t;
-    t = k.c[0] + d * t;
+    dd t = dd_fma(d, k.c[4], k.c[3]);
+    t = dd_fma(d, t, k.c[2]);
+    t = dd_fma(d, t, k.c[1]);
+    t = dd_fma(d, t, k.c[0]);
     dVd[0] = d * t;
-    dd u = k.e[4] + d * k.e[5];
-    u = k.e[3] + d * u;
-    u = k.e[2] + d * u;
-    u = k.e[1] + d * u;
-    u = k.e[0] + d * u;
+    dd u = dd_fma(d, k.e[5], k.e[4]);
+    u = dd_fma(d, u, k.e[3]);
+    u = dd_fma(d, u, k.e[2]);
+    u = dd_fma(d, u, k.e[1]);
+    u = dd_fma(d, u, k.e[0]);
     dVv = d * u;
   }
 };
@@ -171,13 +171,13 @@ template <> struct PotDD<M_QBALL> {
       }
       return;
     }
-    const dd du = d[0] * (k.p1 + 0.5f * d[0]) + d[1] * (k.p2 + 0.5f * d[1]);
+    const dd du = dd_fma(d[0], dd_fma(0.5f, d[0], k.p1), d[1] * dd_fma(0.5f, d[1], k.p2));
     const dd u = k.u0 + du;
     if (u.hi > 0.f) {
       const dd Kl = k.K * dd_log1p(du * k.inv_u0);
-      dVd[0] = k.m2 * (k.A * d[0] + Kl * (k.p1 + d[0]));
-      dVd[1] = k.m2 * (k.A * d[1] + Kl * (k.p2 + d[1]));
-      dVv = k.m2 * (k.B * du + Kl * u);
+      dVd[0] = k.m2 * dd_fma(k.A, d[0], Kl * (k.p1 + d[0]));
+      dVd[1] = k.m2 * dd_fma(k.A, d[1], Kl * (k.p2 + d[1]));
+      dVv = k.m2 * dd_fma(k.B, du, Kl * u);
     } else {   // |Phi| = 0 here: V = V' = 0
       dVd[0] = -(k.m2 * (k.A * k.p1));
       dVd[1] = -(k.m2 * (k.A * k.p2));

@@ -265,7 +265,10 @@ __device__ __forceinline__ void plane_parts(const T (&ctr)[VX], const T (&dn)[VX
       if constexpr (MID) {
         const T L = j > 0 ? ctr[j - 1] : left;
         const T R = j < VX - 1 ? ctr[j + 1] : right;
-        smid[j] = madd(c0, ctr[j], (dn[j] + up[j]) + (L + R));
+        if constexpr (std::is_same<T, dd>::value)
+          smid[j] = dd_sum4_axpy(dn[j], up[j], L, R, -6.0f, ctr[j]);
+        else
+          smid[j] = madd(c0, ctr[j], (dn[j] + up[j]) + (L + R));
       }
     } else {
       const T L = j > 0 ? ctr[j - 1] : left;
@@ -474,12 +477,14 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
 // of the split-FP32 form (stencil on phi + c pi, re-centred output, difference
 // forms of V') in double-float on the FP32 pipe.
 // ---------------------------------------------------------------------------
-// One stage over this block's units.  tot: this thread's stage sums (NQ
-// double-floats, the running accumulators folded in every KGROUP planes).
+// One stage over this block's units.  This thread's stage sums (NQ
+// double-floats, the running accumulators folded in every KGROUP planes) live
+// in its own slots of the block-reduction scratch, sm.red[q * threads + tid]
+// (free during the sweep), to keep registers for the sweep.
 // Returns false (in every thread) if a wait gave up.
 template <int MODEL, int STENCIL, int VX, int MODE>
 __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC_DD>& cx,
-                                         const PShared& sm, uint32_t gq, int ib, dd* tot) {
+                                         const PShared& sm, uint32_t gq, int ib) {
   using C = Ctx<MODEL, PREC_DD>;
   using T = dd;
   using SL = typename C::SL;
@@ -503,13 +508,17 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
   // phi + c pi (D of a constant is zero)
   T Mf[NF];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) Mf[f] = cx.mu_phi[f] + cd * cx.mu_pi[f];
+  for (int f = 0; f < NF; ++f) Mf[f] = dd_fma(cd, cx.mu_pi[f], cx.mu_phi[f]);
   const int side = lane == 31 ? 1 : 0;
   const bool edge = lane == 0 || lane == 31;          // lanes that read a halo column
   const int own = (ly + 1) * TX + lane * VX;          // this lane's sites in a slot row
   DDAcc acc[NQ];
+  dd* tot = reinterpret_cast<dd*>(sm.red) + tid;        // tot[q * kPThreads]
 #pragma unroll
-  for (int i = 0; i < NQ; ++i) acc[i].zero();
+  for (int i = 0; i < NQ; ++i) {
+    acc[i].zero();
+    tot[i * kPThreads] = dd(0.f, 0.f);
+  }
   int kg = 0;
 
   int pui = 0, puq = 0;                                 // producer position, LEAD ahead
@@ -545,7 +554,7 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
 #pragma unroll
         for (int jj = 0; jj < VX; ++jj) {
           cur_pi[f][jj] = b[jj] - cx.mu_pi[f];
-          cur_ph[f][jj] = a[jj] + cd * b[jj];
+          cur_ph[f][jj] = dd_fma(cd, b[jj], a[jj]);
         }
         vstore<T, VX>(&dph[own], cur_ph[f]);
         if (ly < 2) {
@@ -553,7 +562,7 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
           vload<T, VX>(&mph[r], a);
           vload<T, VX>(&mpi[r], b);
 #pragma unroll
-          for (int jj = 0; jj < VX; ++jj) a[jj] = a[jj] + cd * b[jj];
+          for (int jj = 0; jj < VX; ++jj) a[jj] = dd_fma(cd, b[jj], a[jj]);
           vstore<T, VX>(&dph[r], a);
         }
 #pragma unroll
@@ -565,7 +574,7 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
           for (int rr = 0; rr < CR; ++rr) {
             const int r = ly + 1 + rr - (CR - 1) / 2;
             const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
-            el[f][rr] = cph[row] + cd * cpi[row];
+            el[f][rr] = dd_fma(cd, cpi[row], cph[row]);
           }
         }
       }
@@ -622,7 +631,11 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
         if (++kg == KGROUP) {
           kg = 0;
 #pragma unroll
-          for (int i2 = 0; i2 < NQ; ++i2) acc[i2].fold(tot[i2]);
+          for (int i2 = 0; i2 < NQ; ++i2) {
+            dd t = tot[i2 * kPThreads];
+            acc[i2].fold(t);
+            tot[i2 * kPThreads] = t;
+          }
         }
       }
       if (mid) {
@@ -643,7 +656,11 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
     }
   }
 #pragma unroll
-  for (int i2 = 0; i2 < NQ; ++i2) acc[i2].fold(tot[i2]);
+  for (int i2 = 0; i2 < NQ; ++i2) {
+    dd t = tot[i2 * kPThreads];
+    acc[i2].fold(t);
+    tot[i2 * kPThreads] = t;
+  }
   return true;
 }
 
@@ -1024,14 +1041,12 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
                ? stage_fp64<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib, accd)
                : stage_fp64<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib, accd);
     } else if constexpr (PREC == PREC_DD) {
-      dd tot[NQ];
+      ok = (mode == MODE_SWEEP) ? stage_dd<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib)
+                                : stage_dd<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib);
+      // this thread's stage sums, from its own scratch slots (overwritten below)
+      const dd* tot = reinterpret_cast<const dd*>(sm.red) + tid;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) tot[q] = dd(0.f, 0.f);
-      ok = (mode == MODE_SWEEP)
-               ? stage_dd<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib, tot)
-               : stage_dd<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib, tot);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) accd[q] = (double)tot[q];
+      for (int q = 0; q < NQ; ++q) accd[q] = (double)tot[q * kPThreads];
     } else {
       // the Q-ball's difference forms have a branch for a background at the
       // origin; a stage whose background is away from it runs without the test

@@ -450,7 +450,7 @@ __device__ __forceinline__ void site_dd(const Ctx<MODEL, PREC_DD>& cx, int mode,
   PotDD<MODEL>::diff(cx.sk, phj, dVd, dVv);
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    pin[f] = (mode == MODE_SWEEP) ? pim[f] + cx.kD * D[f] - cx.kV * dVd[f] : pim[f];
+    pin[f] = (mode == MODE_SWEEP) ? dd_fma(cx.kD, D[f], dd_fma(-cx.kV, dVd[f], pim[f])) : pim[f];
     acc[SL::DPI + f].add(pin[f]);
     acc[SL::DPI2 + f].add_sqr(pin[f]);
     acc[SL::PHID + f].add_prod(phj[f], D[f]);
