@@ -45,7 +45,9 @@ def _run(requests, budget=8 * GB, slots=32):
 
 
 @pytest.mark.parametrize("name,n,order", [("preheat32", 32, 2), ("oscillon256", 24, 6),
-                                          ("qball256", 32, 4)])
+                                          ("qball256", 32, 4),
+                                          ("preheat128", 128, 4),    # TMA-staged member
+                                          ("oscillon256", 128, 2)])
 def test_served_request_matches_oracle(name, n, order):
     w, cfg, ic = _req(name, n, order)
     seed, steps = 77 + n, 6
