@@ -169,6 +169,50 @@ template <> struct Pot<M_QBALL> {
       dV[0] = 0.0; dV[1] = 0.0; V = 0.0;
     }
   }
+  // eval with the logarithm taken near a reference u_ref (the FP64 sweep's
+  // per-stage value at one site, the same in every block): ln(u) =
+  // ln(u_ref) + log1p(x), x = u / u_ref - 1, log1p(x) by its Taylor series
+  // sum_k (-1)^(k+1) x^k / k -- 5 terms for |x| < 2^-12 (the first omitted
+  // term is below 2^-60 |x|), 11 terms for |x| < 2^-5 (below 2^-60 |x|) --
+  // and the full logarithm farther away.  lref = ln(u_ref) - ln(M^2).
+  __device__ static void eval_near(const K& k, const double* f, double* dV, double& V,
+                                   double inv_uref, double lref) {
+    const double u = 0.5 * fma(f[0], f[0], f[1] * f[1]);
+    if (u > 0.0) {
+      const double x = fma(u, inv_uref, -1.0);
+      const double ax = fabs(x);
+      double l;
+      if (ax < 0.000244140625) {          // 2^-12
+        double q = fma(x, 0.2, -0.25);
+        q = fma(q, x, 1.0 / 3.0);
+        q = fma(q, x, -0.5);
+        q = fma(q, x, 1.0);
+        l = fma(q, x, lref);
+      } else if (ax < 0.03125) {          // 2^-5
+        double q = fma(x, -1.0 / 12.0, 1.0 / 11.0);
+        q = fma(q, x, -0.1);
+        q = fma(q, x, 1.0 / 9.0);
+        q = fma(q, x, -0.125);
+        q = fma(q, x, 1.0 / 7.0);
+        q = fma(q, x, -1.0 / 6.0);
+        q = fma(q, x, 0.2);
+        q = fma(q, x, -0.25);
+        q = fma(q, x, 1.0 / 3.0);
+        q = fma(q, x, -0.5);
+        q = fma(q, x, 1.0);
+        l = fma(q, x, lref);
+      } else {
+        l = log(u) - k.lnM2;
+      }
+      const double kl = k.mK * l;
+      const double fac = fma(k.m2, k.K1, kl);
+      dV[0] = fac * f[0];
+      dV[1] = fac * f[1];
+      V = u * (k.m2 + kl);
+    } else {
+      dV[0] = 0.0; dV[1] = 0.0; V = 0.0;
+    }
+  }
   // du = d1 (p1 + d1/2) + d2 (p2 + d2/2),  l = log1p(du/u0)
   //   dV'_i = m2 [ A d_i + K l (p_i + d_i) ],  A = 1 + K + K L0
   //   dV    = m2 [ B du + K l (u0 + du) ],      B = 1 + K L0,  L0 = ln(u0/M^2)

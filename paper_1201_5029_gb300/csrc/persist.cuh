@@ -1219,6 +1219,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
 #pragma unroll
             for (int f = 0; f < NF; ++f)
               nx.shiftK[f] = (mn == MODE_FLUSH) ? flush_shift(d, ib_next, f, nx.k.c) : 0.0;
+            nx.set_qref(d, ib_next);
           }
         }
         if constexpr (PREC != PREC_FP64) {

@@ -313,6 +313,7 @@ struct Ctx {
   T shiftK[NF];
   double phi0s[NF], pi0s[NF], V0;  // split forms: background after drift / kick
   typename SplitKOf<MODEL, PREC>::type sk;
+  double q_inv, q_lref;            // FP64 Q-ball: 1/u_ref, ln(u_ref/M^2) (0, 0: no reference)
 
   __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode,
                                        double ia_a = -1.0) {
@@ -325,6 +326,19 @@ struct Ctx {
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         shiftK[f] = (mode == MODE_FLUSH) ? (T)flush_shift(d, bg.cur, f, k.c) : (T)0;
+      set_qref(d, bg.cur);
+    }
+  }
+
+  //   set_qref (FP64 Q-ball): the reference of the logarithm, |Phi|^2/2 of the
+  //   drifted field at site 0 of the stage's input buffers (every block reads
+  //   the same two values, so every block uses the same reference)
+  __device__ __forceinline__ void set_qref(const SimDesc& d, int cur) {
+    if constexpr (PREC == PREC_FP64 && MODEL == M_QBALL) {
+      const double f0 = flush_shift(d, cur, 0, k.c), f1 = flush_shift(d, cur, 1, k.c);
+      const double u = 0.5 * fma(f0, f0, f1 * f1);
+      q_inv = u > 0.0 ? 1.0 / u : 0.0;
+      q_lref = u > 0.0 ? log(u) - pk.lnM2 : 0.0;
     }
   }
 
@@ -401,7 +415,12 @@ struct Ctx {
       ps[SL::V] = madd(ph2, t, ps[SL::V]);
     } else if constexpr (PREC == PREC_FP64) {
       double dV[NF], V;
-      P::eval(pk, phj, dV, V);
+      if constexpr (MODEL == M_QBALL) {
+        if (q_inv > 0.0) P::eval_near(pk, phj, dV, V, q_inv, q_lref);
+        else P::eval(pk, phj, dV, V);
+      } else {
+        P::eval(pk, phj, dV, V);
+      }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         if (mode == MODE_SWEEP) {

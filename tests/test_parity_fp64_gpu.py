@@ -216,3 +216,19 @@ def test_tma_kernel_sizes(name, n, order, steps, stencil):
     gphi, gpi, ge = G.run_gpu(P, G.gpu_cfg(P, w, n=n, order=order, stencil=stencil), phi, pi, steps)
     st, oe = G.run_oracle(G.oracle_cfg(w, n=n, order=order, stencil=stencil), phi, pi, steps)
     _check(gphi, gpi, ge, st, oe)
+
+
+@pytest.mark.parametrize("amp", [1e-6, 1e-3, 0.2])
+def test_qball_logarithm_near_reference_all_branches(amp):
+    """The FP64 Q-ball takes ln|Phi|^2 as ln(u_ref) + a log1p series when the
+    site is close to the stage's reference value (5 terms within 2^-12, 11
+    terms within 2^-5) and the full logarithm farther away: fluctuations of
+    1e-6, 1e-3 and 0.2 exercise each branch (the TMA kernel at n = 64, the
+    persistent kernel, and the plain-load kernel at n = 20)."""
+    w = I.workload("qball256")
+    for n in (64, 20):
+        phi, pi = I.initial_fields(w, n=n)
+        phi = phi + amp * np.random.default_rng(11).standard_normal(phi.shape)
+        gphi, gpi, ge = G.run_gpu(P, G.gpu_cfg(P, w, n=n, order=4), phi, pi, 3)
+        st, oe = G.run_oracle(G.oracle_cfg(w, n=n, order=4), phi, pi, 3)
+        _check(gphi, gpi, ge, st, oe)
