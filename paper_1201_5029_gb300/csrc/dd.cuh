@@ -163,6 +163,8 @@ struct DDAcc {
     c = fadd(c, fadd(e, x.lo));
     s = t;
   }
+  // a plain float sum of high parts (for sums whose precision does not matter)
+  __device__ __forceinline__ void add_fast(float x) { s = fadd(s, x); }
   // add the product a b (TwoProduct and cross terms, unnormalised)
   __device__ __forceinline__ void add_prod(dd a, dd b) {
     float p, e;

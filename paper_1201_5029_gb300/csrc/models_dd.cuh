@@ -108,11 +108,21 @@ template <> struct PotDD<M_OSCILLON> {
 };
 
 // ---------------------------------------------------------------- QBALL
-// log(1 + x) for a double-float x: for |x| < 2^-5 the series of
-// 2 atanh(s), s = x / (2 + x):  2 s (1 + s^2/3 + s^4/5 + s^6/7 + ...), the
-// first two terms in double-float and the rest in float (|s| < 2^-6, so s^4/5
-// is 2^-26 of the sum and s^8/9 under 2^-51); otherwise the float64 log1p.
+// log(1 + x) for a double-float x: for |x| < 2^-12 its Taylor series
+// x - x^2/2 + x^3/3 - x^4/4 + x^5/5 with the first two terms in double-float
+// and the rest in float (x^3/3 is below 2^-24 of the sum, so float leaves
+// 2^-48; the first omitted term is below 2^-60 of it); for |x| < 2^-5 the
+// series of 2 atanh(s), s = x / (2 + x):  2 s (1 + s^2/3 + s^4/5 + s^6/7 + ...),
+// the first two terms in double-float and the rest in float (|s| < 2^-6, so
+// s^4/5 is 2^-26 of the sum and s^8/9 under 2^-51); otherwise the float64 log1p.
 __device__ __forceinline__ dd dd_log1p(dd x) {
+  if (fabsf(x.hi) < 0.000244140625f) {
+    const dd h = dd_sqr(x);
+    const float xh = x.hi;
+    const float tail = fmul(xh, fmul(xh, fmul(xh, ffma(xh, ffma(xh, 0.2f, -0.25f),
+                                                      0.333333333f))));
+    return (x - dd(fmul(0.5f, h.hi), fmul(0.5f, h.lo))) + tail;
+  }
   if (fabsf(x.hi) < 0.03125f) {
     const dd s = dd_div(x, x + 2.0f);
     const dd s2 = dd_sqr(s);

@@ -473,8 +473,15 @@ __device__ __forceinline__ void site_dd(const Ctx<MODEL, PREC_DD>& cx, int mode,
     acc[SL::DPI + f].add(pin[f]);
     acc[SL::DPI2 + f].add_sqr(pin[f]);
     acc[SL::PHID + f].add_prod(phj[f], D[f]);
-    acc[SL::DPHI + f].add(phj[f]);
-    if (mode != MODE_SWEEP) acc[SL::DPHI2 + f].add_sqr(phj[f]);
+    if (mode == MODE_SWEEP) {
+      // a sweep's sum of the fluctuations only sets the re-centring shift,
+      // which moves into the background exactly as it leaves the
+      // fluctuations: any value of it is exact bookkeeping
+      acc[SL::DPHI + f].add_fast(phj[f].hi);
+    } else {  // a flush's sums give the field's mean and variance: double-float
+      acc[SL::DPHI + f].add(phj[f]);
+      acc[SL::DPHI2 + f].add_sqr(phj[f]);
+    }
   }
   acc[SL::V].add(dVv);
 }

@@ -107,3 +107,16 @@ def test_rejected_where_it_has_no_kernel():
     with pytest.raises(P.PycoolError) as ei:
         P.Simulation(G.gpu_cfg(P, w, n=40, precision="split_dd"))   # not a multiple of 32
     assert ei.value.status == P.E_INVALID
+
+
+@pytest.mark.parametrize("amp", [1e-6, 1e-3, 0.2])
+def test_qball_log1p_tiers(amp):
+    """The split-DD Q-ball takes log1p of a double-float by its Taylor series
+    within 2^-12, by the atanh series within 2^-5 and in float64 beyond:
+    fluctuations of 1e-6, 1e-3 and 0.2 exercise each tier."""
+    w = I.workload("qball256")
+    phi, pi = I.initial_fields(w, n=64)
+    phi = phi + amp * np.random.default_rng(11).standard_normal(phi.shape)
+    gphi, gpi, ge = G.run_gpu(P, G.gpu_cfg(P, w, n=64, order=4, precision="split_dd"), phi, pi, 3)
+    st, oe = G.run_oracle(G.oracle_cfg(w, n=64, order=4), phi, pi, 3)
+    check(gphi, gpi, ge, st, oe, label=f"qball amp={amp}")
