@@ -174,8 +174,12 @@ pycool_status pycool_create(const pycool_config* cfg, void* dev_state, void* dev
  * on_device == 0: host pointers, copied before the call returns.
  * a0 > 0 is the initial scale factor.  pa0 = NaN: p_a is the negative root of
  * the Hamiltonian constraint H = 0 (Eq. H2; expanding branch, p_a < 0, Eq. p-a);
- * for mpl = +INF, p_a = 0.  For SPLIT_FP32 the lattice mean of each field is
- * taken as the float64 background and the rest rounded to float32. */
+ * for mpl = +INF, p_a = 0.  For the split forms the lattice mean of each field
+ * and momentum (a compensated sum in a fixed order on the device) is taken as
+ * the float64 background and the rest, x - mean, is rounded to float32
+ * (SPLIT_FP32) or split into a double-float pair hi + lo (SPLIT_DD), all in
+ * kernels; host inputs are staged in the simulation's own field buffers, so
+ * the call allocates nothing. */
 pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, const double* pi,
                                  int on_device, double a0, double pa0);
 
@@ -196,8 +200,9 @@ pycool_status pycool_field_stats(pycool_sim* sim, int32_t field, double* mean,
                                  double* variance);
 
 /* Copy the current fields and momenta out, float64 [field][z][y][x]
- * (SPLIT_FP32: phi0 + dphi evaluated in float64).  on_device as for
- * set_initial; host copies synchronise first.  Either pointer may be NULL. */
+ * (split forms: phi0 + dphi evaluated in float64 by a kernel; host outputs go
+ * through the field buffer the current state does not use).  on_device as for
+ * set_initial; the call synchronises.  Either pointer may be NULL. */
 pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double* pi, int on_device);
 
 /* ---- potentials given at run time --------------------------------------------

@@ -76,6 +76,10 @@ int model_nfields(int model) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Blocks of the split forms' initial-mean reduction (a fixed grid, so the
+// summation order and the result depend on the lattice alone).
+constexpr int kMeanBlocks = 304;
+
 Layout layout_for(const pycool_config& c) {
   Layout L;
   const int nf = model_nfields(c.model);
@@ -92,6 +96,7 @@ Layout layout_for(const pycool_config& c) {
   L.off_prows = 0;
   L.off_punits = 0;
   L.off_rt = 0;
+  L.off_mean = 0;
   if (runtime) {   // drifted fields, V' (N_f n^3 each) and V (n^3)
     L.off_rt = align256(L.ws_bytes);
     L.ws_bytes = L.off_rt + 2 * align256((size_t)nf * S * 8) + align256(S * 8);
@@ -101,6 +106,8 @@ Layout layout_for(const pycool_config& c) {
 
 Layout sim_layout(const pycool_config& c) {
   Layout L = layout_for(c);
+  L.off_mean = align256(L.ws_bytes);
+  L.ws_bytes = L.off_mean + align256((size_t)2 * kMeanBlocks * sizeof(double));
   if (L.geo.tma) {
     L.off_prows = align256(L.ws_bytes);
     L.off_punits = L.off_prows + align256((size_t)2 * kMaxPBlocks * kNQ * sizeof(double));
@@ -523,25 +530,103 @@ __global__ void arm_kernel(Background* bg, long long nsweeps) {
   bg->mode = MODE_SWEEP;
 }
 
-__global__ void split_combine_kernel(const float* __restrict__ d, double base0, double base1,
-                                     double* __restrict__ out, long long S, int nf) {
-  const long long total = S * nf;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    out[i] = (i < S ? base0 : base1) + (double)d[i];
+
+// ---------------------------------------------------------------------------
+// Split forms' initial state on the device: the lattice mean of one field is
+// the float64 background phi0, and the rest, x - phi0, is stored as float32
+// (SPLIT_FP32) or as a double-float pair hi + lo (SPLIT_DD).
+// The mean is a compensated sum (Knuth's TwoSum on a running float64 sum, the
+// rounding errors gathered separately) over a fixed grid-stride order, a fixed
+// tree in each block, and one block that folds the block sums in block order:
+// reproducible bit for bit for a given lattice.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mean_two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void mean_block_tree(double s, double c, double* ss, double* cc) {
+  const int t = threadIdx.x;
+  ss[t] = s;
+  cc[t] = c;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (t < h) {
+      double u, e;
+      mean_two_sum(ss[t], ss[t + h], u, e);
+      ss[t] = u;
+      cc[t] += cc[t + h] + e;
+    }
+    __syncthreads();
   }
 }
 
-// split-DD: background + (hi + lo), evaluated in float64
-__global__ void dd_combine_kernel(const float2* __restrict__ d, double base0, double base1,
-                                  double* __restrict__ out, long long S, int nf) {
-  const long long total = S * nf;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float2 v = d[i];
-    out[i] = (i < S ? base0 : base1) + ((double)v.x + (double)v.y);
+__global__ void __launch_bounds__(256) mean_partial_kernel(const double* __restrict__ x,
+                                                           long long S, double* part) {
+  __shared__ double ss[256], cc[256];
+  double s = 0.0, c = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < S; i += (long long)gridDim.x * 256) {
+    double u, e;
+    mean_two_sum(s, x[i], u, e);
+    s = u;
+    c += e;
+  }
+  mean_block_tree(s, c, ss, cc);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ss[0];
+    part[2 * blockIdx.x + 1] = cc[0];
   }
 }
+
+__global__ void __launch_bounds__(256) mean_fold_kernel(const double* __restrict__ part, int nb,
+                                                        long long S, double* mean) {
+  __shared__ double ss[256], cc[256];
+  double s = 0.0, c = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) {
+    double u, e;
+    mean_two_sum(s, part[2 * b], u, e);
+    s = u;
+    c += part[2 * b + 1] + e;
+  }
+  mean_block_tree(s, c, ss, cc);
+  if (threadIdx.x == 0) *mean = (ss[0] + cc[0]) / (double)S;
+}
+
+// out[i] = x[i] - mean as float32, or as the pair (hi, lo) with
+// hi = fl32(x - mean), lo = fl32((x - mean) - hi).
+__global__ void split_store_kernel(const double* __restrict__ x, const double* mean, void* out,
+                                   long long S, int pair) {
+  const double m = *mean;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i] - m;
+    const float hi = __double2float_rn(v);
+    if (pair)
+      static_cast<float2*>(out)[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    else
+      static_cast<float*>(out)[i] = hi;
+  }
+}
+
+// The inverse for a read-out: out[i] = base + fluctuation, in float64, for
+// elements [i0, i0 + count) of one field.
+__global__ void split_load_kernel(const void* __restrict__ d, const double* base, double* out,
+                                  long long i0, long long count, int pair) {
+  const double b = *base;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v;
+    if (pair) {
+      const float2 p = static_cast<const float2*>(d)[i0 + i];
+      v = (double)p.x + (double)p.y;
+    } else {
+      v = (double)static_cast<const float*>(d)[i0 + i];
+    }
+    out[i] = b + v;
+  }
+}
+
 
 cudaError_t launch_arm(Background* bg, long long nsweeps, cudaStream_t s) {
   arm_kernel<<<1, 1, 0, s>>>(bg, nsweeps);
@@ -877,6 +962,48 @@ static pycool_status launch_one(pycool_sim* sim) {
   return PYCOOL_OK;
 }
 
+// The split forms' initial state (Background already on the device, phi0 and
+// pi0 still 0): per field, the device mean goes into Background.phi0[f] /
+// pi0[f], then the fluctuation into buffer 0.  Host inputs are staged, one
+// field at a time, in the simulation's own buffers that the initial state does
+// not use yet: phi buffer 1 (and, for SPLIT_FP32 with its 4-byte words, pi
+// buffer 0 after it) for phi; pi buffer 0 and 1 for pi, whose fluctuation is
+// then written to phi buffer 1 and moved to pi buffer 0.  Nothing is allocated.
+static pycool_status split_initial(pycool_sim* sim, const double* phi, const double* pi,
+                                   bool on_device) {
+  const size_t S = (size_t)sim->hdesc.S;
+  const int pair = sim->hdesc.prec == PREC_DD ? 1 : 0;
+  const size_t word = pair ? 8 : 4;
+  char* f0 = (char*)sim->hdesc.phi[0];
+  char* f1 = (char*)sim->hdesc.phi[1];
+  char* p0 = (char*)sim->hdesc.pi[0];
+  double* part = (double*)(sim->ws + sim->L.off_mean);
+  const int nb = (int)std::min<size_t>(kMeanBlocks, (S + 4095) / 4096);
+  const unsigned sg = (unsigned)std::min<size_t>(152 * 8, (S + 255) / 256);
+  for (int which = 0; which < 2; ++which) {
+    const double* src_all = which == 0 ? phi : pi;
+    for (int f = 0; f < sim->nf; ++f) {
+      const double* x = src_all + (size_t)f * S;
+      // float64 staging of one field (8 S bytes), disjoint from the output
+      double* stage = (double*)(which == 0 ? f1 : p0);
+      char* out = which == 0 ? f0 + (size_t)f * S * word : f1 + (size_t)f * S * word;
+      if (!on_device) {
+        CK(cudaMemcpyAsync(stage, x, S * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+        x = stage;
+      }
+      double* mean = which == 0 ? &sim->d_bg->phi0[f] : &sim->d_bg->pi0[f];
+      mean_partial_kernel<<<nb, 256, 0, sim->stream>>>(x, (long long)S, part);
+      mean_fold_kernel<<<1, 256, 0, sim->stream>>>(part, nb, (long long)S, mean);
+      split_store_kernel<<<sg, 256, 0, sim->stream>>>(x, mean, out, (long long)S, pair);
+      CK(cudaGetLastError());
+      sim->launches += 3;
+    }
+  }
+  // the momenta's fluctuations, written to phi buffer 1, into pi buffer 0
+  CK(cudaMemcpyAsync(p0, f1, (size_t)sim->nf * S * word, cudaMemcpyDeviceToDevice, sim->stream));
+  return PYCOOL_OK;
+}
+
 PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, const double* pi,
                                             int on_device, double a0, double pa0) {
   if (!sim || !phi || !pi) return PYCOOL_E_INVALID;
@@ -897,53 +1024,14 @@ PYCOOL_API pycool_status pycool_set_initial(pycool_sim* sim, const double* phi, 
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(sim->hdesc.phi[0], phi, count * sizeof(double), kind, sim->stream));
     CK(cudaMemcpyAsync(sim->hdesc.pi[0], pi, count * sizeof(double), kind, sim->stream));
+    CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
   } else {
-    // split form: phi0 = lattice mean (float64), dphi = phi - phi0 in float32
-    std::vector<double> hphi, hpi;
-    const double* sp = phi;
-    const double* sq = pi;
-    if (on_device) {
-      hphi.resize(count);
-      hpi.resize(count);
-      CK(cudaMemcpy(hphi.data(), phi, count * sizeof(double), cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(hpi.data(), pi, count * sizeof(double), cudaMemcpyDeviceToHost));
-      sp = hphi.data();
-      sq = hpi.data();
-    }
-    // (split-DD: the fluctuation as a double-float pair hi + lo, 8 bytes)
-    const bool pair = sim->hdesc.prec == PREC_DD;
-    const size_t per = pair ? 2 : 1;
-    std::vector<float> dphi(count * per), dpi(count * per);
-    for (int f = 0; f < nf; ++f) {
-      for (int which = 0; which < 2; ++which) {
-        const double* src = (which == 0 ? sp : sq) + (size_t)f * S;
-        double s = 0.0, comp = 0.0;
-        for (size_t i = 0; i < S; ++i) {
-          const double x = src[i], t = s + x;
-          comp += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
-          s = t;
-        }
-        const double mean = (s + comp) / (double)S;
-        float* dst = (which == 0 ? dphi.data() : dpi.data()) + (size_t)f * S * per;
-        for (size_t i = 0; i < S; ++i) {
-          const double x = src[i] - mean;
-          if (pair) {
-            const float hi = (float)x;
-            dst[2 * i] = hi;
-            dst[2 * i + 1] = (float)(x - (double)hi);
-          } else {
-            dst[i] = (float)x;
-          }
-        }
-        if (which == 0) b.phi0[f] = mean; else b.pi0[f] = mean;
-      }
-    }
-    CK(cudaMemcpy(sim->hdesc.phi[0], dphi.data(), dphi.size() * sizeof(float),
-                  cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(sim->hdesc.pi[0], dpi.data(), dpi.size() * sizeof(float),
-                  cudaMemcpyHostToDevice));
+    // split forms: phi0 = the lattice mean (float64), the rest as float32 or
+    // as a double-float pair, all on the device (split_initial)
+    CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
+    pycool_status st = split_initial(sim, phi, pi, on_device != 0);
+    if (st != PYCOOL_OK) return st;
   }
-  CK(cudaMemcpyAsync(sim->d_bg, &b, sizeof(b), cudaMemcpyHostToDevice, sim->stream));
   CK(cudaMemsetAsync(sim->ws, 0, sim->L.off_partials, sim->stream));
   sim->pp.bar_base = 0;
   // the reducing flush: sums of the initial state (and p_a from H = 0)
@@ -1054,36 +1142,33 @@ PYCOOL_API pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double*
     CK(cudaStreamSynchronize(sim->stream));
     return b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK;
   }
-  // split forms: phi0 + dphi evaluated in float64 (split-DD: dphi = hi + lo)
-  const bool pair = sim->hdesc.prec == PREC_DD;
+  // split forms: phi0 + dphi evaluated in float64 (split-DD: dphi = hi + lo) on
+  // the device; for host outputs through the phi buffer the current state does
+  // not use, in chunks of its size
+  const int pair = sim->hdesc.prec == PREC_DD ? 1 : 0;
+  double* stage = (double*)sim->hdesc.phi[(b.cur & 1) ^ 1];
+  const size_t chunk = sim->L.field_bytes / sizeof(double);
   for (int which = 0; which < 2; ++which) {
     double* dst = which == 0 ? phi : pi;
     if (!dst) continue;
-    const float* src = (const float*)(which == 0 ? src_phi : src_pi);
-    const double* base = which == 0 ? b.phi0 : b.pi0;
-    if (on_device) {
-      if (pair)
-        dd_combine_kernel<<<1024, 256, 0, sim->stream>>>((const float2*)src, base[0], base[1],
-                                                         dst, (long long)S, sim->nf);
-      else
-        split_combine_kernel<<<1024, 256, 0, sim->stream>>>(src, base[0], base[1], dst,
-                                                            (long long)S, sim->nf);
-      CK(cudaGetLastError());
-      sim->launches += 1;
-      CK(cudaStreamSynchronize(sim->stream));
-    } else {
-      std::vector<float> tmp(count * (pair ? 2 : 1));
-      CK(cudaMemcpyAsync(tmp.data(), src, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost,
-                         sim->stream));
-      CK(cudaStreamSynchronize(sim->stream));
-      for (int f = 0; f < sim->nf; ++f)
-        for (size_t i = 0; i < S; ++i) {
-          const size_t e = (size_t)f * S + i;
-          const double v = pair ? (double)tmp[2 * e] + (double)tmp[2 * e + 1] : (double)tmp[e];
-          dst[e] = base[f] + v;
-        }
+    const void* src = which == 0 ? src_phi : src_pi;
+    for (int f = 0; f < sim->nf; ++f) {
+      const double* base = which == 0 ? &sim->d_bg->phi0[f] : &sim->d_bg->pi0[f];
+      for (size_t i0 = 0; i0 < S; i0 += chunk) {
+        const size_t m = std::min(chunk, S - i0);
+        double* out = on_device ? dst + (size_t)f * S + i0 : stage;
+        const unsigned g = (unsigned)std::min<size_t>(152 * 8, (m + 255) / 256);
+        split_load_kernel<<<g, 256, 0, sim->stream>>>(src, base, out, (long long)((size_t)f * S + i0),
+                                                     (long long)m, pair);
+        CK(cudaGetLastError());
+        sim->launches += 1;
+        if (!on_device)
+          CK(cudaMemcpyAsync(dst + (size_t)f * S + i0, stage, m * sizeof(double),
+                             cudaMemcpyDeviceToHost, sim->stream));
+      }
     }
   }
+  CK(cudaStreamSynchronize(sim->stream));
   return b.error ? PYCOOL_E_NONFINITE : PYCOOL_OK;
 }
 

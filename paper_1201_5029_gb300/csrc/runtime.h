@@ -26,6 +26,7 @@ struct Layout {
   size_t off_prows;   // single-simulation API: rows of the persistent kernel (0 = none)
   size_t off_punits;  // single-simulation API: the persistent kernel's unit table
   size_t off_rt;      // runtime potentials: drifted fields, V', V (0 = none)
+  size_t off_mean;    // single-simulation API: partial sums of the split forms' initial means
 };
 
 // Workspace layout of a launch of `ncta` blocks (fills the off_* / ws_bytes fields).
