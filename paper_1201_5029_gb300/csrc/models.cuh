@@ -262,7 +262,18 @@ template <> struct Pot<M_QBALL> {
     const float du = fmaf(d[0], fmaf(0.5f, d[0], k.p1), d[1] * fmaf(0.5f, d[1], k.p2));
     const float u = k.u0 + du;
     if (u > 0.f) {
-      const float l = log1pf(du * k.inv_u0);
+      // log1p(y), y = du / u0: for |y| < 2^-7 the Taylor series y - y^2/2 +
+      // y^3/3 - y^4/4 (the first omitted term is below 2^-30 |y|, under the
+      // rounding of float32), else log1pf
+      const float y = du * k.inv_u0;
+      float l;
+      if (fabsf(y) < 0.0078125f) {
+        float q = fmaf(y, -0.25f, 0.333333343f);
+        q = fmaf(q, y, -0.5f);
+        l = fmaf(q * y, y, y);
+      } else {
+        l = log1pf(y);
+      }
       const float Kl = k.K * l;
       dVd[0] = k.m2 * fmaf(k.A, d[0], Kl * (k.p1 + d[0]));
       dVd[1] = k.m2 * fmaf(k.A, d[1], Kl * (k.p2 + d[1]));

@@ -668,21 +668,24 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
 // Split-FP32 form.
 // ---------------------------------------------------------------------------
 // Producer of ring plane gp (one warp): waits until every warp has released
-// the slot's previous plane, then lane 0 issues the copies.
+// the slot's previous plane, then lane 0 issues the copies.  Kept out of line
+// (it runs once per plane in one warp); its shared-memory pointers come by
+// value, so the caller's PShared stays in registers, not on the stack.
 template <int NF, int VX, bool CORNERS, int NSLOT>
-__device__ __noinline__ bool produce_split(const PParams& p, const PShared& sm, int ib, uint32_t gp,
-                                           int4 u, int q) {
+__device__ __noinline__ bool produce_split(const PParams& p, unsigned char* ring, uint64_t* full,
+                                           uint64_t* empty, uint32_t* issued, long long limit,
+                                           int ib, uint32_t gp, int4 u, int q) {
   using LY = PLayout<NF, VX, 4>;
   bool ok = true;
   if (gp >= (uint32_t)NSLOT) {
     const uint32_t rr = gp - NSLOT;
-    ok = mbar_wait(&sm.empty[rr % NSLOT], (rr / NSLOT) & 1, sm.limit);
+    ok = mbar_wait(&empty[rr % NSLOT], (rr / NSLOT) & 1, limit);
   }
   if (!__all_sync(0xffffffffu, ok)) return false;
   if ((threadIdx.x & 31) == 0) {
-    pproduce<NF, VX, 4, CORNERS>(p, ib, u, q, sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
-                                 &sm.full[gp % NSLOT]);
-    sm.issued[gp % NSLOT] = gp + 1;
+    pproduce<NF, VX, 4, CORNERS>(p, ib, u, q, ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                 &full[gp % NSLOT]);
+    issued[gp % NSLOT] = gp + 1;
   }
   return true;
 }
@@ -791,7 +794,9 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
       if (pQ > 0) {
         const uint32_t gp = g + LEAD;
         if ((int)(gp % kPWarps) == ly)
-          ok = produce_split<NF, VX, CORNERS, NSLOT>(p, sm, ib, gp, sm.units[pui], puq) && ok;
+          ok = produce_split<NF, VX, CORNERS, NSLOT>(p, sm.ring, sm.full, sm.empty, sm.issued,
+                                                     sm.limit, ib, gp, sm.units[pui], puq) &&
+               ok;
         if (++puq == pQ) {
           ++pui;
           puq = 0;

@@ -45,3 +45,26 @@ def test_split_errors_against_oracle(name, order, n, steps, stencil):
     assert erho < 1e-7
     assert max(evar) < 1e-4
     assert max(G.field_errors(gphi, st.phi)) < 1e-5
+
+
+@pytest.mark.parametrize("amp", [1e-6, 0.05])
+@pytest.mark.parametrize("n", [64, 24])
+def test_qball_log1p_branches(amp, n):
+    """The split Q-ball takes log1p(du/u0) by its Taylor series for |du/u0| <
+    2^-7 and by log1pf beyond: fluctuations of 1e-6 keep every site on the
+    series, 0.05 puts many on log1pf (persistent kernel at 64, per-stage
+    kernel at 24).  Errors at 1e-4 of the fluctuation scale, as above."""
+    w = I.workload("qball256")
+    phi, pi = I.initial_fields(w, n=n)
+    phi = phi + amp * np.random.default_rng(12).standard_normal(phi.shape)
+    gphi, gpi, ge = G.run_gpu(P, G.gpu_cfg(P, w, n=n, order=4, precision="split_fp32"),
+                              phi, pi, 3)
+    st, oe = G.run_oracle(G.oracle_cfg(w, n=n, order=4), phi, pi, 3)
+    for g, o in ((gphi, st.phi), (gpi, st.pi)):
+        for f in range(2):
+            scale = float(np.max(np.abs(o[f] - o[f].mean())))
+            err = float(np.max(np.abs(g[f] - o[f]))) / scale
+            print(f"\nqball split amp={amp} n={n}: error {err:.1e} of scale {scale:.1e}")
+            assert err < 1e-4, (amp, n, f, err)
+    # p_a sums V and phi D over fluctuations up to 0.05 in float32 parts
+    assert G.rel(ge["a"], st.a) < 1e-9 and G.rel(ge["pa"], st.pa) < 1e-6
