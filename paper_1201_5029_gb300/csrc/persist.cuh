@@ -401,8 +401,9 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
         }
       }
       if (__syncthreads_or(!ok)) return false;   // one decision for the whole block
-      if (tid == 0 && pui < sm.nunits) {
-        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift
+      if (tid == kPThreads - 32 && pui < sm.nunits) {
+        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift;
+        // the last warp issues the copies (warps 0 and 1 drift the halo rows)
         const uint32_t gp = g + LEAD;
         pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
                                      sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
@@ -579,8 +580,9 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
         }
       }
       if (__syncthreads_or(!ok)) return false;   // one decision for the whole block
-      if (tid == 0 && pui < sm.nunits) {
-        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift
+      if (tid == kPThreads - 32 && pui < sm.nunits) {
+        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift;
+        // the last warp issues the copies (warps 0 and 1 drift the halo rows)
         const uint32_t gp = g + LEAD;
         pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
                                      sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
