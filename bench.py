@@ -298,7 +298,7 @@ def serving_leg(P, I, count, steps_scale, load, other_loads=(), calib_count=100)
     """Serving mix (sizes 32..384^3, three models, orders 2..8): a closed-loop
     calibration of the FP64 form's capacity on the first `calib_count`
     requests, then the Poisson arrival stream of all `count` requests at
-    `load` x that capacity for each form (the headline), and the split form at
+    `load` x that capacity for each form (the headline), and both forms at
     each of `other_loads` x that capacity (reported under "by_load")."""
     reqs = I.serving_requests(count=count, steps_scale=steps_scale)
     work_of = lambda r: r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])  # noqa
@@ -318,11 +318,11 @@ def serving_leg(P, I, count, steps_scale, load, other_loads=(), calib_count=100)
     for prec, items in (("fp64", items64), ("split_fp32", items32)):
         out[prec] = _serve(P, items, arr)
     by_load = {}
+    keep = ("p50_s", "p99_s", "site_updates_per_s", "completed", "failed")
     for lo in other_loads:
         arr_lo = I.poisson_arrivals(lo * capacity, len(reqs), I.SERVING_MIX["arrival_seed"])
-        by_load[str(lo)] = {"split_fp32": {k: v for k, v in _serve(P, items32, arr_lo).items()
-                                           if k in ("p50_s", "p99_s", "site_updates_per_s",
-                                                    "completed", "failed")}}
+        by_load[str(lo)] = {prec: {k: v for k, v in _serve(P, items, arr_lo).items() if k in keep}
+                            for prec, items in (("fp64", items64), ("split_fp32", items32))}
     if by_load:
         out["by_load"] = by_load
     return out
@@ -604,7 +604,7 @@ def main():
     ap.add_argument("--serving-steps-scale", type=float, default=0.02)
     ap.add_argument("--serving-load", type=float, default=0.7)
     ap.add_argument("--serving-other-loads", default="",
-                    help="further offered loads (comma list), split form, under by_load")
+                    help="further offered loads (comma list), both forms, under by_load")
     ap.add_argument("--forms", default="fp64,split_fp32,split_dd",
                     help="comma list of forms to time (profiling a single kernel)")
     args = ap.parse_args()

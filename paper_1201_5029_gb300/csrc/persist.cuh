@@ -91,10 +91,18 @@ struct PRing {
   static constexpr bool ALU = PREC != PREC_SPLIT;
   using LY = PLayout<NF, VX, prec_word(PREC)>;
   static constexpr int DRIFT_ELEMS = NF * (kPTY + 2) * LY::TX;
+  // split-DD: NDRIFT planes in flight, each the drifted phi rows (with the
+  // halo rows), the re-centred pi of the own rows and the halo-column values
+  // (up to 3 rows per edge lane); FP64: two drifted planes
+  static constexpr int NDRIFT = PREC == PREC_DD ? 4 : 2;
+  static constexpr int PI_ELEMS = NF * kPTY * LY::TX;
+  static constexpr int COL_ELEMS = NF * kPTY * 2 * 3;
+  static constexpr int DRIFT_WORDS =
+      PREC == PREC_DD ? NDRIFT * (DRIFT_ELEMS + PI_ELEMS + COL_ELEMS) : 2 * DRIFT_ELEMS;
   static constexpr int KAHAN_BYTES = NQ * kKahanGroups * 8;
   static constexpr int ROWS_BYTES = kMaxPBlocks * kNQ * 8;
   static constexpr int EXTRA_BYTES =
-      ALU ? 2 * DRIFT_ELEMS * 8 + NQ * kPThreads * 8
+      ALU ? DRIFT_WORDS * 8 + NQ * kPThreads * 8
           : (KAHAN_BYTES > ROWS_BYTES ? KAHAN_BYTES : ROWS_BYTES);
   static constexpr int FIT = (kPSmemBudget - EXTRA_BYTES) / LY::SLOT_BYTES;
   static constexpr int NSLOT = ALU ? 3 : (FIT < 10 ? FIT : 10);
@@ -106,6 +114,7 @@ struct PRing {
   static constexpr int RING_BYTES = NSLOT * LY::SLOT_BYTES;
   static constexpr int SMEM_BYTES = RING_BYTES + EXTRA_BYTES;
   static_assert(NSLOT >= 5 || ALU, "split ring too shallow");
+  static_assert(SMEM_BYTES <= kPSmemBudget, "shared memory of the persistent kernel");
   static_assert(PRE >= 1, "a warp to issue the first planes beside the folds");
 };
 
@@ -123,6 +132,7 @@ struct PShared {
   double* red;            // FP64: block-reduction scratch [NQ][kPThreads]
   uint64_t* full;
   uint64_t* empty;
+  uint64_t* dbar;         // split-DD: per drift buffer, every warp has drifted its plane
   const int4* units;      // (x0, y0, z0, Q): tile origin, first output plane, planes incl. halos
   int nunits;
   uint32_t* issued;       // per slot: 1 + ring index of the last plane issued
@@ -473,16 +483,100 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
 // Split-DD form: phi = phi0 + d with the background phi0 in float64 (advanced
 // by the scalar chain) and the fluctuation d stored and updated as a
 // double-float (two float32 per value, 8 bytes: the traffic of the FP64
-// form).  The structure is the FP64 form's (each plane drifted once into a
-// shared-memory buffer, one block barrier per plane); the arithmetic is that
-// of the split-FP32 form (stencil on phi + c pi, re-centred output, difference
-// forms of V') in double-float on the FP32 pipe.
+// form).  The arithmetic is that of the split-FP32 form (stencil on
+// phi + c pi, re-centred output, difference forms of V') in double-float on
+// the FP32 pipe.
+//
+// Planes flow through NDRIFT shared-memory drift buffers without a block
+// barrier in the z loop: at plane g a warp first drifts plane g + 1 (its own
+// row, the halo rows for warps 2j and 2j + 1, j = (g + 1) mod 8, the halo
+// columns for lanes 0 and 31)
+// into buffer (g + 1) % NDRIFT and arrives on that buffer's mbarrier, then
+// waits until every warp has drifted plane g and computes plane g from buffer
+// g % NDRIFT.  A warp can so run up to one plane ahead of the slowest one.
+// Buffer (g + 1) % NDRIFT was last read for plane g + 1 - NDRIFT; a warp
+// writing it has passed the wait for plane g - 1, which every warp arrived at
+// after finishing plane g - 3, so NDRIFT = 4 buffers suffice.  Ring slot
+// g % NSLOT is free once every warp has drifted plane g: the last warp then
+// issues plane g + NSLOT into it.
 // ---------------------------------------------------------------------------
+// Drift of ring plane gg (of unit uu) into drift buffer gg % NDRIFT, then this
+// warp's arrival on the buffer's mbarrier.  Returns false if the plane's
+// copies did not land within the limit (the buffer then holds garbage, which
+// the caller never uses: the stage fails).
+template <int MODEL, int STENCIL, int VX>
+__device__ __forceinline__ bool drift_dd(const Ctx<MODEL, PREC_DD>& cx, const PShared& sm,
+                                         uint32_t gg, int4 uu, int n) {
+  using T = dd;
+  constexpr int NF = Ctx<MODEL, PREC_DD>::NF;
+  constexpr int NQ = Ctx<MODEL, PREC_DD>::SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int CR = CORNERS ? 3 : 1;
+  using LY = PLayout<NF, VX, 8>;
+  using RG = PRing<PREC_DD, NF, VX, NQ>;
+  constexpr int TX = LY::TX, CW = LY::CW, NSLOT = RG::NSLOT, NB = RG::NDRIFT;
+  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+  const int side = lane == 31 ? 1 : 0;
+  const bool edge = lane == 0 || lane == 31;
+  const int own = (ly + 1) * TX + lane * VX;
+  const int s = gg % NSLOT, b = gg % NB;
+  const int hw = (ly - 2 * (int)(gg % (kPWarps / 2)) + kPWarps) % kPWarps;
+  const bool ok = mbar_wait(&sm.full[s], (gg / NSLOT) & 1, sm.limit);
+  const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
+  T* dp = reinterpret_cast<T*>(sm.drift) + (size_t)b * RG::DRIFT_ELEMS;
+  T* pp = reinterpret_cast<T*>(sm.drift) + (size_t)NB * RG::DRIFT_ELEMS + (size_t)b * RG::PI_ELEMS;
+  T* cp = reinterpret_cast<T*>(sm.drift) + (size_t)NB * (RG::DRIFT_ELEMS + RG::PI_ELEMS) +
+          (size_t)b * RG::COL_ELEMS;
+  const T cd = cx.cdrift;
+  const bool clear = yclear(uu, n);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const T* mph = sl + LY::main_off(0, f);
+    const T* mpi = sl + LY::main_off(1, f);
+    T* dph = dp + f * (kPTY + 2) * TX;
+    T a[VX], c[VX];
+    vload<T, VX>(&mph[own], a);
+    vload<T, VX>(&mpi[own], c);
+    T q[VX];
+#pragma unroll
+    for (int jj = 0; jj < VX; ++jj) {
+      q[jj] = c[jj] - cx.mu_pi[f];
+      a[jj] = dd_fma(cd, c[jj], a[jj]);
+    }
+    vstore<T, VX>(&dph[own], a);
+    vstore<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], q);
+    if (hw < 2) {   // the two halo rows rotate over the warps, plane by plane
+      const int r = (hw == 0 ? 0 : kPTY + 1) * TX + lane * VX;
+      vload<T, VX>(&mph[r], a);
+      vload<T, VX>(&mpi[r], c);
+#pragma unroll
+      for (int jj = 0; jj < VX; ++jj) a[jj] = dd_fma(cd, c[jj], a[jj]);
+      vstore<T, VX>(&dph[r], a);
+    }
+    if (edge) {
+      const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
+      const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
+#pragma unroll
+      for (int rr = 0; rr < CR; ++rr) {
+        const int r = ly + 1 + rr - (CR - 1) / 2;
+        const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+        cp[((f * kPTY + ly) * 2 + side) * 3 + rr] = dd_fma(cd, cpi[row], cph[row]);
+      }
+    }
+  }
+  // one arrival for the warp: __syncwarp orders the lanes' shared-memory
+  // writes before lane 0's arrival, whose release makes them visible to the
+  // threads whose wait (acquire) observes the completed phase
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&sm.dbar[b]);
+  return ok;
+}
+
 // One stage over this block's units.  This thread's stage sums (NQ
 // double-floats, the running accumulators folded in every KGROUP planes) live
 // in its own slots of the block-reduction scratch, sm.red[q * threads + tid]
 // (free during the sweep), to keep registers for the sweep.
-// Returns false (in every thread) if a wait gave up.
+// Returns false if a wait gave up (the caller combines the threads' results).
 template <int MODEL, int STENCIL, int VX, int MODE>
 __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC_DD>& cx,
                                          const PShared& sm, uint32_t gq, int ib) {
@@ -495,9 +589,10 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
   constexpr int CR = CORNERS ? 3 : 1;
   using LY = PLayout<NF, VX, 8>;
   using RG = PRing<PREC_DD, NF, VX, NQ>;
-  constexpr int TX = LY::TX, CW = LY::CW;
-  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  constexpr int TX = LY::TX;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD, NB = RG::NDRIFT;
   constexpr int KGROUP = 8;   // output planes per running accumulator before it is folded
+  static_assert(LEAD + 1 == NSLOT, "the stage issues plane gq + LEAD, then g + NSLOT at plane g");
   const SimDesc& d = *sm.d;
   const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
   const int n = p.g.n;
@@ -510,9 +605,9 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
   T Mf[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) Mf[f] = dd_fma(cd, cx.mu_pi[f], cx.mu_phi[f]);
-  const int side = lane == 31 ? 1 : 0;
-  const bool edge = lane == 0 || lane == 31;          // lanes that read a halo column
   const int own = (ly + 1) * TX + lane * VX;          // this lane's sites in a slot row
+  const int side = lane == 31 ? 1 : 0;
+  const bool edge = lane == 0 || lane == 31;
   DDAcc acc[NQ];
   dd* tot = reinterpret_cast<dd*>(sm.red) + tid;        // tot[q * kPThreads]
 #pragma unroll
@@ -521,14 +616,28 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
     tot[i * kPThreads] = dd(0.f, 0.f);
   }
   int kg = 0;
+  bool ok = true;
 
-  int pui = 0, puq = 0;                                 // producer position, LEAD ahead
+  // producer position: the kernel issued planes gq .. gq + LEAD - 1; this
+  // stage issues plane gq + LEAD now (its slot held the previous stage's last
+  // plane, drifted by every warp) and plane g + NSLOT at plane g
+  int pui = 0, puq = 0;
   for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  const bool producer = tid == kPThreads - 32;
+  if (producer && pui < sm.nunits) {
+    const uint32_t gp = gq + LEAD;
+    pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
+                                 sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                 &sm.full[gp % NSLOT]);
+    sm.issued[gp % NSLOT] = gp + 1;
+  }
+  padvance(sm, pui, puq);
+
   uint32_t g = gq;
-  for (int i = 0; i < sm.nunits; ++i) {
+  if (sm.nunits > 0) ok = drift_dd<MODEL, STENCIL, VX>(cx, sm, g, sm.units[0], n);
+  for (int i = 0; i < sm.nunits && ok; ++i) {
     const int4 u = sm.units[i];
     const int Q = u.w;
-    const bool clear = yclear(u, n);
     const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
     T part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
 #pragma unroll
@@ -537,53 +646,18 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
       for (int jj = 0; jj < VX; ++jj)
         part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = T(0.0);
     for (int q = 0; q < Q; ++q, ++g) {
-      const int s = g % NSLOT;
-      const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
-      T* dp = reinterpret_cast<T*>(sm.drift) + (g & 1) * RG::DRIFT_ELEMS;   // drifted plane
-      const bool ok = mbar_wait(&sm.full[s], (g / NSLOT) & 1, sm.limit);
-      // drift the own row and the two halo rows (warps 0 and 1) into the drift
-      // buffer, and the halo-column values lanes 0 and 31 need (registers)
-      T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const T* mph = sl + LY::main_off(0, f);
-        const T* mpi = sl + LY::main_off(1, f);
-        T* dph = dp + f * (kPTY + 2) * TX;
-        T a[VX], b[VX];
-        vload<T, VX>(&mph[own], a);
-        vload<T, VX>(&mpi[own], b);
-#pragma unroll
-        for (int jj = 0; jj < VX; ++jj) {
-          cur_pi[f][jj] = b[jj] - cx.mu_pi[f];
-          cur_ph[f][jj] = dd_fma(cd, b[jj], a[jj]);
-        }
-        vstore<T, VX>(&dph[own], cur_ph[f]);
-        if (ly < 2) {
-          const int r = (ly == 0 ? 0 : kPTY + 1) * TX + lane * VX;
-          vload<T, VX>(&mph[r], a);
-          vload<T, VX>(&mpi[r], b);
-#pragma unroll
-          for (int jj = 0; jj < VX; ++jj) a[jj] = dd_fma(cd, b[jj], a[jj]);
-          vstore<T, VX>(&dph[r], a);
-        }
-#pragma unroll
-        for (int rr = 0; rr < CR; ++rr) el[f][rr] = T(0.0);
-        if (edge) {
-          const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
-          const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
-#pragma unroll
-          for (int rr = 0; rr < CR; ++rr) {
-            const int r = ly + 1 + rr - (CR - 1) / 2;
-            const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
-            el[f][rr] = dd_fma(cd, cpi[row], cph[row]);
-          }
-        }
-      }
-      if (__syncthreads_or(!ok)) return false;   // one decision for the whole block
-      if (tid == kPThreads - 32 && pui < sm.nunits) {
-        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift;
-        // the last warp issues the copies (warps 0 and 1 drift the halo rows)
-        const uint32_t gp = g + LEAD;
+      // look ahead: drift the stage's next plane
+      if (q + 1 < Q)
+        ok = drift_dd<MODEL, STENCIL, VX>(cx, sm, g + 1, u, n) && ok;
+      else if (i + 1 < sm.nunits)
+        ok = drift_dd<MODEL, STENCIL, VX>(cx, sm, g + 1, sm.units[i + 1], n) && ok;
+      // every warp has drifted plane g
+      ok = mbar_wait(&sm.dbar[g % NB], (g / NB) & 1, sm.limit) && ok;
+      if (!ok) break;
+      // the copies of plane g + NSLOT: lane 0 of the warp two after the ones
+      // that drift plane g + 1's halo rows
+      if (tid == 32 * (int)((2 * ((g + 1) % (kPWarps / 2)) + 2) % kPWarps) && pui < sm.nunits) {
+        const uint32_t gp = g + NSLOT;   // into slot g % NSLOT, free now
         pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
                                      sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
                                      &sm.full[gp % NSLOT]);
@@ -591,11 +665,23 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
       }
       padvance(sm, pui, puq);
 
+      const int b = g % NB;
+      const T* dp = reinterpret_cast<const T*>(sm.drift) + (size_t)b * RG::DRIFT_ELEMS;
+      const T* pp = reinterpret_cast<const T*>(sm.drift) + (size_t)NB * RG::DRIFT_ELEMS +
+                    (size_t)b * RG::PI_ELEMS;
+      const T* cp = reinterpret_cast<const T*>(sm.drift) +
+                    (size_t)NB * (RG::DRIFT_ELEMS + RG::PI_ELEMS) + (size_t)b * RG::COL_ELEMS;
+      T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
       const bool mid = q > 0 && q < Q - 1;   // the z-halo planes need S_off only
       T so_new[NF][VX], smid_new[NF][VX];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const T* dph = dp + f * (kPTY + 2) * TX;
+        vload<T, VX>(&dph[own], cur_ph[f]);
+        vload<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], cur_pi[f]);
+#pragma unroll
+        for (int rr = 0; rr < CR; ++rr)
+          el[f][rr] = edge ? cp[((f * kPTY + ly) * 2 + side) * 3 + rr] : T(0.0);
         T dn[VX], up[VX];
 #pragma unroll
         for (int jj = 0; jj < VX; ++jj) dn[jj] = up[jj] = T(0.0);
@@ -663,7 +749,7 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
     acc[i2].fold(t);
     tot[i2 * kPThreads] = t;
   }
-  return true;
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -950,7 +1036,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
                 "the rows of every block fit the reduction scratch");
 
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT], foldbar;
+  __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT], foldbar, dbar[RG::NDRIFT];
   // background and stage coefficients, double-buffered: at a stage boundary
   // one thread derives the next coefficients while another does the rest of
   // the background bookkeeping
@@ -982,9 +1068,10 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   sm.ring = dsm;
   sm.kahan = reinterpret_cast<float2*>(dsm + RG::RING_BYTES);
   sm.drift = reinterpret_cast<double*>(dsm + RG::RING_BYTES);
-  sm.red = reinterpret_cast<double*>(dsm + RG::RING_BYTES) + 2 * RG::DRIFT_ELEMS;
+  sm.red = reinterpret_cast<double*>(dsm + RG::RING_BYTES) + RG::DRIFT_WORDS;
   sm.full = full;
   sm.empty = empty;
+  sm.dbar = dbar;
   sm.units = s_units;
   sm.issued = s_issued;
   sm.limit = p.wait_limit;
@@ -997,6 +1084,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       mbar_init(&empty[s], kPWarps);
     }
     mbar_init(&foldbar, 1);
+    for (int b = 0; b < RG::NDRIFT; ++b) mbar_init(&dbar[b], kPWarps);
     fence_mbar_init();
     s_bad = 0;
     s_fold = -1;
