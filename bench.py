@@ -30,7 +30,6 @@ reports the whole-job rate over the slowest rank.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -79,12 +78,18 @@ FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
 
 
+# the sources evolve_persist is compiled from (its translation units and headers)
+KERNEL_SOURCES = ("persist.cuh", "persist_fp64.cu", "persist_split.cu", "persist_dd.cu",
+                  "sweep.cuh", "internal.cuh", "models.cuh", "models_dd.cuh", "dd.cuh")
+
+
 def kernel_source_hash() -> str:
-    """SHA-256 (first 16 hex digits) of the CUDA sources of the library."""
+    """SHA-256 (first 16 hex digits) of the sources of the persistent evolve
+    kernel: a traffic figure measured on other sources is not used."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1201_5029_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    for name in sorted(KERNEL_SOURCES):
+        with open(os.path.join(ROOT, "paper_1201_5029_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 

@@ -91,14 +91,14 @@ struct PRing {
   static constexpr bool ALU = PREC != PREC_SPLIT;
   using LY = PLayout<NF, VX, prec_word(PREC)>;
   static constexpr int DRIFT_ELEMS = NF * (kPTY + 2) * LY::TX;
-  // split-DD: NDRIFT planes in flight, each the drifted phi rows (with the
-  // halo rows), the re-centred pi of the own rows and the halo-column values
-  // (up to 3 rows per edge lane); FP64: two drifted planes
-  static constexpr int NDRIFT = PREC == PREC_DD ? 4 : 2;
+  // FP64 and split-DD: NDRIFT planes in flight, each the drifted phi rows
+  // (with the halo rows), the pi of the own rows (re-centred for split-DD) and
+  // the halo-column values (up to 3 rows per edge lane)
+  static constexpr int NDRIFT = ALU ? 4 : 2;
   static constexpr int PI_ELEMS = NF * kPTY * LY::TX;
   static constexpr int COL_ELEMS = NF * kPTY * 2 * 3;
   static constexpr int DRIFT_WORDS =
-      PREC == PREC_DD ? NDRIFT * (DRIFT_ELEMS + PI_ELEMS + COL_ELEMS) : 2 * DRIFT_ELEMS;
+      ALU ? NDRIFT * (DRIFT_ELEMS + PI_ELEMS + COL_ELEMS) : 2 * DRIFT_ELEMS;
   static constexpr int KAHAN_BYTES = NQ * kKahanGroups * 8;
   static constexpr int ROWS_BYTES = kMaxPBlocks * kNQ * 8;
   static constexpr int EXTRA_BYTES =
@@ -328,13 +328,89 @@ __device__ __forceinline__ void lane_parts(const T (&ctr)[VX], const T (&dn)[VX]
   plane_parts<T, VX, CORNERS, MID>(ctr, dn, up, left, right, dl, dr, ul, ur, smid, so);
 }
 
+// FP64 and split-DD forms: drift of ring plane gg (of unit uu) into drift
+// buffer gg % NDRIFT, then this warp's arrival on the buffer's mbarrier.  Returns false if the plane's
+// copies did not land within the limit (the buffer then holds garbage, which
+// the caller never uses: the stage fails).
+template <int MODEL, int STENCIL, int VX, int PREC>
+__device__ __forceinline__ bool drift_alu(const Ctx<MODEL, PREC>& cx, const PShared& sm,
+                                          uint32_t gg, int4 uu, int n) {
+  static_assert(PREC == PREC_FP64 || PREC == PREC_DD, "the FP64 and split-DD forms");
+  using T = typename std::conditional<PREC == PREC_DD, dd, double>::type;
+  constexpr int NF = Ctx<MODEL, PREC>::NF;
+  constexpr int NQ = Ctx<MODEL, PREC>::SL::NQ;
+  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
+  constexpr int CR = CORNERS ? 3 : 1;
+  using LY = PLayout<NF, VX, 8>;
+  using RG = PRing<PREC, NF, VX, NQ>;
+  constexpr int TX = LY::TX, CW = LY::CW, NSLOT = RG::NSLOT, NB = RG::NDRIFT;
+  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+  const int side = lane == 31 ? 1 : 0;
+  const bool edge = lane == 0 || lane == 31;
+  const int own = (ly + 1) * TX + lane * VX;
+  const int s = gg % NSLOT, b = gg % NB;
+  const int hw = (ly - 2 * (int)(gg % (kPWarps / 2)) + kPWarps) % kPWarps;
+  const bool ok = mbar_wait(&sm.full[s], (gg / NSLOT) & 1, sm.limit);
+  const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
+  T* dp = reinterpret_cast<T*>(sm.drift) + (size_t)b * RG::DRIFT_ELEMS;
+  T* pp = reinterpret_cast<T*>(sm.drift) + (size_t)NB * RG::DRIFT_ELEMS + (size_t)b * RG::PI_ELEMS;
+  T* cp = reinterpret_cast<T*>(sm.drift) + (size_t)NB * (RG::DRIFT_ELEMS + RG::PI_ELEMS) +
+          (size_t)b * RG::COL_ELEMS;
+  const T cd = cx.cdrift;
+  const bool clear = yclear(uu, n);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const T* mph = sl + LY::main_off(0, f);
+    const T* mpi = sl + LY::main_off(1, f);
+    T* dph = dp + f * (kPTY + 2) * TX;
+    T a[VX], c[VX];
+    vload<T, VX>(&mph[own], a);
+    vload<T, VX>(&mpi[own], c);
+    T q[VX];
+#pragma unroll
+    for (int jj = 0; jj < VX; ++jj) {
+      if constexpr (PREC == PREC_DD) q[jj] = c[jj] - cx.mu_pi[f];   // re-centred
+      else q[jj] = c[jj];
+      a[jj] = madd(cd, c[jj], a[jj]);
+    }
+    vstore<T, VX>(&dph[own], a);
+    vstore<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], q);
+    if (hw < 2) {   // the two halo rows rotate over the warps, plane by plane
+      const int r = (hw == 0 ? 0 : kPTY + 1) * TX + lane * VX;
+      vload<T, VX>(&mph[r], a);
+      vload<T, VX>(&mpi[r], c);
+#pragma unroll
+      for (int jj = 0; jj < VX; ++jj) a[jj] = madd(cd, c[jj], a[jj]);
+      vstore<T, VX>(&dph[r], a);
+    }
+    if (edge) {
+      const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
+      const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
+#pragma unroll
+      for (int rr = 0; rr < CR; ++rr) {
+        const int r = ly + 1 + rr - (CR - 1) / 2;
+        const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+        cp[((f * kPTY + ly) * 2 + side) * 3 + rr] = madd(cd, cpi[row], cph[row]);
+      }
+    }
+  }
+  // one arrival for the warp: __syncwarp orders the lanes' shared-memory
+  // writes before lane 0's arrival, whose release makes them visible to the
+  // threads whose wait (acquire) observes the completed phase
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&sm.dbar[b]);
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 form.
 // ---------------------------------------------------------------------------
-// One stage of the FP64 form over this block's units: each plane is drifted
-// once into a shared-memory drift buffer, then one block barrier, then the
-// stencil from the drifted plane.  Returns false (in every thread) if a wait gave up.
-// gq: ring planes consumed before this stage.
+// One stage of the FP64 form over this block's units.  The planes flow
+// through the drift buffers as in the split-DD form (below): each warp drifts
+// plane g + 1 (drift_alu), then waits until every warp has drifted plane g and
+// computes it, with no block barrier in the z loop; the halo rows and the copy
+// issue rotate over the warps.  Returns false if a wait gave up (the caller
+// combines the threads' results).  gq: ring planes consumed before this stage.
 template <int MODEL, int STENCIL, int VX, int MODE>
 __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PREC_FP64>& cx,
                                            const PShared& sm, uint32_t gq, int ib, double* accd) {
@@ -346,25 +422,37 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
   constexpr int CR = CORNERS ? 3 : 1;
   using LY = PLayout<NF, VX, 8>;
   using RG = PRing<PREC_FP64, NF, VX, SL::NQ>;
-  constexpr int TX = LY::TX, CW = LY::CW;
-  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD;
+  constexpr int TX = LY::TX;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD, NB = RG::NDRIFT;
+  static_assert(LEAD + 1 == NSLOT, "the stage issues plane gq + LEAD, then g + NSLOT at plane g");
   const SimDesc& d = *sm.d;
   const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
   const int n = p.g.n;
   const size_t S = (size_t)d.S, nn = (size_t)n * n;
   T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
   T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
-  const T cd = cx.cdrift;
   const int side = lane == 31 ? 1 : 0;
+  const bool edge = lane == 0 || lane == 31;
   const int own = (ly + 1) * TX + lane * VX;          // this lane's sites in a slot row
+  bool ok = true;
 
-  int pui = 0, puq = 0;                                 // producer position, LEAD ahead
+  // producer position (see stage_dd): plane gq + LEAD now, plane g + NSLOT at plane g
+  int pui = 0, puq = 0;
   for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  if (tid == kPThreads - 32 && pui < sm.nunits) {
+    const uint32_t gp = gq + LEAD;
+    pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
+                                 sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                 &sm.full[gp % NSLOT]);
+    sm.issued[gp % NSLOT] = gp + 1;
+  }
+  padvance(sm, pui, puq);
+
   uint32_t g = gq;
-  for (int i = 0; i < sm.nunits; ++i) {
+  if (sm.nunits > 0) ok = drift_alu<MODEL, STENCIL, VX, PREC_FP64>(cx, sm, g, sm.units[0], n);
+  for (int i = 0; i < sm.nunits && ok; ++i) {
     const int4 u = sm.units[i];
     const int Q = u.w;
-    const bool clear = yclear(u, n);
     const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
     T part_m[NF][VX], so_m[NF][VX], ph_m[NF][VX], pi_m[NF][VX];
 #pragma unroll
@@ -372,49 +460,16 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
 #pragma unroll
       for (int jj = 0; jj < VX; ++jj) part_m[f][jj] = so_m[f][jj] = ph_m[f][jj] = pi_m[f][jj] = 0.0;
     for (int q = 0; q < Q; ++q, ++g) {
-      const int s = g % NSLOT;
-      const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
-      T* dp = sm.drift + (g & 1) * RG::DRIFT_ELEMS;   // this plane's drifted phi
-      const bool ok = mbar_wait(&sm.full[s], (g / NSLOT) & 1, sm.limit);
-      // drift the own row and the two halo rows (warps 0 and 1) into the
-      // drift buffer, and the halo-column values this lane needs (registers)
-      T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const T* mph = sl + LY::main_off(0, f);
-        const T* mpi = sl + LY::main_off(1, f);
-        T* dph = dp + f * (kPTY + 2) * TX;
-        T a[VX], b[VX];
-        vload<T, VX>(&mph[own], a);
-        vload<T, VX>(&mpi[own], b);
-#pragma unroll
-        for (int jj = 0; jj < VX; ++jj) {
-          cur_pi[f][jj] = b[jj];
-          cur_ph[f][jj] = madd(cd, b[jj], a[jj]);
-        }
-        vstore<T, VX>(&dph[own], cur_ph[f]);
-        if (ly < 2) {
-          const int r = (ly == 0 ? 0 : kPTY + 1) * TX + lane * VX;
-          vload<T, VX>(&mph[r], a);
-          vload<T, VX>(&mpi[r], b);
-#pragma unroll
-          for (int jj = 0; jj < VX; ++jj) a[jj] = madd(cd, b[jj], a[jj]);
-          vstore<T, VX>(&dph[r], a);
-        }
-        const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
-        const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
-#pragma unroll
-        for (int rr = 0; rr < CR; ++rr) {
-          const int r = ly + 1 + rr - (CR - 1) / 2;
-          const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
-          el[f][rr] = madd(cd, cpi[row], cph[row]);
-        }
-      }
-      if (__syncthreads_or(!ok)) return false;   // one decision for the whole block
-      if (tid == kPThreads - 32 && pui < sm.nunits) {
-        // slot (g + LEAD) % NSLOT was last read by the previous plane's drift;
-        // the last warp issues the copies (warps 0 and 1 drift the halo rows)
-        const uint32_t gp = g + LEAD;
+      // look ahead: drift the stage's next plane
+      if (q + 1 < Q)
+        ok = drift_alu<MODEL, STENCIL, VX, PREC_FP64>(cx, sm, g + 1, u, n) && ok;
+      else if (i + 1 < sm.nunits)
+        ok = drift_alu<MODEL, STENCIL, VX, PREC_FP64>(cx, sm, g + 1, sm.units[i + 1], n) && ok;
+      // every warp has drifted plane g
+      ok = mbar_wait(&sm.dbar[g % NB], (g / NB) & 1, sm.limit) && ok;
+      if (!ok) break;
+      if (tid == 32 * (int)((2 * ((g + 1) % (kPWarps / 2)) + 2) % kPWarps) && pui < sm.nunits) {
+        const uint32_t gp = g + NSLOT;   // into slot g % NSLOT, free now
         pproduce<NF, VX, 8, CORNERS>(p, ib, sm.units[pui], puq,
                                      sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
                                      &sm.full[gp % NSLOT]);
@@ -422,12 +477,25 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
       }
       padvance(sm, pui, puq);
 
+      const int b = g % NB;
+      const T* dp = sm.drift + (size_t)b * RG::DRIFT_ELEMS;
+      const T* pp = sm.drift + (size_t)NB * RG::DRIFT_ELEMS + (size_t)b * RG::PI_ELEMS;
+      const T* cp = sm.drift + (size_t)NB * (RG::DRIFT_ELEMS + RG::PI_ELEMS) +
+                    (size_t)b * RG::COL_ELEMS;
+      T cur_ph[NF][VX], cur_pi[NF][VX], el[NF][CR];
       const bool mid = q > 0 && q < Q - 1;   // the z-halo planes need S_off only
       T so_new[NF][VX], smid_new[NF][VX];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const T* dph = dp + f * (kPTY + 2) * TX;
+        vload<T, VX>(&dph[own], cur_ph[f]);
+        vload<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], cur_pi[f]);
+#pragma unroll
+        for (int rr = 0; rr < CR; ++rr)
+          el[f][rr] = edge ? cp[((f * kPTY + ly) * 2 + side) * 3 + rr] : 0.0;
         T dn[VX], up[VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) dn[jj] = up[jj] = 0.0;
         if (mid || CORNERS) {
           vload<T, VX>(&dph[own - TX], dn);
           vload<T, VX>(&dph[own + TX], up);
@@ -476,7 +544,7 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
         }
     }
   }
-  return true;
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -500,78 +568,6 @@ __device__ __forceinline__ bool stage_fp64(const PParams& p, const Ctx<MODEL, PR
 // g % NSLOT is free once every warp has drifted plane g: the last warp then
 // issues plane g + NSLOT into it.
 // ---------------------------------------------------------------------------
-// Drift of ring plane gg (of unit uu) into drift buffer gg % NDRIFT, then this
-// warp's arrival on the buffer's mbarrier.  Returns false if the plane's
-// copies did not land within the limit (the buffer then holds garbage, which
-// the caller never uses: the stage fails).
-template <int MODEL, int STENCIL, int VX>
-__device__ __forceinline__ bool drift_dd(const Ctx<MODEL, PREC_DD>& cx, const PShared& sm,
-                                         uint32_t gg, int4 uu, int n) {
-  using T = dd;
-  constexpr int NF = Ctx<MODEL, PREC_DD>::NF;
-  constexpr int NQ = Ctx<MODEL, PREC_DD>::SL::NQ;
-  constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
-  constexpr int CR = CORNERS ? 3 : 1;
-  using LY = PLayout<NF, VX, 8>;
-  using RG = PRing<PREC_DD, NF, VX, NQ>;
-  constexpr int TX = LY::TX, CW = LY::CW, NSLOT = RG::NSLOT, NB = RG::NDRIFT;
-  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
-  const int side = lane == 31 ? 1 : 0;
-  const bool edge = lane == 0 || lane == 31;
-  const int own = (ly + 1) * TX + lane * VX;
-  const int s = gg % NSLOT, b = gg % NB;
-  const int hw = (ly - 2 * (int)(gg % (kPWarps / 2)) + kPWarps) % kPWarps;
-  const bool ok = mbar_wait(&sm.full[s], (gg / NSLOT) & 1, sm.limit);
-  const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
-  T* dp = reinterpret_cast<T*>(sm.drift) + (size_t)b * RG::DRIFT_ELEMS;
-  T* pp = reinterpret_cast<T*>(sm.drift) + (size_t)NB * RG::DRIFT_ELEMS + (size_t)b * RG::PI_ELEMS;
-  T* cp = reinterpret_cast<T*>(sm.drift) + (size_t)NB * (RG::DRIFT_ELEMS + RG::PI_ELEMS) +
-          (size_t)b * RG::COL_ELEMS;
-  const T cd = cx.cdrift;
-  const bool clear = yclear(uu, n);
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const T* mph = sl + LY::main_off(0, f);
-    const T* mpi = sl + LY::main_off(1, f);
-    T* dph = dp + f * (kPTY + 2) * TX;
-    T a[VX], c[VX];
-    vload<T, VX>(&mph[own], a);
-    vload<T, VX>(&mpi[own], c);
-    T q[VX];
-#pragma unroll
-    for (int jj = 0; jj < VX; ++jj) {
-      q[jj] = c[jj] - cx.mu_pi[f];
-      a[jj] = dd_fma(cd, c[jj], a[jj]);
-    }
-    vstore<T, VX>(&dph[own], a);
-    vstore<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], q);
-    if (hw < 2) {   // the two halo rows rotate over the warps, plane by plane
-      const int r = (hw == 0 ? 0 : kPTY + 1) * TX + lane * VX;
-      vload<T, VX>(&mph[r], a);
-      vload<T, VX>(&mpi[r], c);
-#pragma unroll
-      for (int jj = 0; jj < VX; ++jj) a[jj] = dd_fma(cd, c[jj], a[jj]);
-      vstore<T, VX>(&dph[r], a);
-    }
-    if (edge) {
-      const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
-      const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
-#pragma unroll
-      for (int rr = 0; rr < CR; ++rr) {
-        const int r = ly + 1 + rr - (CR - 1) / 2;
-        const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
-        cp[((f * kPTY + ly) * 2 + side) * 3 + rr] = dd_fma(cd, cpi[row], cph[row]);
-      }
-    }
-  }
-  // one arrival for the warp: __syncwarp orders the lanes' shared-memory
-  // writes before lane 0's arrival, whose release makes them visible to the
-  // threads whose wait (acquire) observes the completed phase
-  __syncwarp();
-  if (lane == 0) mbar_arrive(&sm.dbar[b]);
-  return ok;
-}
-
 // One stage over this block's units.  This thread's stage sums (NQ
 // double-floats, the running accumulators folded in every KGROUP planes) live
 // in its own slots of the block-reduction scratch, sm.red[q * threads + tid]
@@ -634,7 +630,7 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
   padvance(sm, pui, puq);
 
   uint32_t g = gq;
-  if (sm.nunits > 0) ok = drift_dd<MODEL, STENCIL, VX>(cx, sm, g, sm.units[0], n);
+  if (sm.nunits > 0) ok = drift_alu<MODEL, STENCIL, VX, PREC_DD>(cx, sm, g, sm.units[0], n);
   for (int i = 0; i < sm.nunits && ok; ++i) {
     const int4 u = sm.units[i];
     const int Q = u.w;
@@ -648,9 +644,9 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
     for (int q = 0; q < Q; ++q, ++g) {
       // look ahead: drift the stage's next plane
       if (q + 1 < Q)
-        ok = drift_dd<MODEL, STENCIL, VX>(cx, sm, g + 1, u, n) && ok;
+        ok = drift_alu<MODEL, STENCIL, VX, PREC_DD>(cx, sm, g + 1, u, n) && ok;
       else if (i + 1 < sm.nunits)
-        ok = drift_dd<MODEL, STENCIL, VX>(cx, sm, g + 1, sm.units[i + 1], n) && ok;
+        ok = drift_alu<MODEL, STENCIL, VX, PREC_DD>(cx, sm, g + 1, sm.units[i + 1], n) && ok;
       // every warp has drifted plane g
       ok = mbar_wait(&sm.dbar[g % NB], (g / NB) & 1, sm.limit) && ok;
       if (!ok) break;
