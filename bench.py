@@ -117,11 +117,13 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.used = False   # a second `with` appends: summary() covers every region
         self.path = os.path.join("/tmp", f"pycool_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
-            self.fh = open(self.path, "w")
+            self.fh = open(self.path, "a" if self.used else "w")
+            self.used = True
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-i", str(self.index), "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -647,38 +649,23 @@ def main():
     peaks, peak_kind = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
 
-    with ClockSampler(local) as clk:
+    clk = ClockSampler(local)
+    with clk:
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         w, phi, pi, head = time_workload(P, torch, I, args.workload, forms, args.steps,
                                          args.warmup, flush_buf, stream, ws, hbm, peak_kind)
-        extra = {}
-        for name in extras:
-            extra[name] = time_workload(P, torch, I, name, forms, args.steps, args.warmup,
-                                        flush_buf, stream, ws, hbm, peak_kind)[3]
         torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-    clocks = clk.summary()
     nf = phi.shape[0]
     S = w["n"] ** 3
     s = P.pycool_stages_per_step(w["order"])
+    full = forms == list(FORMS)
 
-    if forms != list(FORMS):
-        if rank == 0:  # profiling run: a short line per workload and form, no baselines
-            for name, leg in [(args.workload, head)] + list(extra.items()):
-                for f in forms:
-                    r = leg["forms"][f]
-                    print(json.dumps({"workload": name, "form": f, "value": r["value"],
-                                      "unit": UNIT, "ms_per_step": r["ms_per_step"],
-                                      "launches": r["launches"], "status": r["status"],
-                                      "roofline_frac": r["roofline"]["frac"]}), flush=True)
-        return 0
-
-    # e2e through the public API with host buffers (FP64 form, headline workload)
+    # e2e through the public API with host buffers (FP64 form, headline workload),
+    # right after the headline's device timing
     e2e = None
-    if rank == 0 and not args.no_e2e:
+    if full and rank == 0 and not args.no_e2e:
         phi_pin = torch.from_numpy(phi).pin_memory().numpy()
         pi_pin = torch.from_numpy(pi).pin_memory().numpy()
         out_phi = torch.empty(phi.shape, dtype=torch.float64).pin_memory().numpy()
@@ -690,6 +677,29 @@ def main():
                "d2h_bytes_per_step": int(out_phi.nbytes + out_pi.nbytes),
                "form": "fp64", "steps": k,
                "note": "set_initial(host) + evolve(1) + get_fields(host) per step"}
+
+    extra = {}
+    with clk:
+        if ws > 1:
+            torch.distributed.barrier()
+        for name in extras:
+            extra[name] = time_workload(P, torch, I, name, forms, args.steps, args.warmup,
+                                        flush_buf, stream, ws, hbm, peak_kind)[3]
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+    clocks = clk.summary()
+
+    if not full:
+        if rank == 0:  # profiling run: a short line per workload and form, no baselines
+            for name, leg in [(args.workload, head)] + list(extra.items()):
+                for f in forms:
+                    r = leg["forms"][f]
+                    print(json.dumps({"workload": name, "form": f, "value": r["value"],
+                                      "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                                      "launches": r["launches"], "status": r["status"],
+                                      "roofline_frac": r["roofline"]["frac"]}), flush=True)
+        return 0
 
     serving = None
     if rank == 0 and not args.no_serving:
