@@ -114,11 +114,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, tag: str = "main"):
         self.index = index
         self.proc = None
         self.used = False   # a second `with` appends: summary() covers every region
-        self.path = os.path.join("/tmp", f"pycool_clocks_{os.getpid()}.csv")
+        self.path = os.path.join("/tmp", f"pycool_clocks_{os.getpid()}_{tag}.csv")
 
     def __enter__(self):
         try:
@@ -223,15 +223,25 @@ def e2e_form(P, torch, w, precision, steps, phi_pin, pi_pin, out_phi, out_pi, st
     sim.evolve(1)
     sim.get_fields(out_phi, out_pi)
     torch.cuda.synchronize()
+    phases = [0.0, 0.0, 0.0]
     t0 = time.perf_counter()
     for _ in range(steps):
+        ta = time.perf_counter()
         sim.set_initial(phi_pin, pi_pin)     # H2D from pinned host memory
+        tb = time.perf_counter()
         sim.evolve(1)
+        sim.sync()
+        tc = time.perf_counter()
         sim.get_fields(out_phi, out_pi)      # D2H of the step's result
+        td = time.perf_counter()
+        phases[0] += tb - ta
+        phases[1] += tc - tb
+        phases[2] += td - tc
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
-    return dt
+    return dt, {"set_initial": 1e3 * phases[0] / steps, "evolve": 1e3 * phases[1] / steps,
+                "get_fields": 1e3 * phases[2] / steps}
 
 
 def roofline(w, form, s, ms_per_step, hbm, peak_kind):
@@ -671,11 +681,15 @@ def main():
         out_phi = torch.empty(phi.shape, dtype=torch.float64).pin_memory().numpy()
         out_pi = torch.empty(pi.shape, dtype=torch.float64).pin_memory().numpy()
         k = args.e2e_steps
-        dt = e2e_form(P, torch, w, "fp64", k, phi_pin, pi_pin, out_phi, out_pi, stream)
+        eclk = ClockSampler(local, "e2e")
+        with eclk:
+            dt, phases = e2e_form(P, torch, w, "fp64", k, phi_pin, pi_pin, out_phi, out_pi,
+                                  stream)
         e2e = {"value": ws * S * s * k / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(phi.nbytes + pi.nbytes),
                "d2h_bytes_per_step": int(out_phi.nbytes + out_pi.nbytes),
-               "form": "fp64", "steps": k,
+               "form": "fp64", "steps": k, "ms_per_step_phases": phases,
+               "clocks": eclk.summary(),
                "note": "set_initial(host) + evolve(1) + get_fields(host) per step"}
 
     extra = {}
