@@ -80,7 +80,8 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
 
 # the sources evolve_persist is compiled from (its translation units and headers)
 KERNEL_SOURCES = ("persist.cuh", "persist_fp64.cu", "persist_split.cu", "persist_dd.cu",
-                  "sweep.cuh", "internal.cuh", "models.cuh", "models_dd.cuh", "dd.cuh")
+                  "persist_fp64_wide.cu", "persist_dd_wide.cu", "sweep.cuh", "internal.cuh",
+                  "models.cuh", "models_dd.cuh", "dd.cuh")
 
 
 def kernel_source_hash() -> str:

@@ -22,8 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpycool.so")
 SOURCES = ("api.cu", "sweep_fp64.cu", "sweep_split.cu", "persist_fp64.cu", "persist_split.cu",
-           "persist_dd.cu", "linear.cu", "observe.cu", "runtime_model.cu",
-           "server.cu", "noalloc.cu")
+           "persist_dd.cu", "persist_fp64_wide.cu", "persist_dd_wide.cu", "linear.cu",
+           "observe.cu", "runtime_model.cu", "server.cu", "noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

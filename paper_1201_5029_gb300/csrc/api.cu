@@ -108,7 +108,13 @@ Layout sim_layout(const pycool_config& c) {
   Layout L = layout_for(c);
   L.off_mean = align256(L.ws_bytes);
   L.ws_bytes = L.off_mean + align256((size_t)2 * kMeanBlocks * sizeof(double));
-  if (L.geo.tma) {
+  // the persistent kernel: n a multiple of 32, compiled models; the 13-point
+  // stencil in the FP64 and split-DD forms only (its per-stage fallback,
+  // like the split-FP32 form's, keeps the plain geometry)
+  const bool persist_ok =
+      L.geo.tma || (c.stencil == PYCOOL_STENCIL_4TH && c.n % 32 == 0 &&
+                    c.model < kRuntimeModelBase && c.precision != PYCOOL_SPLIT_FP32);
+  if (persist_ok) {
     L.off_prows = align256(L.ws_bytes);
     L.off_punits = L.off_prows + align256((size_t)2 * kMaxPBlocks * kNQ * sizeof(double));
     L.ws_bytes = L.off_punits + align256((size_t)kMaxPBlocks * kMaxPUnits * sizeof(int4)) +
@@ -131,10 +137,11 @@ Layout sim_layout(const pycool_config& c) {
 // block processes its units in the order dealt.  (rc, rw) minimises the
 // busiest block's cost, then the total.
 PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
-                std::vector<int4>* units, std::vector<int>* off) {
+                std::vector<int4>* units, std::vector<int>* off, int halo) {
   PGeo g;
   std::memset(&g, 0, sizeof(g));
   g.n = n;
+  g.halo = halo;
   g.vx = 1;
   for (int v = 4; v >= 1; v /= 2)
     if (v * nf * word <= 16 && n % (32 * v) == 0) { g.vx = v; break; }
@@ -193,13 +200,13 @@ PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
         const double p = is_wrap(u.t) ? pen : 1.0;
         const int len = u.z1 - u.z0;
         int k = len;
-        if (top.first + (len + 2.0 * h) * p > T + 1e-9) {
-          k = (int)std::floor((T - top.first) / p - 2.0 * h);
+        if (top.first + (len + 2.0 * halo * h) * p > T + 1e-9) {
+          k = (int)std::floor((T - top.first) / p - 2.0 * halo * h);
           if (len - k < kMinPiece) k = len - kMinPiece;
           if (k < kMinPiece) return false;   // the least loaded block is full: so are all
         }
         out.push_back(U{u.z0, u.z0 + k, u.t, top.second});
-        top.first += (k + 2.0 * h) * p;
+        top.first += (k + 2.0 * halo * h) * p;
         std::push_heap(heap.begin(), heap.end(), cmp);
         u.z0 += k;
       }
@@ -210,7 +217,7 @@ PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
     std::vector<double> load(cap, 0.0);
     std::vector<int> count(cap, 0);
     for (const U& u : out) {
-      load[u.b] += (u.z1 - u.z0 + 2.0 * h) * (is_wrap(u.t) ? pen : 1.0);
+      load[u.b] += (u.z1 - u.z0 + 2.0 * halo * h) * (is_wrap(u.t) ? pen : 1.0);
       count[u.b] += 1;
     }
     mx = *std::max_element(load.begin(), load.end());
@@ -231,7 +238,7 @@ PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
       if (j > 0 && rw == std::min(rws[j - 1], std::max(1, n / kMinPiece))) continue;
       if (pen == 1.0 && rw != rc) continue;
       chunks(rc, rw);
-      double lo = work / cap, hi = (double)n * pen + 2.0 * h * pen + lo;
+      double lo = work / cap, hi = (double)n * pen + 2.0 * halo * h * pen + lo;
       while (!deal(hi)) hi *= 2.0;
       for (int it = 0; it < 40 && hi - lo > 1e-3; ++it) {
         const double mid = 0.5 * (lo + hi);
@@ -267,7 +274,7 @@ PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
     std::vector<int> fill(off->begin(), off->end() - 1);
     for (const U& u : out)   // per block, in the order dealt
       (*units)[fill[u.b]++] =
-          int4{(u.t % g.tiles_x) * g.tx, (u.t / g.tiles_x) * 16, u.z0, u.z1 - u.z0 + 2};
+          int4{(u.t % g.tiles_x) * g.tx, (u.t / g.tiles_x) * 16, u.z0, u.z1 - u.z0 + 2 * halo};
   }
   return g;
 }
@@ -283,7 +290,7 @@ static bool check_plan(const PGeo& g, const std::vector<int4>& units, const std:
     if (off[b + 1] < off[b] || off[b + 1] - off[b] > kMaxPUnits) return false;
     for (int i = off[b]; i < off[b + 1]; ++i) {
       const int4 u = units[i];
-      const int planes = u.w - 2;
+      const int planes = u.w - 2 * g.halo;
       if (u.x < 0 || u.x % g.tx || u.x + g.tx > g.n || u.y < 0 || u.y % 16 || u.y + 16 > g.n ||
           u.z < 0 || planes < 1 || u.z + planes > g.n)
         return false;
@@ -347,8 +354,10 @@ pycool_status validate(const pycool_config* c) {
   if (c->stencil != PYCOOL_STENCIL_7PT && c->stencil != PYCOOL_STENCIL_ISO27 &&
       c->stencil != PYCOOL_STENCIL_4TH)
     return PYCOOL_E_INVALID;
-  // the fourth-order stencil has a per-stage kernel in the FP64 and split-FP32 forms
-  if (c->stencil == PYCOOL_STENCIL_4TH && c->precision == PYCOOL_SPLIT_DD) return PYCOOL_E_INVALID;
+  // the fourth-order stencil: a per-stage kernel in the FP64 and split-FP32
+  // forms, the persistent kernel in the FP64 and split-DD forms (n % 32 == 0)
+  if (c->stencil == PYCOOL_STENCIL_4TH && c->precision == PYCOOL_SPLIT_DD && c->n % 32 != 0)
+    return PYCOOL_E_INVALID;
   // a potential given at run time: FP64 form, 7-point or 27-point stencil
   if (c->model >= kRuntimeModelBase &&
       (c->precision != PYCOOL_FP64 || c->stencil == PYCOOL_STENCIL_4TH))
@@ -497,8 +506,9 @@ cudaError_t encode_persist_maps(const SimDesc& d, const PGeo& g, PParams& p) {
   const cuuint64_t strides[4] = {n * word, n * n * word, n * n * n * word, bstride};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const int cw = (int)(16 / word);
-  const int shapes[6][3] = {{g.tx, 18, d.nf}, {cw, 18, d.nf}, {g.tx, 16, 1},
-                            {g.tx, 1, 1},     {cw, 16, 1},    {cw, 1, 1}};
+  const int H = g.halo;   // halo rows per side of the tile box and of the wrap tiles' row box
+  const int shapes[6][3] = {{g.tx, 16 + 2 * H, d.nf}, {cw, 18, d.nf}, {g.tx, 16, 1},
+                            {g.tx, H, 1},             {cw, 16, 1},    {cw, 1, 1}};
   for (int k = 0; k < 6; ++k) {
     const cuuint32_t box[5] = {(cuuint32_t)shapes[k][0], (cuuint32_t)shapes[k][1], 1,
                                (cuuint32_t)shapes[k][2], 1};
@@ -512,6 +522,9 @@ cudaError_t encode_persist_maps(const SimDesc& d, const PGeo& g, PParams& p) {
 
 cudaError_t launch_persist(const SimDesc& d, const PParams& p, int grid, cudaStream_t s, int* bps) {
   if (d.prec == PREC_SPLIT) return launch_persist_split(d.model, d.stencil, p.g.vx, p, grid, s, bps);
+  if (d.stencil == 13)
+    return d.prec == PREC_DD ? launch_persist_dd_wide(d.model, d.stencil, p.g.vx, p, grid, s, bps)
+                             : launch_persist_fp64_wide(d.model, d.stencil, p.g.vx, p, grid, s, bps);
   if (d.prec == PREC_DD) return launch_persist_dd(d.model, d.stencil, p.g.vx, p, grid, s, bps);
   return launch_persist_fp64(d.model, d.stencil, p.g.vx, p, grid, s, bps);
 }
@@ -796,7 +809,8 @@ static pycool_status setup_persist(pycool_sim* sim) {
   std::vector<int> uoff;
   int l2 = 0;
   CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, sim->device));
-  PGeo g = plan_units(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms, l2, &units, &uoff);
+  PGeo g = plan_units(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms, l2, &units, &uoff,
+                      sim->hdesc.stencil == 13 ? 2 : 1);
   PParams& p = sim->pp;
   std::memset(&p, 0, sizeof(p));
   p.g = g;

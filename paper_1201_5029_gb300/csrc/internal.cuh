@@ -158,6 +158,7 @@ constexpr int kMaxPUnits = 64;             // work units per block
 // the common target (plan_units); each block reads its units from a table.
 struct PGeo {
   int n, vx, tx, tiles_x, ntiles, rc, rw, nunits, G;
+  int halo;   // z-halo planes (and halo rows) per side: 1, or 2 for the 13-point stencil
 };
 
 // Kernel parameters, passed as one __grid_constant__ struct (the tensor maps
@@ -167,6 +168,7 @@ struct PParams {
   // state block) viewed as ONE 5-D tensor (x: n, y: n, z: n, field: N_f,
   // buffer: 4), so that a stage switch uses the same six descriptors;
   // cw = 16 bytes / word; every box spans one buffer and one z-plane:
+  // (with H = 2 halo rows, the 13-point stencil: box 0 is tx x 20 x N_f, box 3 tx x 2 x 1)
   //   0: tx x 18 x N_f  tile with both halo rows, every field (y0 > 0, y0 + 16 < n)
   //   1: cw x 18 x N_f  halo column with its corner cells, every field (same tiles)
   //   2: tx x 16 x 1    tile rows of one field        (tiles at the y wrap)
@@ -192,7 +194,7 @@ struct PParams {
 // The persistent geometry and its unit table (units grouped by block; off has
 // G + 1 entries).
 PGeo plan_units(int n, int word, int nf, int prec, int sms, long long l2_bytes,
-                std::vector<int4>* units, std::vector<int>* off);
+                std::vector<int4>* units, std::vector<int>* off, int halo = 1);
 
 // Launchers (one translation unit per precision).
 cudaError_t launch_sweep_fp64(int model, int stencil, int vx, int tma, const LaunchTable& t, int grid,
@@ -206,5 +208,10 @@ cudaError_t launch_persist_split(int model, int stencil, int vx, const PParams& 
                                  cudaStream_t s, int* bps);
 cudaError_t launch_persist_dd(int model, int stencil, int vx, const PParams& p, int grid,
                               cudaStream_t s, int* bps);
+// the 13-point stencil's instances (FP64 and split-DD)
+cudaError_t launch_persist_fp64_wide(int model, int stencil, int vx, const PParams& p, int grid,
+                                     cudaStream_t s, int* bps);
+cudaError_t launch_persist_dd_wide(int model, int stencil, int vx, const PParams& p, int grid,
+                                   cudaStream_t s, int* bps);
 
 }  // namespace pycool

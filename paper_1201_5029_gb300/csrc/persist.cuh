@@ -53,11 +53,15 @@ static_assert((kPTY + 2) * 16 <= kColFieldBytes, "a dense 18-row column fits a f
 //                               of two layouts: tiles clear of the y wrap get one
 //                               dense box [f][TY+2][CW]; tiles at the wrap get per
 //                               field [f][512 B: low cell | TY rows | high cell]
-template <int NF, int VX, int WORD>
+// H: halo rows (and z-halo planes) per side, 1 for the 7- and 27-point
+// stencils, 2 for the 13-point one (main rows 0 .. H-1 and TY+H .. TY+2H-1 are
+// halo rows; the column layouts are the same for both, a column box being 16
+// bytes wide: two columns of 8-byte values).
+template <int NF, int VX, int WORD, int H = 1>
 struct PLayout {
   static constexpr int TX = 32 * VX;
   static constexpr int CW = 16 / WORD;                                // column box width
-  static constexpr int MAIN = (kPTY + 2) * TX;                        // elements per (array, field)
+  static constexpr int MAIN = (kPTY + 2 * H) * TX;                    // elements per (array, field)
   static constexpr int COLF = kColFieldBytes / WORD;                  // elements per field column
   static constexpr int SLOT = 2 * NF * (MAIN + 2 * COLF);             // elements per slot
   static constexpr int SLOT_BYTES = SLOT * WORD;
@@ -86,11 +90,11 @@ struct PLayout {
 //               block's row of the stage sums (the fold reads them there),
 //               whichever is larger.
 // The FP64 and split-DD forms (bound by arithmetic: ALU) share the FP64 ring.
-template <int PREC, int NF, int VX, int NQ>
+template <int PREC, int NF, int VX, int NQ, int H = 1>
 struct PRing {
   static constexpr bool ALU = PREC != PREC_SPLIT;
-  using LY = PLayout<NF, VX, prec_word(PREC)>;
-  static constexpr int DRIFT_ELEMS = NF * (kPTY + 2) * LY::TX;
+  using LY = PLayout<NF, VX, prec_word(PREC), H>;
+  static constexpr int DRIFT_ELEMS = NF * (kPTY + 2 * H) * LY::TX;
   // FP64 and split-DD: NDRIFT planes in flight, each the drifted phi rows
   // (with the halo rows), the pi of the own rows (re-centred for split-DD) and
   // the halo-column values (up to 3 rows per edge lane)
@@ -118,9 +122,12 @@ struct PRing {
   static_assert(PRE >= 1, "a warp to issue the first planes beside the folds");
 };
 
-template <int MODEL, int PREC, int VX>
+template <int STENCIL> constexpr int halo_of() { return STENCIL == 13 ? 2 : 1; }
+
+template <int MODEL, int PREC, int VX, int STENCIL>
 constexpr size_t persist_smem_bytes() {
-  return (size_t)PRing<PREC, Pot<MODEL>::NF, VX, Slots<Pot<MODEL>::NF, PREC>::NQ>::SMEM_BYTES;
+  return (size_t)PRing<PREC, Pot<MODEL>::NF, VX, Slots<Pot<MODEL>::NF, PREC>::NQ,
+                       halo_of<STENCIL>()>::SMEM_BYTES;
 }
 
 // Shared-memory state of a block, passed to the stage functions.
@@ -209,15 +216,23 @@ __device__ __forceinline__ bool yclear(int4 u, int n) { return u.y > 0 && u.y + 
 // with both halo rows, two columns, all fields at once); a tile at the wrap
 // takes its rows and cells one field at a time.  Every box is in bounds: x0
 // and the column x are multiples of 16 bytes, wrapped rows are separate boxes.
-template <int NF, int VX, int WORD, bool CORNERS>
+//
+// H = 2 (13-point stencil): the tile box and the wrap tiles' halo-row boxes are
+// H rows deeper (their tensor maps are made so for such a simulation), the
+// column boxes unchanged (two columns each, rows y0-1 .. y0+TY, of which the
+// stencil uses the tile rows), and a unit starts H planes below its first
+// output plane.
+template <int NF, int VX, int WORD, bool CORNERS, int H = 1>
 __device__ __forceinline__ void pproduce(const PParams& p, int ib, int4 u, int q,
                                          unsigned char* slot, uint64_t* bar) {
-  using LY = PLayout<NF, VX, WORD>;
+  static_assert(H == 1 || !CORNERS, "corner cells belong to the 27-point stencil");
+  using LY = PLayout<NF, VX, WORD, H>;
   constexpr int TX = LY::TX, CW = LY::CW;
-  constexpr uint32_t kClear = 2u * NF * ((kPTY + 2) * TX * WORD + 2 * (kPTY + 2) * 16);
-  constexpr uint32_t kWrap = 2u * NF * ((kPTY + 2) * TX * WORD + 2 * kPTY * 16 + (CORNERS ? 4 * 16 : 0));
+  constexpr uint32_t kClear = 2u * NF * ((kPTY + 2 * H) * TX * WORD + 2 * (kPTY + 2) * 16);
+  constexpr uint32_t kWrap =
+      2u * NF * ((kPTY + 2 * H) * TX * WORD + 2 * kPTY * 16 + (CORNERS ? 4 * 16 : 0));
   const int n = p.g.n;
-  const int zw = wrapi(u.z - 1 + q, n);
+  const int zw = wrapi(u.z - H + q, n);
   const int xl = (u.x == 0 ? n : u.x) - CW;
   const int xr = (u.x + TX == n) ? 0 : u.x + TX;
   const CUtensorMap* m = p.tm;
@@ -226,13 +241,15 @@ __device__ __forceinline__ void pproduce(const PParams& p, int ib, int4 u, int q
 #pragma unroll
     for (int arr = 0; arr < 2; ++arr) {
       const int bi = arr == 0 ? (ib & 1) : 2 + ((ib >> 1) & 1);   // buffer of phi / pi
-      tma_load_5d(slot + (size_t)LY::main_off(arr, 0) * WORD, &m[0], u.x, u.y - 1, zw, 0, bi, bar);
+      tma_load_5d(slot + (size_t)LY::main_off(arr, 0) * WORD, &m[0], u.x, u.y - H, zw, 0, bi, bar);
       tma_load_5d(slot + (size_t)LY::col_base(arr, 0) * WORD, &m[1], xl, u.y - 1, zw, 0, bi, bar);
       tma_load_5d(slot + (size_t)LY::col_base(arr, 1) * WORD, &m[1], xr, u.y - 1, zw, 0, bi, bar);
     }
     return;
   }
-  const int yl = wrapi(u.y - 1, n), yh = wrapi(u.y + kPTY, n);
+  // the H halo rows each side (rows never split across the wrap: n and the
+  // tile origins are multiples of 16)
+  const int yl = wrapi(u.y - H, n), yh = wrapi(u.y + kPTY, n);
   mbar_expect_tx(bar, kWrap);
 #pragma unroll
   for (int arr = 0; arr < 2; ++arr) {
@@ -240,9 +257,9 @@ __device__ __forceinline__ void pproduce(const PParams& p, int ib, int4 u, int q
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       unsigned char* mb = slot + (size_t)LY::main_off(arr, f) * WORD;
-      tma_load_5d(mb + (size_t)TX * WORD, &m[2], u.x, u.y, zw, f, bi, bar);
+      tma_load_5d(mb + (size_t)H * TX * WORD, &m[2], u.x, u.y, zw, f, bi, bar);
       tma_load_5d(mb, &m[3], u.x, yl, zw, f, bi, bar);
-      tma_load_5d(mb + (size_t)(kPTY + 1) * TX * WORD, &m[3], u.x, yh, zw, f, bi, bar);
+      tma_load_5d(mb + (size_t)(kPTY + H) * TX * WORD, &m[3], u.x, yh, zw, f, bi, bar);
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         unsigned char* cb = slot + (size_t)(LY::col_base(arr, side) + f * LY::COLF) * WORD;
@@ -341,15 +358,18 @@ __device__ __forceinline__ bool drift_alu(const Ctx<MODEL, PREC>& cx, const PSha
   constexpr int NQ = Ctx<MODEL, PREC>::SL::NQ;
   constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
   constexpr int CR = CORNERS ? 3 : 1;
-  using LY = PLayout<NF, VX, 8>;
-  using RG = PRing<PREC, NF, VX, NQ>;
+  constexpr int H = halo_of<STENCIL>();
+  using LY = PLayout<NF, VX, 8, H>;
+  using RG = PRing<PREC, NF, VX, NQ, H>;
   constexpr int TX = LY::TX, CW = LY::CW, NSLOT = RG::NSLOT, NB = RG::NDRIFT;
+  static_assert(H == 1 || CW >= 2, "two halo columns per column box");
   const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
   const int side = lane == 31 ? 1 : 0;
   const bool edge = lane == 0 || lane == 31;
-  const int own = (ly + 1) * TX + lane * VX;
+  const int own = (ly + H) * TX + lane * VX;
   const int s = gg % NSLOT, b = gg % NB;
-  const int hw = (ly - 2 * (int)(gg % (kPWarps / 2)) + kPWarps) % kPWarps;
+  // the 2H halo rows of this plane go to warps 2H j .. 2H j + 2H - 1, j = gg mod (16 / 2H)
+  const int hw = (ly - 2 * H * (int)(gg % (kPWarps / (2 * H))) + kPWarps) % kPWarps;
   const bool ok = mbar_wait(&sm.full[s], (gg / NSLOT) & 1, sm.limit);
   const T* sl = (const T*)(sm.ring + (size_t)s * LY::SLOT_BYTES);
   T* dp = reinterpret_cast<T*>(sm.drift) + (size_t)b * RG::DRIFT_ELEMS;
@@ -362,7 +382,7 @@ __device__ __forceinline__ bool drift_alu(const Ctx<MODEL, PREC>& cx, const PSha
   for (int f = 0; f < NF; ++f) {
     const T* mph = sl + LY::main_off(0, f);
     const T* mpi = sl + LY::main_off(1, f);
-    T* dph = dp + f * (kPTY + 2) * TX;
+    T* dph = dp + f * (kPTY + 2 * H) * TX;
     T a[VX], c[VX];
     vload<T, VX>(&mph[own], a);
     vload<T, VX>(&mpi[own], c);
@@ -375,8 +395,8 @@ __device__ __forceinline__ bool drift_alu(const Ctx<MODEL, PREC>& cx, const PSha
     }
     vstore<T, VX>(&dph[own], a);
     vstore<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], q);
-    if (hw < 2) {   // the two halo rows rotate over the warps, plane by plane
-      const int r = (hw == 0 ? 0 : kPTY + 1) * TX + lane * VX;
+    if (hw < 2 * H) {   // the halo rows rotate over the warps, plane by plane
+      const int r = (hw < H ? hw : kPTY + hw) * TX + lane * VX;
       vload<T, VX>(&mph[r], a);
       vload<T, VX>(&mpi[r], c);
 #pragma unroll
@@ -384,13 +404,24 @@ __device__ __forceinline__ bool drift_alu(const Ctx<MODEL, PREC>& cx, const PSha
       vstore<T, VX>(&dph[r], a);
     }
     if (edge) {
-      const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
-      const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
+      if constexpr (H == 1) {   // the adjacent column, rows ly - 1 .. ly + 1 (CR of them)
+        const T* cph = sl + LY::col_base(0, side) + (side ? 0 : CW - 1);
+        const T* cpi = sl + LY::col_base(1, side) + (side ? 0 : CW - 1);
 #pragma unroll
-      for (int rr = 0; rr < CR; ++rr) {
-        const int r = ly + 1 + rr - (CR - 1) / 2;
-        const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
-        cp[((f * kPTY + ly) * 2 + side) * 3 + rr] = madd(cd, cpi[row], cph[row]);
+        for (int rr = 0; rr < CR; ++rr) {
+          const int r = ly + 1 + rr - (CR - 1) / 2;
+          const int row = clear ? LY::col_dense(f, r) : LY::col_wrap(f, r);
+          cp[((f * kPTY + ly) * 2 + side) * 3 + rr] = madd(cd, cpi[row], cph[row]);
+        }
+      } else {   // both columns of this side (k = 0 adjacent, 1 far), row ly
+        const int row = clear ? LY::col_dense(f, ly + 1) : LY::col_wrap(f, ly + 1);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int cc = side ? k : CW - 1 - k;
+          const T* cph = sl + LY::col_base(0, side) + cc;
+          const T* cpi = sl + LY::col_base(1, side) + cc;
+          cp[((f * kPTY + ly) * 2 + side) * 3 + k] = madd(cd, cpi[row], cph[row]);
+        }
       }
     }
   }
@@ -749,6 +780,231 @@ __device__ __forceinline__ bool stage_dd(const PParams& p, const Ctx<MODEL, PREC
 }
 
 // ---------------------------------------------------------------------------
+// 13-point (fourth-order) stencil, FP64 and split-DD forms: per axis
+// D_axis = (-f(-2) + 16 f(-1) - 30 f(0) + 16 f(+1) - f(+2)) / 12 (Sec. 2.1,
+// after Eq. G).  The planes flow through the drift pipeline of the other
+// stencils with two halo rows, columns and planes each side.  A plane's
+// in-plane part m = w1 (x and y neighbours at 1) + w2 (at 2) + w0 centre (w0
+// for all three axes) is completed along z by a queue of two partial sums: when
+// plane p arrives, plane p - 2 gets its last term w2 f(p) and is output, plane
+// p - 1 gets w1 f(p), and plane p starts as m(p) + w1 f(p - 1) + w2 f(p - 2).
+// The split-DD form sums 12 D with the integer weights (16, -1, -90: exact in
+// float) and multiplies by 1/12 once per site.
+// ---------------------------------------------------------------------------
+template <typename T, int VX>
+__device__ __forceinline__ void wide_shuffles(const T (&ctr)[VX], T (&e)[VX + 4]) {
+  // e[j + 2] = the drifted value at x0 + lane VX + j, j = -2 .. VX + 1
+#pragma unroll
+  for (int j = 0; j < VX; ++j) e[j + 2] = ctr[j];
+  if constexpr (VX == 1) {
+    e[1] = shfl_up1(ctr[0]);
+    e[3] = shfl_down1(ctr[0]);
+    e[0] = shfl_up1(e[1]);     // lane - 2
+    e[4] = shfl_down1(e[3]);   // lane + 2
+  } else {
+    static_assert(VX == 2, "one or two sites per lane");
+    e[0] = shfl_up1(ctr[0]);
+    e[1] = shfl_up1(ctr[1]);
+    e[4] = shfl_down1(ctr[0]);
+    e[5] = shfl_down1(ctr[1]);
+  }
+}
+
+template <int MODEL, int VX, int MODE, int PREC>
+__device__ __forceinline__ bool stage_wide(const PParams& p, const Ctx<MODEL, PREC>& cx,
+                                           const PShared& sm, uint32_t gq, int ib, double* accd) {
+  using C = Ctx<MODEL, PREC>;
+  using T = typename std::conditional<PREC == PREC_DD, dd, double>::type;
+  using SL = typename C::SL;
+  constexpr int NF = C::NF;
+  constexpr int NQ = SL::NQ;
+  constexpr int H = 2;
+  using LY = PLayout<NF, VX, 8, H>;
+  using RG = PRing<PREC, NF, VX, NQ, H>;
+  constexpr int TX = LY::TX;
+  constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD, NB = RG::NDRIFT;
+  constexpr int KGROUP = 8;   // split-DD: output planes per running accumulator
+  static_assert(LEAD + 1 == NSLOT, "the stage issues plane gq + LEAD, then g + NSLOT at plane g");
+  const SimDesc& d = *sm.d;
+  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+  const int n = p.g.n;
+  const size_t S = (size_t)d.S, nn = (size_t)n * n;
+  T* __restrict__ phi_out = (T*)d.phi[(ib & 1) ^ 1];
+  T* __restrict__ pi_out = (T*)d.pi[((ib >> 1) & 1) ^ 1];
+  const int own = (ly + H) * TX + lane * VX;
+  // weights: FP64 the stencil's own; split-DD 12 x them, then 1/12 at the end
+  const T w1 = PREC == PREC_DD ? T(16.0) : T(16.0 / 12.0);
+  const T w2 = PREC == PREC_DD ? T(-1.0) : T(-1.0 / 12.0);
+  const T w0 = PREC == PREC_DD ? T(-90.0) : T(-90.0 / 12.0);
+  const T inv12 = T(1.0 / 12.0);
+  T Mf[NF];   // split-DD: the re-centring of the drifted field
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if constexpr (PREC == PREC_DD) Mf[f] = dd_fma(cx.cdrift, cx.mu_pi[f], cx.mu_phi[f]);
+    else Mf[f] = 0.0;
+  }
+  DDAcc acc[PREC == PREC_DD ? NQ : 1];
+  dd* tot = reinterpret_cast<dd*>(sm.red) + tid;   // split-DD stage sums, tot[q * kPThreads]
+  if constexpr (PREC == PREC_DD) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      acc[i].zero();
+      tot[i * kPThreads] = dd(0.f, 0.f);
+    }
+  }
+  int kg = 0;
+  bool ok = true;
+
+  int pui = 0, puq = 0;
+  for (int l = 0; l < LEAD; ++l) padvance(sm, pui, puq);
+  if (tid == kPThreads - 32 && pui < sm.nunits) {
+    const uint32_t gp = gq + LEAD;
+    pproduce<NF, VX, 8, false, H>(p, ib, sm.units[pui], puq,
+                                  sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                  &sm.full[gp % NSLOT]);
+    sm.issued[gp % NSLOT] = gp + 1;
+  }
+  padvance(sm, pui, puq);
+
+  uint32_t g = gq;
+  if (sm.nunits > 0) ok = drift_alu<MODEL, 13, VX, PREC>(cx, sm, g, sm.units[0], n);
+  for (int i = 0; i < sm.nunits && ok; ++i) {
+    const int4 u = sm.units[i];
+    const int Q = u.w;
+    const size_t o0 = (size_t)u.z * nn + (size_t)(u.y + ly) * n + u.x + lane * VX;
+    // z queue: partial sums of planes p-1, p-2; drifted field and momentum at p-1, p-2
+    T P1[NF][VX], P2[NF][VX], c1[NF][VX], c2[NF][VX], q1[NF][VX], q2[NF][VX];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int jj = 0; jj < VX; ++jj)
+        P1[f][jj] = P2[f][jj] = c1[f][jj] = c2[f][jj] = q1[f][jj] = q2[f][jj] = T(0.0);
+    for (int q = 0; q < Q; ++q, ++g) {
+      if (q + 1 < Q)
+        ok = drift_alu<MODEL, 13, VX, PREC>(cx, sm, g + 1, u, n) && ok;
+      else if (i + 1 < sm.nunits)
+        ok = drift_alu<MODEL, 13, VX, PREC>(cx, sm, g + 1, sm.units[i + 1], n) && ok;
+      ok = mbar_wait(&sm.dbar[g % NB], (g / NB) & 1, sm.limit) && ok;
+      if (!ok) break;
+      if (tid == 32 * (int)((4 * ((g + 1) % (kPWarps / 4)) + 4) % kPWarps) && pui < sm.nunits) {
+        const uint32_t gp = g + NSLOT;   // into slot g % NSLOT, free now
+        pproduce<NF, VX, 8, false, H>(p, ib, sm.units[pui], puq,
+                                      sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                      &sm.full[gp % NSLOT]);
+        sm.issued[gp % NSLOT] = gp + 1;
+      }
+      padvance(sm, pui, puq);
+      const int b = g % NB;
+      const T* dp = reinterpret_cast<const T*>(sm.drift) + (size_t)b * RG::DRIFT_ELEMS;
+      const T* pp = reinterpret_cast<const T*>(sm.drift) + (size_t)NB * RG::DRIFT_ELEMS +
+                    (size_t)b * RG::PI_ELEMS;
+      const T* cp = reinterpret_cast<const T*>(sm.drift) +
+                    (size_t)NB * (RG::DRIFT_ELEMS + RG::PI_ELEMS) + (size_t)b * RG::COL_ELEMS;
+      const bool mid = q >= 2 && q < Q - 2;   // a plane whose sites are output
+      T cur[NF][VX], qn[NF][VX], D[NF][VX];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* dph = dp + f * (kPTY + 2 * H) * TX;
+        vload<T, VX>(&dph[own], cur[f]);
+        vload<T, VX>(&pp[(f * kPTY + ly) * TX + lane * VX], qn[f]);
+        T m[VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) m[jj] = T(0.0);
+        if (mid) {   // q is the same in the whole block: every lane shuffles
+          T e[VX + 4];
+          wide_shuffles<T, VX>(cur[f], e);
+          // the lanes at the tile's x edges take the halo columns ([0] adjacent, [1] far)
+          const T* cl = cp + ((f * kPTY + ly) * 2 + 0) * 3;
+          const T* cr = cp + ((f * kPTY + ly) * 2 + 1) * 3;
+          if (lane == 0) { e[1] = cl[0]; e[0] = cl[1]; }
+          if (lane == 31) { e[VX + 2] = cr[0]; e[VX + 3] = cr[1]; }
+          if constexpr (VX == 1) {
+            if (lane == 1) e[0] = cl[0];
+            if (lane == 30) e[4] = cr[0];
+          }
+          T dn1[VX], up1[VX], dn2[VX], up2[VX];
+          vload<T, VX>(&dph[own - TX], dn1);
+          vload<T, VX>(&dph[own + TX], up1);
+          vload<T, VX>(&dph[own - 2 * TX], dn2);
+          vload<T, VX>(&dph[own + 2 * TX], up2);
+#pragma unroll
+          for (int jj = 0; jj < VX; ++jj) {
+            const T nr = (dn1[jj] + up1[jj]) + (e[jj + 1] + e[jj + 3]);
+            const T fr = (dn2[jj] + up2[jj]) + (e[jj] + e[jj + 4]);
+            m[jj] = madd(w0, cur[f][jj], madd(w2, fr, w1 * nr));
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          D[f][jj] = madd(w2, cur[f][jj], P2[f][jj]);   // plane p - 2: its last term
+          const T np1 = madd(w1, cur[f][jj], P1[f][jj]);
+          P1[f][jj] = madd(w2, c2[f][jj], madd(w1, c1[f][jj], m[jj]));
+          P2[f][jj] = np1;
+        }
+      }
+      if (q >= 4) {  // output plane z0 + q - 4
+        const size_t o = o0 + (size_t)(q - 4) * nn;
+        T pin[NF][VX], phs[NF][VX];
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          T phj[NF], Dj[NF], pmj[NF], pnj[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            if constexpr (PREC == PREC_DD) {
+              phs[f][jj] = c2[f][jj] - Mf[f];   // the re-centred drifted field
+              Dj[f] = D[f][jj] * inv12;
+            } else {
+              phs[f][jj] = c2[f][jj];
+              Dj[f] = D[f][jj];
+            }
+            phj[f] = phs[f][jj];
+            pmj[f] = q2[f][jj];
+          }
+          if constexpr (PREC == PREC_DD) site_dd<MODEL>(cx, MODE, phj, Dj, pmj, pnj, acc);
+          else cx.site(MODE, phj, Dj, pmj, pnj, accd);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pin[f][jj] = pnj[f];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          gstore<T, VX>(phi_out + f * S + o, phs[f]);
+          if (MODE == MODE_SWEEP) gstore<T, VX>(pi_out + f * S + o, pin[f]);
+        }
+        if constexpr (PREC == PREC_DD) {
+          if (++kg == KGROUP) {
+            kg = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < NQ; ++i2) {
+              dd t = tot[i2 * kPThreads];
+              acc[i2].fold(t);
+              tot[i2 * kPThreads] = t;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int jj = 0; jj < VX; ++jj) {
+          c2[f][jj] = c1[f][jj];
+          c1[f][jj] = cur[f][jj];
+          q2[f][jj] = q1[f][jj];
+          q1[f][jj] = qn[f][jj];
+        }
+    }
+  }
+  if constexpr (PREC == PREC_DD) {
+#pragma unroll
+    for (int i2 = 0; i2 < NQ; ++i2) {
+      dd t = tot[i2 * kPThreads];
+      acc[i2].fold(t);
+      tot[i2 * kPThreads] = t;
+    }
+  }
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
 // Split-FP32 form.
 // ---------------------------------------------------------------------------
 // Producer of ring plane gp (one warp): waits until every warp has released
@@ -984,18 +1240,18 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
 // stage starts, the first LEAD planes spread over a few warps.  Every plane of the previous stage has
 // been consumed and released before the block barrier that precedes this
 // call, so the slot needs no wait (the "empty" phases still complete as usual).
-template <int PREC, int NF, int VX, bool CORNERS, int NSLOT>
+template <int PREC, int NF, int VX, bool CORNERS, int NSLOT, int H = 1>
 __device__ __forceinline__ void prefetch_plane(const PParams& p, const PShared& sm, int ib,
                                                uint32_t gq, int l) {
   constexpr int WORD = prec_word(PREC);
-  using LY = PLayout<NF, VX, WORD>;
+  using LY = PLayout<NF, VX, WORD, H>;
   int ui = 0, uq = 0;
   for (int j = 0; j < l; ++j) padvance(sm, ui, uq);
   if (ui >= sm.nunits || (threadIdx.x & 31) != 0) return;
   const uint32_t gp = gq + l;
-  pproduce<NF, VX, WORD, CORNERS>(p, ib, sm.units[ui], uq,
-                                  sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
-                                  &sm.full[gp % NSLOT]);
+  pproduce<NF, VX, WORD, CORNERS, H>(p, ib, sm.units[ui], uq,
+                                     sm.ring + (size_t)(gp % NSLOT) * LY::SLOT_BYTES,
+                                     &sm.full[gp % NSLOT]);
   sm.issued[gp % NSLOT] = gp + 1;
 }
 
@@ -1025,7 +1281,9 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   constexpr int NQ = SL::NQ;
   constexpr int NF = C::NF;
   constexpr bool CORNERS = StencilW<STENCIL>::kCorners;
-  using RG = PRing<PREC, NF, VX, NQ>;
+  constexpr int H = halo_of<STENCIL>();
+  static_assert(STENCIL != 13 || PREC != PREC_SPLIT, "the 13-point stencil: FP64 and split-DD");
+  using RG = PRing<PREC, NF, VX, NQ, H>;
   constexpr int NSLOT = RG::NSLOT, LEAD = RG::LEAD, PRE = RG::PRE;
   static_assert(NQ <= kPWarps, "one warp per reduced quantity");
   static_assert(PREC == PREC_SPLIT || (size_t)kMaxPBlocks * kNQ * 8 <= (size_t)NQ * kPThreads * 8,
@@ -1112,7 +1370,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   // scalar coefficients (the FP64 chain of the merged half-stages)
   {
     for (int l = kPWarps - 1 - warp; l < LEAD; l += kPWarps)   // warp 15 - l issues plane l
-      prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib, gq, l);
+      prefetch_plane<PREC, NF, VX, CORNERS, NSLOT, H>(p, sm, ib, gq, l);
     if (tid == 0) sctxv[0].init(sbv[0], d, K > 0 ? MODE_SWEEP : MODE_FLUSH);
     __syncthreads();
     fault = s_bad != 0;
@@ -1127,7 +1385,15 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     double accd[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) accd[q] = 0.0;
-    if constexpr (PREC == PREC_FP64) {
+    if constexpr (STENCIL == 13) {
+      ok = (mode == MODE_SWEEP) ? stage_wide<MODEL, VX, MODE_SWEEP, PREC>(p, cx, sm, gq, ib, accd)
+                                : stage_wide<MODEL, VX, MODE_FLUSH, PREC>(p, cx, sm, gq, ib, accd);
+      if constexpr (PREC == PREC_DD) {
+        const dd* tot = reinterpret_cast<const dd*>(sm.red) + tid;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) accd[q] = (double)tot[q * kPThreads];
+      }
+    } else if constexpr (PREC == PREC_FP64) {
       ok = (mode == MODE_SWEEP)
                ? stage_fp64<MODEL, STENCIL, VX, MODE_SWEEP>(p, cx, sm, gq, ib, accd)
                : stage_fp64<MODEL, STENCIL, VX, MODE_FLUSH>(p, cx, sm, gq, ib, accd);
@@ -1285,7 +1551,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
       if (pre && l0 < PRE) {
         named_sync(1, kPreThreads);
         for (int l = l0; l < LEAD; l += PRE)
-          prefetch_plane<PREC, NF, VX, CORNERS, NSLOT>(p, sm, ib_next, gq, l);
+          prefetch_plane<PREC, NF, VX, CORNERS, NSLOT, H>(p, sm, ib_next, gq, l);
       }
       // @prefetch-issued
     }
@@ -1359,15 +1625,16 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
         reinterpret_cast<const unsigned long long*>(&sbv[cb])[tid];
 }
 
-// Launch helper (one translation unit per precision).  grid == 0: only set
+// Launch helper (one translation unit per precision and stencil set: WIDE =
+// the 13-point stencil).  grid == 0: only set
 // the kernel's shared-memory attribute and report its occupancy in *bps.
-template <int PREC>
+template <int PREC, bool WIDE = false>
 cudaError_t launch_persist_impl(int model, int stencil, int vx, const PParams& p, int grid,
                                 cudaStream_t s, int* bps) {
 #define PYCOOL_P(M, ST, V)                                                                  \
   if constexpr (V * Pot<M>::NF * prec_word(PREC) <= 16) {                                  \
     if (model == M && stencil == ST && vx == V) {                                           \
-      constexpr size_t smem = persist_smem_bytes<M, PREC, V>();                             \
+      constexpr size_t smem = persist_smem_bytes<M, PREC, V, ST>();                         \
       auto kern = evolve_persist<M, ST, PREC, V>;                                           \
       if (grid == 0) {                                                                      \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -1391,9 +1658,17 @@ cudaError_t launch_persist_impl(int model, int stencil, int vx, const PParams& p
 #define PYCOOL_PM(X, V)                                                                     \
   X(M_FREE, 7, V) X(M_FREE, 27, V) X(M_CHAOTIC2, 7, V) X(M_CHAOTIC2, 27, V)                 \
   X(M_OSCILLON, 7, V) X(M_OSCILLON, 27, V) X(M_QBALL, 7, V) X(M_QBALL, 27, V)
-  PYCOOL_PM(PYCOOL_P, 1)
-  PYCOOL_PM(PYCOOL_P, 2)
-  if constexpr (PREC == PREC_SPLIT) { PYCOOL_PM(PYCOOL_P, 4) }
+#define PYCOOL_PW(X, V) X(M_FREE, 13, V) X(M_CHAOTIC2, 13, V) X(M_OSCILLON, 13, V) X(M_QBALL, 13, V)
+  if constexpr (WIDE) {
+    static_assert(PREC != PREC_SPLIT, "the 13-point stencil: FP64 and split-DD");
+    PYCOOL_PW(PYCOOL_P, 1)
+    PYCOOL_PW(PYCOOL_P, 2)
+  } else {
+    PYCOOL_PM(PYCOOL_P, 1)
+    PYCOOL_PM(PYCOOL_P, 2)
+    if constexpr (PREC == PREC_SPLIT) { PYCOOL_PM(PYCOOL_P, 4) }
+  }
+#undef PYCOOL_PW
 #undef PYCOOL_PM
 #undef PYCOOL_P
   return cudaErrorInvalidValue;
