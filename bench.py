@@ -492,8 +492,9 @@ def next_rows_leg(P, torch, I, w, stream, steps=3):
                       k_eff^2 for `steps` steps, per-mode apply, inverse FFTs);
       observables   : per-site energy density and pressure, and the spectra of
                       every field (FP64 state of the workload);
-      fourth_order  : `steps` time steps with the 13-point stencil (per-stage
-                      kernel), FP64;
+      fourth_order  : `steps` time steps with the 13-point stencil, FP64 (the
+                      persistent kernel when n is a multiple of 32);
+      fourth_order_split_dd : the same in the split-DD form (persistent kernel);
       runtime_model : `steps` time steps of a potential compiled at run time
                       (the workload's own potential as C expressions), FP64.
     Each figure is site-updates/s (n^3 x stages x steps / time) or, for the
@@ -537,6 +538,8 @@ def next_rows_leg(P, torch, I, w, stream, steps=3):
     except Exception as e:  # noqa: BLE001
         out["error"] = f"{type(e).__name__}: {e}"
     for name, make in (("fourth_order", lambda: P.config_from_workload(w, stencil="4th")),
+                       ("fourth_order_split_dd", lambda: P.config_from_workload(
+                           w, stencil="4th", precision="split_dd")),
                        ("runtime_model", lambda: P.make_config(
                            n, w["L"], P.pycool_model_define(*RUNTIME_EXPRESSIONS[w["model"]]),
                            w["params"], w["dt"], order=w["order"], mpl=w["mpl"]))):
@@ -548,7 +551,7 @@ def next_rows_leg(P, torch, I, w, stream, steps=3):
                 ms = _event_ms(torch, stream, lambda: sim.evolve(1), steps)
                 st = sim.sync()
             out[name] = {"value": S * stages / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                         "status": st, "form": "fp64"}
+                         "status": st, "form": "split_dd" if name.endswith("split_dd") else "fp64"}
         except Exception as e:  # noqa: BLE001
             out[name] = {"error": f"{type(e).__name__}: {e}"}
     return out

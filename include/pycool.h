@@ -88,9 +88,10 @@ typedef enum { PYCOOL_FP64 = 0, PYCOOL_SPLIT_FP32 = 1, PYCOOL_SPLIT_DD = 2 } pyc
  *   ISO27 : c = (-128, 14, 3, 1)/30 (isotropic at O(k^4)),
  *   4TH   : the fourth-order stencil Sec. 2.1 mentions (HLATTICE's, not
  *           printed): per axis (-1, 16, -30, 16, -1)/12 over two sites each
- *           way, 13 points; symbol -k^2 + O(k^6).  FP64 and SPLIT_FP32 forms,
- *           per-stage kernel (no persistent kernel, no linearised path);
- *           n >= 4. */
+ *           way, 13 points; symbol -k^2 + O(k^6).  n >= 4.  FP64: the
+ *           persistent kernel when n % 32 == 0, else a per-stage kernel;
+ *           SPLIT_DD: the persistent kernel, n % 32 == 0 (E_INVALID otherwise);
+ *           SPLIT_FP32: the per-stage kernel.  No linearised path. */
 typedef enum {
   PYCOOL_STENCIL_7PT = 7,
   PYCOOL_STENCIL_4TH = 13,
