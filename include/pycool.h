@@ -282,18 +282,22 @@ int64_t pycool_kernel_launches(const pycool_sim* sim);
  * to at most `sms` blocks so that the blocks' modelled work is even; the
  * model depends on whether a stage's traffic fits the device's L2 of
  * l2_bytes (pycool_evolve passes the device's SM count and L2 size).
- *   geo (out, 9 int32): n, vx, tile width, tiles in x, tiles, z-chunks per
- *       tile clear of the periodic y boundary, per tile at it, units, blocks G
+ *   stencil: a pycool_stencil; 4TH (the FP64 and SPLIT_DD forms only) loads
+ *       two halo planes, rows and columns per side, the others one
+ *   geo (out, 10 int32): n, vx, tile width, tiles in x, tiles, z-chunks per
+ *       tile clear of the periodic y boundary, per tile at it, units, blocks G,
+ *       z-halo planes per side H
  *   units (out, 4 int32 per unit, room for cap_units units, may be NULL):
- *       x0, y0, z0, planes + 2 (the planes loaded: the range and its z halo),
+ *       x0, y0, z0, planes + 2 H (the planes loaded: the range and its z halo),
  *       block by block, each block's in processing order
  *   uoff (out, room for cap_blocks + 1, may be NULL): block b's units are
  *       units[uoff[b] .. uoff[b + 1])
  * Every (tile, z) pair of the lattice belongs to exactly one unit.
  * E_INVALID: n not a positive multiple of 32, nf not 1 or 2, precision not a
- * pycool_precision, sms < 1, l2_bytes < 0, or arrays too small for the plan. */
-pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int32_t sms,
-                                  int64_t l2_bytes, int32_t* geo, int32_t* units,
+ * pycool_precision, stencil not a pycool_stencil or 4TH with SPLIT_FP32,
+ * sms < 1, l2_bytes < 0, or arrays too small for the plan. */
+pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int32_t stencil,
+                                  int32_t sms, int64_t l2_bytes, int32_t* geo, int32_t* units,
                                   int32_t cap_units, int32_t* uoff, int32_t cap_blocks);
 
 /* Growth functions of the linearised evolution (Sec. 2.2, Eqs. a-lin, phi-0,

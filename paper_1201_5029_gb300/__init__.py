@@ -121,8 +121,9 @@ def _load():
         "pycool_spectrum": (S, [P, C.c_int32, C.c_int32, P, P, C.c_int32]),
         "pycool_linear_evolve": (S, [C.POINTER(pycool_config), C.c_double, C.c_double, P, P,
                                      C.c_int64, P, P, P, P]),
-        "pycool_persist_plan": (S, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
-                                    C.POINTER(C.c_int32), P, C.c_int32, P, C.c_int32]),
+        "pycool_persist_plan": (S, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_int64, C.POINTER(C.c_int32), P, C.c_int32, P,
+                                    C.c_int32]),
         "pycool_destroy": (None, [P]),
         "pycool_strerror": (C.c_char_p, [S]),
         "pycool_server_create": (S, [C.c_size_t, C.c_int32, C.POINTER(P)]),
@@ -447,20 +448,22 @@ def pycool_spectrum(sim, n: int, which: int, field: int):
     return power, count
 
 
-def pycool_persist_plan(n: int, nf: int, precision: int, sms: int, l2_bytes: int):
+def pycool_persist_plan(n: int, nf: int, precision: int, sms: int, l2_bytes: int,
+                        stencil: int = STENCIL_7PT):
     """The persistent kernel's work plan (host only): (geo, units, uoff) with
-    geo a dict, units an int32 array (units, 4) of (x0, y0, z0, planes + 2)
+    geo a dict, units an int32 array (units, 4) of (x0, y0, z0, planes + 2 H)
     and uoff the int32 block offsets into units."""
     import numpy as np
-    geo = (C.c_int32 * 9)()
-    _check(lib.pycool_persist_plan(n, nf, precision, sms, l2_bytes, geo, None, 0, None, 0),
-           "pycool_persist_plan")
-    keys = ("n", "vx", "tx", "tiles_x", "ntiles", "rc", "rw", "nunits", "G")
+    geo = (C.c_int32 * 10)()
+    _check(lib.pycool_persist_plan(n, nf, precision, stencil, sms, l2_bytes, geo, None, 0, None,
+                                   0), "pycool_persist_plan")
+    keys = ("n", "vx", "tx", "tiles_x", "ntiles", "rc", "rw", "nunits", "G", "halo")
     g = dict(zip(keys, list(geo)))
     units = np.zeros((g["nunits"], 4), dtype=np.int32)
     uoff = np.zeros(g["G"] + 1, dtype=np.int32)
-    _check(lib.pycool_persist_plan(n, nf, precision, sms, l2_bytes, geo, units.ctypes.data,
-                                   g["nunits"], uoff.ctypes.data, g["G"]), "pycool_persist_plan")
+    _check(lib.pycool_persist_plan(n, nf, precision, stencil, sms, l2_bytes, geo,
+                                   units.ctypes.data, g["nunits"], uoff.ctypes.data, g["G"]),
+           "pycool_persist_plan")
     return g, units, uoff
 
 

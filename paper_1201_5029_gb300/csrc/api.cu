@@ -305,21 +305,26 @@ static bool check_plan(const PGeo& g, const std::vector<int4>& units, const std:
 }
 
 PYCOOL_API pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision,
-                                             int32_t sms, int64_t l2_bytes, int32_t* geo,
-                                             int32_t* units, int32_t cap_units, int32_t* uoff,
-                                             int32_t cap_blocks) {
+                                             int32_t stencil, int32_t sms, int64_t l2_bytes,
+                                             int32_t* geo, int32_t* units, int32_t cap_units,
+                                             int32_t* uoff, int32_t cap_blocks) {
   if (n < 32 || n % 32 || (nf != 1 && nf != 2) || sms < 1 || l2_bytes < 0 || !geo ||
       (precision != PYCOOL_FP64 && precision != PYCOOL_SPLIT_FP32 &&
-       precision != PYCOOL_SPLIT_DD))
+       precision != PYCOOL_SPLIT_DD) ||
+      (stencil != PYCOOL_STENCIL_7PT && stencil != PYCOOL_STENCIL_ISO27 &&
+       stencil != PYCOOL_STENCIL_4TH) ||
+      (stencil == PYCOOL_STENCIL_4TH && precision == PYCOOL_SPLIT_FP32))
     return PYCOOL_E_INVALID;
   const int prec = precision == PYCOOL_FP64 ? PREC_FP64
                    : (precision == PYCOOL_SPLIT_DD ? PREC_DD : PREC_SPLIT);
   std::vector<int4> u;
   std::vector<int> off;
-  const PGeo g = plan_units(n, prec_word(prec), nf, prec, sms, l2_bytes, &u, &off);
+  const PGeo g = plan_units(n, prec_word(prec), nf, prec, sms, l2_bytes, &u, &off,
+                            stencil == PYCOOL_STENCIL_4TH ? 2 : 1);
   if (!check_plan(g, u, off)) return PYCOOL_E_INVALID;
-  const int32_t vals[9] = {g.n, g.vx, g.tx, g.tiles_x, g.ntiles, g.rc, g.rw, g.nunits, g.G};
-  for (int i = 0; i < 9; ++i) geo[i] = vals[i];
+  const int32_t vals[10] = {g.n, g.vx, g.tx, g.tiles_x, g.ntiles, g.rc, g.rw, g.nunits, g.G,
+                            g.halo};
+  for (int i = 0; i < 10; ++i) geo[i] = vals[i];
   if (units) {
     if (cap_units < g.nunits) return PYCOOL_E_INVALID;
     for (int i = 0; i < g.nunits; ++i) {
