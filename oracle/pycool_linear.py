@@ -83,9 +83,17 @@ def k_eff2(n: int, stencil: str = "7pt") -> np.ndarray:
     """k_eff^2 of every lattice mode, shape (n, n, n) in numpy FFT order: minus
     the eigenvalue of the stencil D (Eq. D) on the plane wave exp(i k.x),
     summed over the stencil's offsets (no closed form used)."""
-    c = O.stencil_coefficients(stencil)
     th = 2.0 * np.pi * np.fft.fftfreq(n)      # k dx = 2 pi m / n, m in numpy FFT order
     tz, ty, tx = np.meshgrid(th, th, th, indexing="ij")
+    if stencil == "4th":
+        # the 13-point stencil: the centre and, along each axis, the sites at
+        # offsets +-1 and +-2 (each pair gives 2 c cos(offset k dx))
+        sym = np.full((n, n, n), O._FOURTH_CENTRE)
+        for t in (tz, ty, tx):
+            for off, coef in O._FOURTH:
+                sym = sym + 2.0 * coef * np.cos(off * t)
+        return -sym
+    c = O.stencil_coefficients(stencil)
     sym = np.zeros((n, n, n))
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):

@@ -53,12 +53,24 @@ def test_keff2_seven_point_closed_form(n):
     assert np.max(np.abs(k2 - closed)) < 1e-13
 
 
+@pytest.mark.parametrize("n", [6, 8, 16])
+def test_keff2_fourth_order_closed_form(n):
+    """Per axis (30 - 32 cos t + 2 cos 2t)/12 = (1 - cos t)(7 - cos t)/3
+    = 4 sin^2(t/2) + (4/3) sin^4(t/2), t = k dx."""
+    k2 = L.k_eff2(n, "4th")
+    m = np.fft.fftfreq(n) * n
+    s2 = np.sin(np.pi * m / n) ** 2
+    s = 4.0 * s2 + 4.0 / 3.0 * s2 ** 2
+    closed = s[:, None, None] + s[None, :, None] + s[None, None, :]
+    assert np.max(np.abs(k2 - closed)) < 1e-13
+
+
 @pytest.mark.parametrize("mode", [(1, 2, 3), (0, 4, 1), (3, 3, 3)])
 def test_keff2_matches_lattice_laplacian(mode):
     n = 8
     z, y, x = np.meshgrid(*[np.arange(n)] * 3, indexing="ij")
     th = 2 * np.pi * (mode[0] * z + mode[1] * y + mode[2] * x) / n
-    for stencil in ("7pt", "iso27"):
+    for stencil in ("7pt", "iso27", "4th"):
         f = np.cos(th)[None]
         D = O.laplacian(f, stencil)[0]
         k2 = L.k_eff2(n, stencil)[mode]
