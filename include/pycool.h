@@ -321,7 +321,7 @@ pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int3
  * Errors: E_INVALID (bad config or arguments), E_UNSTABLE_DT, E_NOMEM, E_CUDA.
  * The Q-ball's second derivatives need |Phi0| > 0 throughout. */
 /* The distinct k_eff^2 values of an n^3 lattice (host arithmetic only): the
- * symbol of -D (Eq. D, stencil PYCOOL_STENCIL_7PT or _ISO27) on every plane
+ * symbol of -D (Eq. D; stencil PYCOOL_STENCIL_7PT, _ISO27 or _4TH) on every plane
  * wave exp(2 pi i m.x / n), m in numpy's FFT order ([z][y][x], x fastest);
  * values that follow their predecessor in the sorted list within 1e-12
  * (relative to max(1, |v|)) count as one -- a chain of such values joins one
@@ -342,7 +342,8 @@ pycool_status pycool_linear_modes(int32_t n, int32_t stencil, double* values, in
  *   2. forward real-to-complex FFTs of the perturbations (cuFFT), every
  *      field, their k = 0 coefficients cleared;
  *   3. the growth functions T of the distinct k_eff^2 values of the lattice's
- *      stencil (pycool_linear_growth's kernel, background read on the device);
+ *      stencil, any of the three (pycool_linear_growth's kernel, background
+ *      read on the device);
  *   4. every mode (dPhi, dPi)_k <- T[k_eff^2(k)] (dPhi, dPi)_k / n^3, and the
  *      k = 0 coefficient <- the evolved background;
  *   5. inverse FFTs into phi_out, pi_out: background(eta) + perturbations(eta).
@@ -358,8 +359,9 @@ pycool_status pycool_linear_modes(int32_t n, int32_t stencil, double* values, in
  * lattice size and the FFT plans of a (size, N_f, device) are kept for the
  * process's lifetime: the first call for a size pays for them, and calls that
  * share a plan run one at a time.
- * Errors: E_INVALID (bad config, n outside 2..512, bad pointers), E_NOMEM,
- * E_CUDA.  The Q-ball's second derivatives need |Phi0| > 0 throughout. */
+ * Errors: E_INVALID (bad config, n outside 2..512, bad pointers, a physical
+ * time step or a potential given at run time), E_NOMEM, E_CUDA.  The Q-ball's
+ * second derivatives need |Phi0| > 0 throughout. */
 pycool_status pycool_linear_evolve(const pycool_config* cfg, double a0, double pa0,
                                    const double* phi, const double* pi, int64_t steps,
                                    double* phi_out, double* pi_out, double* background,

@@ -269,11 +269,14 @@ bool linear_modes_host(int n, int stencil, std::vector<double>& vals, std::vecto
   const double c7[4] = {-6.0, 1.0, 0.0, 0.0};
   const double c27[4] = {-128.0 / 30.0, 14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0};
   const double* c = stencil == PYCOOL_STENCIL_7PT ? c7 : c27;
-  // one axis: wave number m (numpy FFT order) -> cos(2 pi m / n)
-  std::vector<double> cs(n);
+  const bool fourth = stencil == PYCOOL_STENCIL_4TH;
+  // one axis: wave number m (numpy FFT order) -> cos(2 pi m / n); the
+  // fourth-order stencil's part of one axis, -(2 (16/12) cos t - 2 (1/12) cos 2t)
+  std::vector<double> cs(n), ax4(n);
   for (int m = 0; m < n; ++m) {
     const int mm = m <= (n - 1) / 2 ? m : m - n;
     cs[m] = std::cos(2.0 * M_PI * mm / n);
+    ax4[m] = -(2.0 * (16.0 / 12.0) * cs[m] + 2.0 * (-1.0 / 12.0) * std::cos(4.0 * M_PI * mm / n));
   }
   const size_t S = (size_t)n * n * n;
   std::vector<double> k2(S);
@@ -281,10 +284,17 @@ bool linear_modes_host(int n, int stencil, std::vector<double>& vals, std::vecto
     for (int y = 0; y < n; ++y)
       for (int x = 0; x < n; ++x) {
         const double cz = cs[z], cy = cs[y], cx = cs[x];
-        // sum over the offsets of each class of c_d cos(k.o): products of cosines
-        const double sym = c[0] + 2.0 * c[1] * (cz + cy + cx) +
-                           4.0 * c[2] * (cz * cy + cz * cx + cy * cx) + 8.0 * c[3] * cz * cy * cx;
-        k2[((size_t)z * n + y) * n + x] = -sym;
+        double v;
+        if (fourth) {   // the centre (-90/12) and the two sites each way along every axis
+          v = 90.0 / 12.0 + ax4[z] + ax4[y] + ax4[x];
+        } else {
+          // sum over the offsets of each class of c_d cos(k.o): products of cosines
+          const double sym = c[0] + 2.0 * c[1] * (cz + cy + cx) +
+                             4.0 * c[2] * (cz * cy + cz * cx + cy * cx) +
+                             8.0 * c[3] * cz * cy * cx;
+          v = -sym;
+        }
+        k2[((size_t)z * n + y) * n + x] = v;
       }
   std::vector<double> sorted(k2);
   std::sort(sorted.begin(), sorted.end());
@@ -369,7 +379,8 @@ using namespace pycool;
 extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_modes(
     int32_t n, int32_t stencil, double* values, int64_t cap, int64_t* count, int32_t* index) {
   if (n < 1 || n > 512 || !count || cap < 0 ||
-      (stencil != PYCOOL_STENCIL_7PT && stencil != PYCOOL_STENCIL_ISO27))
+      (stencil != PYCOOL_STENCIL_7PT && stencil != PYCOOL_STENCIL_ISO27 &&
+       stencil != PYCOOL_STENCIL_4TH))
     return PYCOOL_E_INVALID;
   std::vector<double> vals;
   std::vector<int32_t> idx;
@@ -447,7 +458,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
   if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // no second derivatives
   if (!phi || !pi || !phi_out || !pi_out || !background || steps < 0 || !(a0 > 0.0) ||
       !std::isfinite(pa0) || cfg->n < 2 || cfg->n > 512 ||
-      cfg->time_step != PYCOOL_TIME_CONFORMAL || cfg->stencil == PYCOOL_STENCIL_4TH)
+      cfg->time_step != PYCOOL_TIME_CONFORMAL)
     return PYCOOL_E_INVALID;
   {  // the outputs serve as scratch while the inputs are read: no overlap
     const size_t bytes = (size_t)model_nfields(cfg->model) * cfg->n * cfg->n * cfg->n * 8;

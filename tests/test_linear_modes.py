@@ -13,7 +13,7 @@ from oracle import pycool_linear as L  # noqa: E402
 
 
 @pytest.mark.parametrize("n,stencil", [(8, "7pt"), (10, "7pt"), (12, "iso27"), (64, "7pt"),
-                                       (96, "iso27")])
+                                       (96, "iso27"), (8, "4th"), (12, "4th"), (64, "4th")])
 def test_modes_match_oracle_grouping(n, stencil):
     vals, idx = P.pycool_linear_modes(n, stencil)
     ov, oi = L.distinct_k2(L.k_eff2(n, stencil))
