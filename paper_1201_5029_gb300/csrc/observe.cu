@@ -1,7 +1,7 @@
 // Output-interval observables (Sec. 2.1 Eq. rho-pres with the gradient stencil
 // of Eq. G; the spectra of the post-processing, Sec. 2.4), computed at a
 // synchronised state on the device:
-//   energy_fields : rho(x) and P(x) at every site,
+//   energy_fields : rho(x) and P(x) at every site (7-, 27- or 13-point G),
 //       rho = sum_i [pi_i^2/(2 a^6) + G[phi_i]/(2 a^2 dx^2)] + V(phi),
 //       P   = sum_i [pi_i^2/(2 a^6) - G[phi_i]/(6 a^2 dx^2)] - V(phi),
 //       G[phi](x) = 1/2 sum_alpha c_d(alpha) (phi(alpha) - phi(x))^2;
@@ -73,15 +73,34 @@ __global__ void __launch_bounds__(256) energy_fields_kernel(const ObsArgs o) {
       const void* qb = static_cast<const char*>(o.pi) + (size_t)fi * S * prec_word(PREC);
       const double ctr = fluct_at<PREC>(pb, i);
       double G = 0.0;
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int cls = (dz != 0) + (dy != 0) + (dx != 0);
-            if (cls == 0 || c[cls] == 0.0) continue;
-            const int zz = (z + dz + n) % n, yy = (y + dy + n) % n, xx = (x + dx + n) % n;
-            const double diff = fluct_at<PREC>(pb, ((size_t)zz * n + yy) * n + xx) - ctr;
-            G = fma(0.5 * c[cls], diff * diff, G);
-          }
+      if constexpr (STENCIL == 13) {
+        // the 13-point stencil: the sites at +-1 (weight 16/12) and +-2
+        // (weight -1/12) along each axis
+        const double ck[2] = {16.0 / 12.0, -1.0 / 12.0};
+#pragma unroll
+        for (int axis = 0; axis < 3; ++axis)
+#pragma unroll
+          for (int k = 1; k <= 2; ++k)
+#pragma unroll
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+              const int o = sgn * k;
+              const int zz = axis == 0 ? (z + o + 2 * n) % n : z;
+              const int yy = axis == 1 ? (y + o + 2 * n) % n : y;
+              const int xx = axis == 2 ? (x + o + 2 * n) % n : x;
+              const double diff = fluct_at<PREC>(pb, ((size_t)zz * n + yy) * n + xx) - ctr;
+              G = fma(0.5 * ck[k - 1], diff * diff, G);
+            }
+      } else {
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int cls = (dz != 0) + (dy != 0) + (dx != 0);
+              if (cls == 0 || c[cls] == 0.0) continue;
+              const int zz = (z + dz + n) % n, yy = (y + dy + n) % n, xx = (x + dx + n) % n;
+              const double diff = fluct_at<PREC>(pb, ((size_t)zz * n + yy) * n + xx) - ctr;
+              G = fma(0.5 * c[cls], diff * diff, G);
+            }
+      }
       const double q = o.pi0[fi] + fluct_at<PREC>(qb, i);
       kin = fma(q, q, kin);
       grad += G;
@@ -166,14 +185,15 @@ cudaError_t launch_energy_fields(const SimDesc& d, const Background& b, double* 
     energy_fields_kernel<M, ST, PR><<<g, 256, 0, s>>>(o);                               \
     return cudaGetLastError();                                                           \
   }
+#define PYCOOL_OBS_M(M, PR) PYCOOL_OBS(M, 7, PR) PYCOOL_OBS(M, 27, PR) PYCOOL_OBS(M, 13, PR)
 #define PYCOOL_OBS_P(PR)                                                                 \
-  PYCOOL_OBS(M_FREE, 7, PR) PYCOOL_OBS(M_FREE, 27, PR) PYCOOL_OBS(M_CHAOTIC2, 7, PR)     \
-  PYCOOL_OBS(M_CHAOTIC2, 27, PR) PYCOOL_OBS(M_OSCILLON, 7, PR) PYCOOL_OBS(M_OSCILLON, 27, PR) \
-  PYCOOL_OBS(M_QBALL, 7, PR) PYCOOL_OBS(M_QBALL, 27, PR)
+  PYCOOL_OBS_M(M_FREE, PR) PYCOOL_OBS_M(M_CHAOTIC2, PR) PYCOOL_OBS_M(M_OSCILLON, PR)      \
+  PYCOOL_OBS_M(M_QBALL, PR)
   PYCOOL_OBS_P(PREC_FP64)
   PYCOOL_OBS_P(PREC_SPLIT)
   PYCOOL_OBS_P(PREC_DD)
 #undef PYCOOL_OBS_P
+#undef PYCOOL_OBS_M
 #undef PYCOOL_OBS
   return cudaErrorInvalidValue;
 }

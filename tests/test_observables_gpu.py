@@ -21,10 +21,10 @@ from oracle import pycool_observables as B  # noqa: E402
 import gpu_helpers as G  # noqa: E402
 
 CASES = [("preheat128", 4, 32, 5, "7pt"), ("oscillon256", 6, 64, 3, "iso27"),
-         ("qball256", 8, 32, 2, "7pt")]
+         ("qball256", 8, 32, 2, "7pt"), ("preheat128", 4, 32, 4, "4th")]
 
 
-@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+@pytest.fixture(scope="module", params=CASES, ids=[f"{c[0]}-{c[4]}" for c in CASES])
 def case(request):
     name, order, n, steps, stencil = request.param
     w = I.workload(name)
