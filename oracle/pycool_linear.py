@@ -169,11 +169,14 @@ def _stage(cfg, s: LinearState, h: float, k2: np.ndarray, modes: bool = True) ->
 
 
 def step(cfg: O.LatticeConfig, s: LinearState, k2: Optional[np.ndarray] = None) -> None:
-    """One time step d-eta of the background and every perturbation mode."""
+    """One time step d-eta of the background and every perturbation mode;
+    d-eta by the lattice's rule (O.step_size: dt, or dt / a at the step's start
+    for the physical-time step of Sec. 3.1)."""
     if k2 is None:
         k2 = k_eff2(cfg.n, cfg.stencil)
+    deta = O.step_size(cfg, s)
     for w in O.stage_weights(cfg.order):
-        _stage(cfg, s, w * cfg.dt, k2)
+        _stage(cfg, s, w * deta, k2)
 
 
 def evolve(cfg: O.LatticeConfig, s: LinearState, steps: int) -> LinearState:
@@ -217,8 +220,9 @@ def transfer_matrices(cfg: O.LatticeConfig, a0: float, pa0: float, phi0: np.ndar
                     pi0=np.array(pi0, dtype=np.float64), dphi=dphi, dpi=dpi)
     k2 = np.asarray(k2_values, dtype=np.float64)[:, None]
     for _ in range(int(steps)):
+        deta = O.step_size(cfg, s)
         for w in O.stage_weights(cfg.order):
-            _stage(cfg, s, w * cfg.dt, k2)
+            _stage(cfg, s, w * deta, k2)
     T = np.concatenate([np.transpose(s.dphi, (1, 0, 2)), np.transpose(s.dpi, (1, 0, 2))], axis=1)
     return T, s
 

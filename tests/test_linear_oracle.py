@@ -77,9 +77,12 @@ def test_keff2_matches_lattice_laplacian(mode):
         assert np.max(np.abs(D + k2 * f[0])) < 1e-12
 
 
-def test_background_equals_homogeneous_lattice():
+@pytest.mark.parametrize("time_step", ["conformal", "physical"])
+def test_background_equals_homogeneous_lattice(time_step):
+    """The linearised evolution's background is the homogeneous lattice's
+    evolution, in either time variable (physical: d-eta = dt / a per step)."""
     cfg = O.LatticeConfig(n=4, L=5.0, model="chaotic2", params=(1.0, 50.0), dt=0.02, order=4,
-                          mpl=1.0)
+                          mpl=1.0, time_step=time_step)
     phi = np.stack([np.full((4, 4, 4), 0.9), np.full((4, 4, 4), 0.15)])
     pi = np.stack([np.full((4, 4, 4), -0.4), np.full((4, 4, 4), 0.05)])
     st = O.make_state(cfg, phi, pi)
@@ -93,9 +96,9 @@ def test_background_equals_homogeneous_lattice():
         assert abs(ls.pi0[f] - st.pi[f, 0, 0, 0]) < 1e-13 * max(1.0, abs(st.pi[f, 0, 0, 0]))
 
 
-def _lin_vs_full(eps, steps=40, n=12):
+def _lin_vs_full(eps, steps=40, n=12, time_step="conformal"):
     cfg = O.LatticeConfig(n=n, L=6.0, model="chaotic2", params=(1.0, 50.0), dt=0.02, order=4,
-                          mpl=1.0)
+                          mpl=1.0, time_step=time_step)
     rng = np.random.default_rng(5)
     phi = np.stack([1.0 + eps * rng.standard_normal((n, n, n)),
                     0.2 + eps * rng.standard_normal((n, n, n))])
@@ -114,9 +117,10 @@ def _lin_vs_full(eps, steps=40, n=12):
     return err, abs(st.a - ls.a) / st.a
 
 
-def test_linearisation_error_is_second_order():
-    e1, a1 = _lin_vs_full(1e-4)
-    e2, a2 = _lin_vs_full(2e-4)
+@pytest.mark.parametrize("time_step", ["conformal", "physical"])
+def test_linearisation_error_is_second_order(time_step):
+    e1, a1 = _lin_vs_full(1e-4, time_step=time_step)
+    e2, a2 = _lin_vs_full(2e-4, time_step=time_step)
     # perturbation fields: relative difference first order in the amplitude
     assert 1.8 < e2 / e1 < 2.2
     assert e1 < 2e-3
