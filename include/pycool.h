@@ -306,7 +306,8 @@ pycool_status pycool_persist_plan(int32_t n, int32_t nf, int32_t precision, int3
  * discrete Laplacian, dimensionless: -D applied to a plane wave) the
  * 2N_f x 2N_f matrix T with (dPhi_k, dPi_k)(eta) = T (dPhi_k, dPi_k)(0) for
  * every Fourier mode k of the perturbations with that k_eff^2, after `steps`
- * time steps of the configuration's order, d-eta and potential (n and L set
+ * time steps of the configuration's order, time-step rule (dt, or the
+ * physical-time step dt / a at each step's start) and potential (n and L set
  * V_L and dx; precision and stencil are not used).  The equations of the modes
  * are linear, so modes with equal k_eff^2 share one T: the caller reconstructs
  * each mode as T times its initial values.
@@ -359,8 +360,8 @@ pycool_status pycool_linear_modes(int32_t n, int32_t stencil, double* values, in
  * lattice size and the FFT plans of a (size, N_f, device) are kept for the
  * process's lifetime: the first call for a size pays for them, and calls that
  * share a plan run one at a time.
- * Errors: E_INVALID (bad config, n outside 2..512, bad pointers, a physical
- * time step or a potential given at run time), E_NOMEM, E_CUDA.  The Q-ball's
+ * Errors: E_INVALID (bad config, n outside 2..512, bad pointers, or a
+ * potential given at run time), E_NOMEM, E_CUDA.  The Q-ball's
  * second derivatives need |Phi0| > 0 throughout. */
 pycool_status pycool_linear_evolve(const pycool_config* cfg, double a0, double pa0,
                                    const double* phi, const double* pi, int64_t steps,

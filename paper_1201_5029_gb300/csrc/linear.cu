@@ -41,6 +41,7 @@ struct LinArgs {
   double w[kMaxStages];
   int nstages;
   long long steps;
+  int physical;           // d-eta = dt / a at each step's start (Sec. 3.1), else dt
   double dt, dx2inv, VL, inv6VLm2, rho_m0;
   double params[8], derived[4];
 };
@@ -129,15 +130,17 @@ __global__ void __launch_bounds__(128) linear_growth(const LinArgs a) {
     for (int i = 0; i < NF; ++i) p0[i] = p0[i] - a4 * dV[i] * h;
   };
 
-  for (long long s = 0; s < a.steps; ++s)
+  for (long long s = 0; s < a.steps; ++s) {
+    const double deta = a.physical ? a.dt / A : a.dt;   // the background's a at the step's start
     for (int i = 0; i < a.nstages; ++i) {
-      const double h = a.w[i] * a.dt;
+      const double h = a.w[i] * deta;
       h1(0.5 * h);
       h2(0.5 * h);
       h3(h);
       h2(0.5 * h);
       h1(0.5 * h);
     }
+  }
   double* out = a.T + (size_t)k * N2 * N2;
 #pragma unroll
   for (int r = 0; r < N2; ++r)
@@ -402,7 +405,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_gr
   if (v != PYCOOL_OK) return v;
   if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // no second derivatives
   if (!phi0 || !pi0 || !k2 || !T || !background || nk < 1 || steps < 0 || !(a0 > 0.0) ||
-      !std::isfinite(pa0) || cfg->time_step != PYCOOL_TIME_CONFORMAL)
+      !std::isfinite(pa0))
     return PYCOOL_E_INVALID;
   const int nf = model_nfields(cfg->model);
   LinArgs a;
@@ -414,6 +417,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_gr
   a.nstages = stage_table(cfg->order, a.w);
   a.steps = steps;
   a.dt = cfg->dt;
+  a.physical = cfg->time_step == PYCOOL_TIME_PHYSICAL ? 1 : 0;
   const double dx = cfg->L / cfg->n;
   a.dx2inv = 1.0 / (dx * dx);
   a.VL = (double)cfg->n * cfg->n * cfg->n;
@@ -457,8 +461,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
   if (v != PYCOOL_OK) return v;
   if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // no second derivatives
   if (!phi || !pi || !phi_out || !pi_out || !background || steps < 0 || !(a0 > 0.0) ||
-      !std::isfinite(pa0) || cfg->n < 2 || cfg->n > 512 ||
-      cfg->time_step != PYCOOL_TIME_CONFORMAL)
+      !std::isfinite(pa0) || cfg->n < 2 || cfg->n > 512)
     return PYCOOL_E_INVALID;
   {  // the outputs serve as scratch while the inputs are read: no overlap
     const size_t bytes = (size_t)model_nfields(cfg->model) * cfg->n * cfg->n * cfg->n * 8;
@@ -492,6 +495,7 @@ extern "C" __attribute__((visibility("default"))) pycool_status pycool_linear_ev
   a.nstages = stage_table(cfg->order, a.w);
   a.steps = steps;
   a.dt = cfg->dt;
+  a.physical = cfg->time_step == PYCOOL_TIME_PHYSICAL ? 1 : 0;
   const double dx = cfg->L / n;
   a.dx2inv = 1.0 / (dx * dx);
   a.VL = (double)S;

@@ -75,12 +75,16 @@ LATTICE_CASES = [  # workload-like model, n, order, steps, mpl, stencil
     ("qball256", 32, 8, 5, 100.0, "7pt"),
     ("preheat128", 32, 4, 10, 1.0, "4th"),
     ("oscillon256", 24, 2, 10, 100.0, "iso27"),
+    ("preheat128", 32, 4, 10, 1.0, "7pt-physical"),
+    ("oscillon256", 32, 6, 10, 1.0, "7pt-physical"),
 ]
 
 
 @pytest.mark.parametrize("name,n,order,steps,mpl,stencil", LATTICE_CASES,
                          ids=[f"{c[0]}-{c[5]}" for c in LATTICE_CASES])
 def test_linear_evolve_on_device_matches_oracle(name, n, order, steps, mpl, stencil):
+    time_step = "physical" if stencil.endswith("-physical") else "conformal"
+    stencil = stencil.split("-")[0]
     """pycool_linear_evolve (background, FFT, growth functions, per-mode
     apply, inverse FFT, all on the device) against the oracle's direct
     evolution of every mode, element by element on the lattice: the background
@@ -93,14 +97,14 @@ def test_linear_evolve_on_device_matches_oracle(name, n, order, steps, mpl, sten
     w = I.workload(name)
     phi, pi = I.initial_fields(w, n=n)
     cfg = O.LatticeConfig(n=n, L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
-                          order=order, mpl=mpl, stencil=stencil)
+                          order=order, mpl=mpl, stencil=stencil, time_step=time_step)
     pa0 = O.initial_pa(cfg, 1.0, phi, pi)
     ls = L.from_lattice(cfg, phi, pi, 1.0, pa0)
     L.evolve(cfg, ls, steps)
     ophi, opi = L.to_lattice(ls)
 
     gcfg = P.make_config(n=n, L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
-                         order=order, mpl=mpl, stencil=stencil)
+                         order=order, mpl=mpl, stencil=stencil, time_step=time_step)
     dphi, dpi = torch.from_numpy(phi).cuda(), torch.from_numpy(pi).cuda()
     outp, outq = torch.empty_like(dphi), torch.empty_like(dpi)
     a, pa, f0, p0 = P.pycool_linear_evolve(gcfg, 1.0, pa0, dphi, dpi, steps, outp, outq)
@@ -112,6 +116,6 @@ def test_linear_evolve_on_device_matches_oracle(name, n, order, steps, mpl, sten
     levels = 3 * int(np.log2(n))
     for g, o in ((gphi, ophi), (gpi, opi)):
         fe, ft = G.fluct_errors(g, o), G.fluct_tolerances(o, levels, TOL)
-        print(f"\n{name} n={n} {stencil}: perturbation errors {['%.1e' % x for x in fe]} "
+        print(f"\n{name} n={n} {stencil} {time_step}: perturbation errors {['%.1e' % x for x in fe]} "
               f"bounds {['%.1e' % x for x in ft]}")
         assert all(e < t for e, t in zip(fe, ft)), (fe, ft)
