@@ -213,12 +213,13 @@ pycool_status pycool_get_fields(pycool_sim* sim, double* phi, double* pi, int on
  * p[0..7] (the config's params), e.g. "0.5*p[0]*f0*f0 + 0.25*p[1]*f0*f0*f0*f0";
  * the library compiles them with NVRTC into one kernel for this device and
  * returns a model id (>= 16) to put in pycool_config.model.  Such a model
- * runs in the FP64 form with the 7-point or 27-point stencil, one stage as
+ * runs in the FP64 form with any of the three stencils, one stage as
  * three launches (the library's drift, the compiled potential, the library's
  * stencil, kick and sums); params[0] is taken as the mass scale m^2 of the
- * stability check.  Not available with such models: the split forms, the
- * server, the allocation-free sweep, the linearised evolution and
- * pycool_energy_fields (E_INVALID).  The expressions are compiled into the
+ * stability check.  pycool_energy_fields runs the compiled kernel on the
+ * current fields for V.  Not available with such models: the split forms,
+ * the server, the allocation-free sweep and the linearised evolution
+ * (E_INVALID).  The expressions are compiled into the
  * caller's own process; a compile error returns E_INVALID and prints the
  * compiler's log to stderr.  E_CUDA: the compiled kernel could not be
  * loaded (no GPU); E_NOMEM: 64 models already defined in this process.

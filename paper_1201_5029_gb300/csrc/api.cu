@@ -363,10 +363,8 @@ pycool_status validate(const pycool_config* c) {
   // forms, the persistent kernel in the FP64 and split-DD forms (n % 32 == 0)
   if (c->stencil == PYCOOL_STENCIL_4TH && c->precision == PYCOOL_SPLIT_DD && c->n % 32 != 0)
     return PYCOOL_E_INVALID;
-  // a potential given at run time: FP64 form, 7-point or 27-point stencil
-  if (c->model >= kRuntimeModelBase &&
-      (c->precision != PYCOOL_FP64 || c->stencil == PYCOOL_STENCIL_4TH))
-    return PYCOOL_E_INVALID;
+  // a potential given at run time: the FP64 form (any stencil)
+  if (c->model >= kRuntimeModelBase && c->precision != PYCOOL_FP64) return PYCOOL_E_INVALID;
   // its +-2 neighbours wrap once around the lattice at most: n >= 4
   if (c->stencil == PYCOOL_STENCIL_4TH && c->n < 4) return PYCOOL_E_INVALID;
   if (c->time_step != PYCOOL_TIME_CONFORMAL && c->time_step != PYCOOL_TIME_PHYSICAL)
@@ -1260,11 +1258,17 @@ static pycool_status observed_state(pycool_sim* sim, Background* b) {
 PYCOOL_API pycool_status pycool_energy_fields(pycool_sim* sim, double* rho, double* P,
                                               int on_device) {
   if (!sim || !rho || !P) return PYCOOL_E_INVALID;
-  if (sim->cfg.model >= kRuntimeModelBase) return PYCOOL_E_INVALID;   // V is not on the device
   if (sim->poisoned) return PYCOOL_E_STATE;
   Background b;
   pycool_status st = observed_state(sim, &b);
   if (st != PYCOOL_OK) return st;
+  if (sim->cfg.model >= kRuntimeModelBase) {
+    // V at every site of the current fields: the compiled potential kernel
+    // into the simulation's runtime scratch (the FP64 form: plain fields)
+    CK(launch_runtime_potential(sim->hdesc, (const double*)sim->hdesc.phi[b.cur & 1],
+                                sim->stream));
+    sim->launches += 1;
+  }
   const size_t bytes = (size_t)sim->hdesc.S * sizeof(double);
   if (on_device) {
     CK(launch_energy_fields(sim->hdesc, b, rho, P, sim->stream));

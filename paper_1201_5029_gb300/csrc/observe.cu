@@ -4,6 +4,8 @@
 //   energy_fields : rho(x) and P(x) at every site (7-, 27- or 13-point G),
 //       rho = sum_i [pi_i^2/(2 a^6) + G[phi_i]/(2 a^2 dx^2)] + V(phi),
 //       P   = sum_i [pi_i^2/(2 a^6) - G[phi_i]/(6 a^2 dx^2)] - V(phi),
+//       (a potential given at run time: V from its compiled kernel, run on
+//       the same state just before),
 //       G[phi](x) = 1/2 sum_alpha c_d(alpha) (phi(alpha) - phi(x))^2;
 //     the split forms take the differences phi(alpha) - phi(x) from the
 //     fluctuations alone (the background cancels) and V in float64 at
@@ -48,6 +50,7 @@ struct ObsArgs {
   double* rho;
   double* P;
   int n, nf;
+  const double* Vext;   // potentials given at run time: V at every site (the compiled kernel's)
   double a, dx2inv;
   double phi0[kMaxFields], pi0[kMaxFields];   // split forms: background (0 for FP64)
   double params[8], derived[4];
@@ -106,8 +109,13 @@ __global__ void __launch_bounds__(256) energy_fields_kernel(const ObsArgs o) {
       grad += G;
       f[fi] = o.phi0[fi] + ctr;
     }
-    double dV[NF], V;
-    P::eval(pk, f, dV, V);
+    double V;
+    if constexpr (MODEL == M_RUNTIME1 || MODEL == M_RUNTIME2) {
+      V = o.Vext[i];
+    } else {
+      double dV[NF];
+      P::eval(pk, f, dV, V);
+    }
     const double k = kin / (2.0 * a6), g = grad * o.dx2inv / a2;
     o.rho[i] = k + 0.5 * g + V;
     o.P[i] = k - g / 6.0 - V;
@@ -179,6 +187,7 @@ cudaError_t launch_energy_fields(const SimDesc& d, const Background& b, double* 
   ObsArgs o = obs_args(d, b);
   o.rho = rho;
   o.P = P;
+  o.Vext = d.rt_V;
   const unsigned g = grid_for((size_t)d.S);
 #define PYCOOL_OBS(M, ST, PR)                                                            \
   if (d.model == M && d.stencil == ST && d.prec == PR) {                                 \
@@ -192,6 +201,8 @@ cudaError_t launch_energy_fields(const SimDesc& d, const Background& b, double* 
   PYCOOL_OBS_P(PREC_FP64)
   PYCOOL_OBS_P(PREC_SPLIT)
   PYCOOL_OBS_P(PREC_DD)
+  PYCOOL_OBS_M(M_RUNTIME1, PREC_FP64)
+  PYCOOL_OBS_M(M_RUNTIME2, PREC_FP64)
 #undef PYCOOL_OBS_P
 #undef PYCOOL_OBS_M
 #undef PYCOOL_OBS

@@ -17,6 +17,9 @@ namespace pycool {
 // model id (-1 if unknown), and one stage of such a simulation.
 int runtime_model_nfields(int id);
 cudaError_t launch_runtime_stage(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s);
+// The compiled potential of a runtime-model simulation at `phis` (V', V into
+// the simulation's runtime scratch).
+cudaError_t launch_runtime_potential(const SimDesc& d, const double* phis, cudaStream_t s);
 
 struct Layout {
   Geometry geo;

@@ -66,14 +66,30 @@ int runtime_model_nfields(int id) {
   return (i >= 0 && i < (int)g_rt.size()) ? g_rt[i].nf : -1;
 }
 
-// One stage of a runtime-model simulation: drift, the compiled potential, kick.
-cudaError_t launch_runtime_stage(const SimDesc& d, const LaunchTable& t, int grid,
-                                 cudaStream_t s) {
+// The compiled potential of a runtime-model simulation at the fields `phis`
+// (N_f n^3 float64 values): V' into d.rt_dV, V into d.rt_V.
+cudaError_t launch_runtime_potential(const SimDesc& d, const double* phis, cudaStream_t s) {
   cudaKernel_t kern = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_rt_mu);
     if (d.rt_index < 0 || d.rt_index >= (int)g_rt.size()) return cudaErrorInvalidValue;
     kern = g_rt[d.rt_index].kern;
+  }
+  double* dV = d.rt_dV;
+  double* V = d.rt_V;
+  long long S = (long long)d.S;
+  RtParams prm;
+  for (int i = 0; i < 8; ++i) prm.p[i] = d.params[i];
+  void* args[] = {(void*)&phis, (void*)&dV, (void*)&V, (void*)&S, (void*)&prm};
+  return cudaLaunchKernel((const void*)kern, dim3(152 * 8), dim3(256), args, 0, s);
+}
+
+// One stage of a runtime-model simulation: drift, the compiled potential, kick.
+cudaError_t launch_runtime_stage(const SimDesc& d, const LaunchTable& t, int grid,
+                                 cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lk(g_rt_mu);
+    if (d.rt_index < 0 || d.rt_index >= (int)g_rt.size()) return cudaErrorInvalidValue;
   }
   if (grid == 0) return cudaSuccess;
   const unsigned eg = 152 * 8;
@@ -81,22 +97,15 @@ cudaError_t launch_runtime_stage(const SimDesc& d, const LaunchTable& t, int gri
   else rt_drift<M_RUNTIME2><<<eg, kThreads, 0, s>>>(t);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const double* phis = d.rt_phis;
-  double* dV = d.rt_dV;
-  double* V = d.rt_V;
-  long long S = (long long)d.S;
-  RtParams prm;
-  for (int i = 0; i < 8; ++i) prm.p[i] = d.params[i];
-  void* args[] = {(void*)&phis, (void*)&dV, (void*)&V, (void*)&S, (void*)&prm};
-  e = cudaLaunchKernel((const void*)kern, dim3(eg), dim3(256), args, 0, s);
+  e = launch_runtime_potential(d, d.rt_phis, s);
   if (e != cudaSuccess) return e;
 #define PYCOOL_RT(M, ST)                                              \
   if (d.model == M && d.stencil == ST) {                              \
     rt_kick<M, ST><<<grid, kThreads, 0, s>>>(t);                      \
     return cudaGetLastError();                                        \
   }
-  PYCOOL_RT(M_RUNTIME1, 7) PYCOOL_RT(M_RUNTIME1, 27) PYCOOL_RT(M_RUNTIME2, 7)
-  PYCOOL_RT(M_RUNTIME2, 27)
+  PYCOOL_RT(M_RUNTIME1, 7) PYCOOL_RT(M_RUNTIME1, 27) PYCOOL_RT(M_RUNTIME1, 13)
+  PYCOOL_RT(M_RUNTIME2, 7) PYCOOL_RT(M_RUNTIME2, 27) PYCOOL_RT(M_RUNTIME2, 13)
 #undef PYCOOL_RT
   return cudaErrorInvalidValue;
 }

@@ -1847,18 +1847,32 @@ __global__ void __launch_bounds__(kThreads, 2) rt_kick(const LaunchTable tab) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const double* ph = d.rt_phis + (size_t)f * S;
-        double faces = 0.0, edges = 0.0, corners = 0.0;
-        for (int dz = -1; dz <= 1; ++dz)
-          for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-              const int cls = (dz != 0) + (dy != 0) + (dx != 0);
-              if (cls == 0 || (!CORNERS && cls > 1)) continue;
-              const double v = ph[(size_t)wrapi(z + dz, n) * nn + (size_t)wrapi(gy + dy, n) * n +
-                                  wrapi(gx + dx, n)];
-              if (cls == 1) faces += v; else if (cls == 2) edges += v; else corners += v;
-            }
         const double ctr = ph[o];
-        const double D = fma(c3, corners, fma(c2, edges, fma(c1, faces, c0 * ctr)));
+        double D;
+        if constexpr (STENCIL == 13) {
+          // the fourth-order stencil: +-1 and +-2 along each axis
+          auto at = [&](int dz, int dy, int dx) {
+            return ph[(size_t)((z + dz + 2 * n) % n) * nn + (size_t)((gy + dy + 2 * n) % n) * n +
+                      (gx + dx + 2 * n) % n];
+          };
+          const double near = (at(-1, 0, 0) + at(1, 0, 0)) + (at(0, -1, 0) + at(0, 1, 0)) +
+                              (at(0, 0, -1) + at(0, 0, 1));
+          const double far = (at(-2, 0, 0) + at(2, 0, 0)) + (at(0, -2, 0) + at(0, 2, 0)) +
+                             (at(0, 0, -2) + at(0, 0, 2));
+          D = fma(-90.0 / 12.0, ctr, fma(-1.0 / 12.0, far, (16.0 / 12.0) * near));
+        } else {
+          double faces = 0.0, edges = 0.0, corners = 0.0;
+          for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                const int cls = (dz != 0) + (dy != 0) + (dx != 0);
+                if (cls == 0 || (!CORNERS && cls > 1)) continue;
+                const double v = ph[(size_t)wrapi(z + dz, n) * nn +
+                                    (size_t)wrapi(gy + dy, n) * n + wrapi(gx + dx, n)];
+                if (cls == 1) faces += v; else if (cls == 2) edges += v; else corners += v;
+              }
+          D = fma(c3, corners, fma(c2, edges, fma(c1, faces, c0 * ctr)));
+        }
         const double pim = pi_in[(size_t)f * S + o];
         double pin = pim;
         if (mode == MODE_SWEEP) {
