@@ -138,6 +138,7 @@ template <> struct PotDD<M_QBALL> {
   // du = d1 (p1 + d1/2) + d2 (p2 + d2/2),  l = log1p(du/u0)
   //   dV'_i = m2 [ A d_i + K l (p_i + d_i) ],  A = 1 + K + K L0
   //   dV    = m2 [ B du + K l (u0 + du) ],      B = 1 + K L0,  L0 = ln(u0/M^2)
+  // with m2 folded into the constants: mA = m2 A, mB = m2 B, mK = m2 K.
   // direct (background at the origin, V(phi0) = V'(phi0) = 0): the potential
   // of the fluctuation itself, u = |d|^2/2, with a float64 logarithm.
   struct SplitK { dd m2, K, A, B, p1, p2, u0, inv_u0, hp1, hp2; int direct; double lnM2, Kd, m2d; };
@@ -148,9 +149,9 @@ template <> struct PotDD<M_QBALL> {
     k.direct = !(u0 > 1e-30);
     const double L = u0 > 0.0 ? log(u0) - dv[0] : 0.0;
     const double L0 = k.direct ? 0.0 : L;
-    k.m2 = dd(p[0]); k.K = dd(p[1]);
-    k.A = dd(1.0 + p[1] + p[1] * L0);
-    k.B = dd(1.0 + p[1] * L0);
+    k.m2 = dd(p[0]); k.K = dd(p[0] * p[1]);
+    k.A = dd(p[0] * (1.0 + p[1] + p[1] * L0));
+    k.B = dd(p[0] * (1.0 + p[1] * L0));
     k.p1 = dd(b[0]); k.p2 = dd(b[1]);
     k.u0 = dd(u0);
     k.inv_u0 = k.direct ? dd() : dd(1.0 / u0);
@@ -184,14 +185,14 @@ template <> struct PotDD<M_QBALL> {
     const dd du = dd_fma(d[0], dd_fma(0.5f, d[0], k.p1), d[1] * dd_fma(0.5f, d[1], k.p2));
     const dd u = k.u0 + du;
     if (u.hi > 0.f) {
-      const dd Kl = k.K * dd_log1p(du * k.inv_u0);
-      dVd[0] = k.m2 * dd_fma(k.A, d[0], Kl * (k.p1 + d[0]));
-      dVd[1] = k.m2 * dd_fma(k.A, d[1], Kl * (k.p2 + d[1]));
-      dVv = k.m2 * dd_fma(k.B, du, Kl * u);
+      const dd Kl = k.K * dd_log1p(du * k.inv_u0);   // m2 K l
+      dVd[0] = dd_fma(k.A, d[0], Kl * (k.p1 + d[0]));
+      dVd[1] = dd_fma(k.A, d[1], Kl * (k.p2 + d[1]));
+      dVv = dd_fma(k.B, du, Kl * u);
     } else {   // |Phi| = 0 here: V = V' = 0
-      dVd[0] = -(k.m2 * (k.A * k.p1));
-      dVd[1] = -(k.m2 * (k.A * k.p2));
-      dVv = -(k.m2 * (k.B * k.u0));
+      dVd[0] = -(k.A * k.p1);
+      dVd[1] = -(k.A * k.p2);
+      dVv = -(k.B * k.u0);
     }
   }
 };

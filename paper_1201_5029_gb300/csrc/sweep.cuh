@@ -470,7 +470,13 @@ __device__ __forceinline__ void site_dd(const Ctx<MODEL, PREC_DD>& cx, int mode,
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     pin[f] = (mode == MODE_SWEEP) ? dd_fma(cx.kD, D[f], dd_fma(-cx.kV, dVd[f], pim[f])) : pim[f];
-    acc[SL::DPI + f].add(pin[f]);
+    // a sweep's sum of the momentum fluctuations sets the re-centring shift
+    // (exact bookkeeping for any value) and enters sum pi^2 only as
+    // 2 pi0 sum dpi, a term first order in the fluctuations: high parts in
+    // plain float (its rounding is below 1e-12 of sum pi^2); a flush's sum in
+    // double-float
+    if (mode == MODE_SWEEP) acc[SL::DPI + f].add_fast(pin[f].hi);
+    else acc[SL::DPI + f].add(pin[f]);
     acc[SL::DPI2 + f].add_sqr(pin[f]);
     acc[SL::PHID + f].add_prod(phj[f], D[f]);
     if (mode == MODE_SWEEP) {
