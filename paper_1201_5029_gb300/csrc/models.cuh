@@ -150,10 +150,10 @@ template <> struct Pot<M_OSCILLON> {
 // ---------------------------------------------------------------- QBALL
 template <> struct Pot<M_QBALL> {
   static constexpr int NF = 2;
-  struct K { double m2, K1, mK, lnM2; };
+  struct K { double m2, K1, mK, lnM2, m2K1; };
   // dv[0] = ln(M^2), computed once on the host
   __device__ static K prep(const double* p, const double* dv) {
-    return K{p[0], 1.0 + p[1], p[0] * p[1], dv[0]};
+    return K{p[0], 1.0 + p[1], p[0] * p[1], dv[0], p[0] * (1.0 + p[1])};
   }
   // u = (f1^2 + f2^2)/2 ; V' = m2 (1 + K + K ln(u/M^2)) f_i ; V = m2 u (1 + K ln(u/M^2))
   __device__ static void eval(const K& k, const double* f, double* dV, double& V) {
@@ -169,49 +169,52 @@ template <> struct Pot<M_QBALL> {
       dV[0] = 0.0; dV[1] = 0.0; V = 0.0;
     }
   }
-  // eval with the logarithm taken near a reference u_ref (the FP64 sweep's
-  // per-stage value at one site, the same in every block): ln(u) =
-  // ln(u_ref) + log1p(x), x = u / u_ref - 1, log1p(x) by its Taylor series
-  // sum_k (-1)^(k+1) x^k / k -- 5 terms for |x| < 2^-12 (the first omitted
-  // term is below 2^-60 |x|), 11 terms for |x| < 2^-5 (below 2^-60 |x|) --
-  // and the full logarithm farther away.  lref = ln(u_ref) - ln(M^2).
-  __device__ static void eval_near(const K& k, const double* f, double* dV, double& V,
-                                   double inv_uref, double lref) {
-    const double u = 0.5 * fma(f[0], f[0], f[1] * f[1]);
-    if (u > 0.0) {
-      const double x = fma(u, inv_uref, -1.0);
-      const double ax = fabs(x);
-      double l;
-      if (ax < 0.000244140625) {          // 2^-12
-        double q = fma(x, 0.2, -0.25);
-        q = fma(q, x, 1.0 / 3.0);
-        q = fma(q, x, -0.5);
-        q = fma(q, x, 1.0);
-        l = fma(q, x, lref);
-      } else if (ax < 0.03125) {          // 2^-5
-        double q = fma(x, -1.0 / 12.0, 1.0 / 11.0);
-        q = fma(q, x, -0.1);
-        q = fma(q, x, 1.0 / 9.0);
-        q = fma(q, x, -0.125);
-        q = fma(q, x, 1.0 / 7.0);
-        q = fma(q, x, -1.0 / 6.0);
-        q = fma(q, x, 0.2);
-        q = fma(q, x, -0.25);
-        q = fma(q, x, 1.0 / 3.0);
-        q = fma(q, x, -0.5);
-        q = fma(q, x, 1.0);
-        l = fma(q, x, lref);
-      } else {
-        l = log(u) - k.lnM2;
-      }
-      const double kl = k.mK * l;
-      const double fac = fma(k.m2, k.K1, kl);
-      dV[0] = fac * f[0];
-      dV[1] = fac * f[1];
-      V = u * (k.m2 + kl);
-    } else {
-      dV[0] = 0.0; dV[1] = 0.0; V = 0.0;
+  // For the FP64 sweep: from u2 = |Phi|^2 = 2u, the factor fac of V'_i =
+  // fac f_i and twice the potential,
+  //   fac = m2 (1 + K) + m2 K l,   V2 = 2V = u2 (m2 + m2 K l),   l = ln(u/M^2),
+  // with the logarithm taken near a reference u_ref (the sweep's per-stage
+  // value at one site, the same in every block): hinv = 1/(2 u_ref), lref =
+  // ln(u_ref/M^2), x = u/u_ref - 1 = u2 hinv - 1 and l = lref + log1p(x) by its
+  // Taylor series sum_k (-1)^(k+1) x^k / k -- 5 terms for |x| < 2^-12 (the
+  // first omitted term is below 2^-60 |x|), 11 terms for |x| < 2^-5 (below
+  // 2^-60 |x|) -- and the full logarithm farther away or without a reference
+  // (hinv = 0 gives x = -1).  The tiers are chosen on the high word of x as an
+  // integer, and Phi = 0 on the bits of u2 (never negative), so that no
+  // float64 instruction is spent on the tests.
+  __device__ static void fac_near(const K& k, double u2, double hinv, double lref, double& fac,
+                                  double& V2) {
+    if (__double_as_longlong(u2) == 0) {   // Phi = 0: V = V' = 0
+      fac = 0.0;
+      V2 = 0.0;
+      return;
     }
+    const double x = fma(u2, hinv, -1.0);
+    const int hx = __double2hiint(x) & 0x7fffffff;
+    double l;
+    if (hx < 0x3F300000) {            // |x| < 2^-12
+      double q = fma(x, 0.2, -0.25);
+      q = fma(q, x, 1.0 / 3.0);
+      q = fma(q, x, -0.5);
+      q = fma(q, x, 1.0);
+      l = fma(q, x, lref);
+    } else if (hx < 0x3FA00000) {     // |x| < 2^-5
+      double q = fma(x, -1.0 / 12.0, 1.0 / 11.0);
+      q = fma(q, x, -0.1);
+      q = fma(q, x, 1.0 / 9.0);
+      q = fma(q, x, -0.125);
+      q = fma(q, x, 1.0 / 7.0);
+      q = fma(q, x, -1.0 / 6.0);
+      q = fma(q, x, 0.2);
+      q = fma(q, x, -0.25);
+      q = fma(q, x, 1.0 / 3.0);
+      q = fma(q, x, -0.5);
+      q = fma(q, x, 1.0);
+      l = fma(q, x, lref);
+    } else {
+      l = log(0.5 * u2) - k.lnM2;
+    }
+    fac = fma(k.mK, l, k.m2K1);
+    V2 = u2 * fma(k.mK, l, k.m2);
   }
   // du = d1 (p1 + d1/2) + d2 (p2 + d2/2),  l = log1p(du/u0)
   //   dV'_i = m2 [ A d_i + K l (p_i + d_i) ],  A = 1 + K + K L0

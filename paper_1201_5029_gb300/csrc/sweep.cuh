@@ -313,7 +313,7 @@ struct Ctx {
   T shiftK[NF];
   double phi0s[NF], pi0s[NF], V0;  // split forms: background after drift / kick
   typename SplitKOf<MODEL, PREC>::type sk;
-  double q_inv, q_lref;            // FP64 Q-ball: 1/u_ref, ln(u_ref/M^2) (0, 0: no reference)
+  double q_inv, q_lref;            // FP64 Q-ball: 1/(2 u_ref), ln(u_ref/M^2) (0, 0: no reference)
 
   __device__ __forceinline__ void init(const Background& bg, const SimDesc& d, int mode,
                                        double ia_a = -1.0) {
@@ -337,7 +337,7 @@ struct Ctx {
     if constexpr (PREC == PREC_FP64 && MODEL == M_QBALL) {
       const double f0 = flush_shift(d, cur, 0, k.c), f1 = flush_shift(d, cur, 1, k.c);
       const double u = 0.5 * fma(f0, f0, f1 * f1);
-      q_inv = u > 0.0 ? 1.0 / u : 0.0;
+      q_inv = u > 0.0 ? 0.5 / u : 0.0;
       q_lref = u > 0.0 ? log(u) - pk.lnM2 : 0.0;
     }
   }
@@ -413,14 +413,35 @@ struct Ctx {
         ps[SL::PHID + f] = madd(phj[f], D[f], ps[SL::PHID + f]);
       }
       ps[SL::V] = madd(ph2, t, ps[SL::V]);
+    } else if constexpr (PREC == PREC_FP64 && MODEL == M_QBALL) {
+      // V'_i = fac phi_i and 2V from |Phi|^2 (Pot::fac_near: the logarithm
+      // near the stage's reference value); the kicks as pi - (kV fac) phi_i,
+      // and 2V accumulated (halved once, in post_stage)
+      const double u2 = fma(phj[0], phj[0], phj[1] * phj[1]);
+      double fac, V2;
+      P::fac_near(pk, u2, q_inv, q_lref, fac, V2);
+      if (mode == MODE_SWEEP) {
+        const double kf = -kV * fac;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) pin[f] = madd(kD, D[f], madd(kf, phj[f], pim[f]));
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (mode == MODE_SWEEP) {
+          ps[SL::PI2 + f] = madd(pin[f], pin[f], ps[SL::PI2 + f]);
+        } else {
+          pin[f] = pim[f];
+          ps[SL::PI2 + f] = madd(pim[f], pim[f], ps[SL::PI2 + f]);
+          const T dd = phj[f] - shiftK[f];
+          ps[SL::DPHI + f] += dd;
+          ps[SL::DPHI2 + f] = madd(dd, dd, ps[SL::DPHI2 + f]);
+        }
+        ps[SL::PHID + f] = madd(phj[f], D[f], ps[SL::PHID + f]);
+      }
+      ps[SL::V] += V2;
     } else if constexpr (PREC == PREC_FP64) {
       double dV[NF], V;
-      if constexpr (MODEL == M_QBALL) {
-        if (q_inv > 0.0) P::eval_near(pk, phj, dV, V, q_inv, q_lref);
-        else P::eval(pk, phj, dV, V);
-      } else {
-        P::eval(pk, phj, dV, V);
-      }
+      P::eval(pk, phj, dV, V);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         if (mode == MODE_SWEEP) {
@@ -626,8 +647,8 @@ __device__ __forceinline__ void stage_sums(const C& cx, const SumCoef<C::NF>& q,
       fdphi[f] = (mode == MODE_FLUSH) ? sout[SL::DPHI + f] : 0.0;
       fdphi2[f] = (mode == MODE_FLUSH) ? sout[SL::DPHI2 + f] : 0.0;
     }
-    // the chaotic model's FP64 site accumulates 2V (see Ctx::site)
-    sum_V = (MODEL == M_CHAOTIC2) ? 0.5 * sout[SL::V] : sout[SL::V];
+    // the chaotic and Q-ball models' FP64 sites accumulate 2V (see Ctx::site)
+    sum_V = (MODEL == M_CHAOTIC2 || MODEL == M_QBALL) ? 0.5 * sout[SL::V] : sout[SL::V];
   } else {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
