@@ -425,6 +425,10 @@ __device__ __forceinline__ bool drift_alu(const Ctx<MODEL, PREC>& cx, const PSha
       }
     }
   }
+  // The ring slot read above is refilled by a TMA copy (async proxy) once
+  // every warp has arrived: a proxy fence orders this thread's generic reads
+  // of it before that write.
+  fence_proxy_async();
   // one arrival for the warp: __syncwarp orders the lanes' shared-memory
   // writes before lane 0's arrival, whose release makes them visible to the
   // threads whose wait (acquire) observes the completed phase
@@ -1173,6 +1177,7 @@ __device__ __forceinline__ bool stage_split(const PParams& p, const Ctx<MODEL, P
 #pragma unroll
         for (int rr = 0; rr < CR; ++rr) el[f][rr] = madd(cd, cpi[crow[f][rr]], cph[crow[f][rr]]);
       }
+      fence_proxy_async();   // generic reads of the slot before the TMA copy that refills it
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the slot
       if (++s == NSLOT) { s = 0; par ^= 1u; }

@@ -1089,12 +1089,13 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tma(const LaunchTable tab) 
       }
       if (q + 1 < Q) load_col(p + 1);
     }
+    // every thread's generic reads and writes of the slot recycled below come
+    // before the TMA copy (async proxy) that refills it: a proxy fence by each
+    // thread, then the block barrier
+    fence_proxy_async();
     __syncthreads();
     if (s_fault) break;
-    if (tid == 0 && q + 2 < Q) {
-      fence_proxy_async();   // generic writes to the recycled slot before the async copy
-      issue(q + 2);
-    }
+    if (tid == 0 && q + 2 < Q) issue(q + 2);
 
     T so_new[NF][VX], smid_new[NF][VX];   // S_off(p), S_mid(p)
 #pragma unroll
@@ -1425,6 +1426,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_split_pipe(const LaunchTabl
           el[f][rr] = madd(cx.cdrift, colb[s][1][f][side][row], colb[s][0][f][side][row]);
         }
     }
+    // The slot is refilled by a TMA copy (async proxy): this thread's generic
+    // reads of it are ordered before that write by a proxy fence, ahead of the
+    // release (without it, a refill could land under a read still in flight).
+    fence_proxy_async();
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with the slot
 

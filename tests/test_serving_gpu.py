@@ -108,6 +108,59 @@ def test_result_bitwise_identical_alone_and_in_mix(prec):
     assert stats["completed"] == len(mix) + 1
 
 
+def test_twenty_sampled_requests_bitwise_alone_and_in_mix():
+    """20 requests of the serving mix's own stream (its first 16 and its first
+    two of 256^3 and of 384^3: the three models, orders 2..8, both forms
+    alternately, a few steps each): each result, run alone, equals its result
+    in the mix of all 20 bit for bit."""
+    mixd = I.SERVING_MIX
+    pool = I.serving_requests(steps_scale=0.002)          # the 500-request stream
+    reqs = (pool[:16] + [r for r in pool if r["n"] == 256][:2] +
+            [r for r in pool if r["n"] == 384][:2])
+    items = []
+    for i, r in enumerate(reqs):
+        w = I.workload(r["workload"])
+        cfg = P.make_config(r["n"], mixd["L"][w["model"]], w["model"], w["params"],
+                            mixd["dt"][w["model"]], order=r["order"],
+                            precision="fp64" if i % 2 == 0 else "split_fp32", mpl=w["mpl"])
+        ic = P.make_ic(w["background"], w["momentum"], w["noise"])
+        items.append((cfg, ic, r["seed"], r["steps"]))
+    assert len(reqs) == 20 and {r["n"] for r in reqs} >= {32, 64, 128, 256, 384}
+    out, stats = _run(items, budget=40 * GB, slots=32)
+    assert all(s == P.OK for s, _ in out) and stats["completed"] == 20
+    for i, x in enumerate(items):
+        [(st, e)], _ = _run([x], budget=40 * GB)
+        assert st == P.OK
+        assert _obs_tuple(e) == _obs_tuple(out[i][1]), i
+
+
+@pytest.mark.parametrize("name,n,prec", [("preheat32", 256, "split_fp32"),
+                                         ("preheat32", 320, "split_fp32"),
+                                         ("qball256", 256, "fp64")])
+def test_long_z_chunks_are_reproducible_run_to_run(name, n, prec):
+    """Members whose blocks stream 64-plane z-chunks through the 8-slot TMA
+    ring (each slot refilled seven times per sweep): the same request, served
+    three times in turn by one server (each run on the arena the previous one
+    left) and once after a different request, gives the same result bit for
+    bit.  A refill that overtook a read of its slot (a missing proxy fence
+    between the generic reads and the TMA write) changed the last digits of
+    the observables from run to run here."""
+    w, cfg, ic = _req(name, n, 8 if prec == "split_fp32" else 4, prec)
+    x = (cfg, ic, 4321, 2)
+    other = _req("oscillon256", 128, 2)
+    srv = P.pycool_server_create(8 * GB, 4)
+    try:
+        res = []
+        for item in (x, x, x, (other[1], other[2], 7, 1), x):
+            t = P.pycool_server_submit(srv, *item)
+            st, e = P.pycool_server_wait(srv, t, 120.0)
+            assert st == P.OK
+            res.append(_obs_tuple(e))
+    finally:
+        P.pycool_server_destroy(srv)
+    assert res[0] == res[1] == res[2] == res[4]
+
+
 def test_admission_under_a_tight_budget_gives_the_same_results():
     mix = _mix(2000)
     free, _ = _run(mix)
