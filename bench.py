@@ -76,6 +76,7 @@ FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 # A figure counts only while the kernel sources still hash to the value it was
 # taken with; otherwise the line's traffic is reported as null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+NOMINAL_HBM_GBS = 8000.0   # GB300's nominal HBM3e bandwidth (the fractions also quote it)
 
 
 # the sources evolve_persist is compiled from (its translation units and headers)
@@ -268,10 +269,11 @@ def roofline(w, form, s, ms_per_step, hbm, peak_kind):
                "peak_kind": "float64 pipe: 2 DFMA/SM/clk x 152 SMs x 2.07 GHz (GB300 FP64 is "
                             "1/64 of FP32; float64 arithmetic binds this form, not HBM)",
                "flops_per_launch": flops, "achieved_gbs": gbs, "hbm_frac": gbs / hbm,
-               "hbm_peak_gbs": hbm}
+               "hbm_peak_gbs": hbm, "hbm_frac_of_nominal": gbs / NOMINAL_HBM_GBS}
     else:
         out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-               "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+               "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+               "frac_of_nominal": gbs / NOMINAL_HBM_GBS}
         if form == "split_dd":
             out["note"] = ("double-float fluctuations: 8 bytes per value like FP64, arithmetic "
                            "on the FP32 pipe (error-free transformations); the form is held to "
@@ -587,6 +589,7 @@ def time_workload(P, torch, I, name, forms, steps, warmup, flush_buf, stream, ws
         rate = whole_job_rate(ws, S, r["stages"], steps, tot[prec])
         msps = tot[prec] / steps
         out["forms"][prec] = {"value": rate, "unit": UNIT, "ms_per_step": msps,
+                              "steps_per_s": ws * 1e3 / msps,
                               "launches": r["launches"], "status": r["status"],
                               "roofline": roofline(w, prec, r["stages"], msps, hbm, peak_kind)}
     for f, dt in (("split_fp32", "f32 fluctuations + f64 background/sums"),
@@ -754,6 +757,7 @@ def main():
         line = {
             "metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": f64["ms_per_step"],
+            "steps_per_s": f64["steps_per_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded white-noise / spectral initial fluctuations, no dataset)",
             "config": head["config"],
