@@ -293,10 +293,14 @@ def _serving_configs(P, I, reqs, prec):
     return out
 
 
-def _serve(P, items, arrivals, slots=64, budget=96 << 30):
+def _serve(P, items, arrivals, slots=64, budget=96 << 30, persist_min_n=None):
     """Submit each request at its arrival time (None: all at once), wait for all.
-    Returns the server's latency percentiles and the aggregate rate."""
+    Returns the server's latency percentiles and the aggregate rate.
+    persist_min_n: side from which FP64 members run on the persistent kernel
+    (None: the server's default)."""
     srv = P.pycool_server_create(budget, slots)
+    if persist_min_n is not None:
+        P.pycool_server_set_persistent_min_n(srv, persist_min_n)
     t0 = time.perf_counter()
     tickets, work = [], 0
     for i, (cfg, ic, r) in enumerate(items):
@@ -314,17 +318,21 @@ def _serve(P, items, arrivals, slots=64, budget=96 << 30):
                 completed=s["completed"], failed=int(bad), wall_s=wall)
 
 
-def serving_leg(P, I, count, steps_scale, load, other_loads=(), calib_count=100):
+def serving_leg(P, I, count, steps_scale, load, other_loads=(), calib_count=100,
+                persist_min_n=256, compare_per_stage=False):
     """Serving mix (sizes 32..384^3, three models, orders 2..8): a closed-loop
     calibration of the FP64 form's capacity on the first `calib_count`
     requests, then the Poisson arrival stream of all `count` requests at
     `load` x that capacity for each form (the headline), and both forms at
-    each of `other_loads` x that capacity (reported under "by_load")."""
+    each of `other_loads` x that capacity (reported under "by_load").
+    FP64 members of side >= persist_min_n (a multiple of 32; 0: none) run on
+    the persistent kernel; compare_per_stage adds the FP64 replay of the same
+    arrival stream with every member on the per-stage kernels."""
     reqs = I.serving_requests(count=count, steps_scale=steps_scale)
     work_of = lambda r: r["n"] ** 3 * r["steps"] * P.pycool_stages_per_step(r["order"])  # noqa
     mean_work = sum(work_of(r) for r in reqs) / len(reqs)
     items64 = _serving_configs(P, I, reqs, "fp64")
-    calib = _serve(P, items64[:calib_count], None)
+    calib = _serve(P, items64[:calib_count], None, persist_min_n=persist_min_n)
     capacity = calib["site_updates_per_s"] / mean_work          # requests/s
     rate = load * capacity
     arr = I.poisson_arrivals(rate, len(reqs), I.SERVING_MIX["arrival_seed"])
@@ -333,15 +341,20 @@ def serving_leg(P, I, count, steps_scale, load, other_loads=(), calib_count=100)
            "capacity_calibration": f"closed loop, first {min(calib_count, len(reqs))} requests, "
                                    "FP64",
            "mean_site_stages_per_request": mean_work,
+           "persistent_min_n": persist_min_n,
            "latency": "submit (Poisson arrival) -> observables read back on the host"}
     items32 = _serving_configs(P, I, reqs, "split_fp32")
     for prec, items in (("fp64", items64), ("split_fp32", items32)):
-        out[prec] = _serve(P, items, arr)
+        out[prec] = _serve(P, items, arr, persist_min_n=persist_min_n)
+    if compare_per_stage:
+        out["fp64_all_per_stage"] = _serve(P, items64, arr, persist_min_n=0)
     by_load = {}
     keep = ("p50_s", "p99_s", "site_updates_per_s", "completed", "failed")
     for lo in other_loads:
         arr_lo = I.poisson_arrivals(lo * capacity, len(reqs), I.SERVING_MIX["arrival_seed"])
-        by_load[str(lo)] = {prec: {k: v for k, v in _serve(P, items, arr_lo).items() if k in keep}
+        by_load[str(lo)] = {prec: {k: v for k, v in
+                                   _serve(P, items, arr_lo, persist_min_n=persist_min_n).items()
+                                   if k in keep}
                             for prec, items in (("fp64", items64), ("split_fp32", items32))}
     if by_load:
         out["by_load"] = by_load
@@ -629,6 +642,11 @@ def main():
     ap.add_argument("--serving-load", type=float, default=0.7)
     ap.add_argument("--serving-other-loads", default="",
                     help="further offered loads (comma list), both forms, under by_load")
+    ap.add_argument("--serving-persist-min-n", type=int, default=256,
+                    help="FP64 serving members of this side and above (a multiple of 32) run "
+                         "on the persistent kernel; 0: none")
+    ap.add_argument("--serving-compare-per-stage", action="store_true",
+                    help="also replay the FP64 stream with every member on the per-stage kernels")
     ap.add_argument("--forms", default="fp64,split_fp32,split_dd",
                     help="comma list of forms to time (profiling a single kernel)")
     args = ap.parse_args()
@@ -726,7 +744,9 @@ def main():
     if rank == 0 and not args.no_serving:
         serving = serving_leg(P, I, args.serving_requests, args.serving_steps_scale,
                               args.serving_load,
-                              [float(x) for x in args.serving_other_loads.split(",") if x])
+                              [float(x) for x in args.serving_other_loads.split(",") if x],
+                              persist_min_n=args.serving_persist_min_n,
+                              compare_per_stage=args.serving_compare_per_stage)
 
     # the linearised evolution's growth functions on the same lattice (Sec. 2.2):
     # a side measurement, never allowed to take the main line down

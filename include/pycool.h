@@ -438,6 +438,19 @@ pycool_status pycool_server_stats(pycool_server* srv, double* p50_s, double* p99
  * request has finished already (collect it with wait).  Thread-safe. */
 pycool_status pycool_server_cancel(pycool_server* srv, uint64_t ticket);
 
+/* Which requests run on the persistent kernel (the one-launch-per-evolve
+ * stepper of pycool_evolve, Sec. 2.3) instead of the per-stage launches they
+ * share with the other members of their group: FP64 requests whose side n is a
+ * multiple of 32 and at least min_n (0: none; default 256).  Such a member gets
+ * one cooperative launch of up to one graph's worth of stage sweeps (8) at
+ * each graph boundary, alone on the GPU: a cooperative grid holds every SM.
+ * Its launches leave the stage boundary pending, as the per-stage launches do;
+ * its last launch ends with the flush.  Applies to requests admitted after the
+ * call; the path a request takes depends on its config and min_n only, so
+ * results stay identical alone and in a mix.  E_INVALID unless min_n is 0 or a
+ * multiple of 32.  Thread-safe. */
+pycool_status pycool_server_set_persistent_min_n(pycool_server* srv, int32_t min_n);
+
 /* Stop the server thread and release every resident simulation and the arena. */
 void pycool_server_destroy(pycool_server* srv);
 

@@ -134,6 +134,7 @@ def _load():
                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "pycool_server_destroy": (None, [P]),
         "pycool_server_cancel": (S, [P, C.c_uint64]),
+        "pycool_server_set_persistent_min_n": (S, [P, C.c_int32]),
         "pycool_debug_fail_alloc": (S, [C.c_int32]),
         "pycool_debug_barrier_stall": (S, [P, C.c_int64]),
         "pycool_noalloc_max_blocks": (C.c_size_t, []),
@@ -513,6 +514,13 @@ def pycool_server_stats(srv) -> dict:
 
 def pycool_server_destroy(srv) -> None:
     lib.pycool_server_destroy(srv)
+
+
+def pycool_server_set_persistent_min_n(srv, min_n: int) -> None:
+    """FP64 requests with side n % 32 == 0 and n >= min_n (0: none) run on the
+    persistent kernel; applies to requests admitted after the call."""
+    _check(lib.pycool_server_set_persistent_min_n(srv, int(min_n)),
+           "pycool_server_set_persistent_min_n")
 
 
 def pycool_server_cancel(srv, ticket: int) -> int:

@@ -802,43 +802,66 @@ static pycool_status build_graph(pycool_sim* sim) {
   return PYCOOL_OK;
 }
 
-// Persistent path: geometry for this device, tensor maps, occupancy check.
-// Leaves sim->persist false (per-stage launches) if one block per SM does not fit.
-static pycool_status setup_persist(pycool_sim* sim) {
-  int sms = 0;
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
-  const int word = prec_word(sim->hdesc.prec);
+// Persistent path for a state and workspace laid out by sim_layout(): the
+// geometry and work plan for this device (uploaded into the workspace on
+// stream st), the tensor maps and the occupancy check.  *fits is false if one
+// block per SM does not fit (the caller then runs the per-stage kernels).
+pycool_status pycool::persist_setup(const pycool_config& cfg, const SimDesc& hd, const Layout& L,
+                                    char* state, char* ws, cudaStream_t st, PParams& p,
+                                    bool* fits) {
+#define PCK(call)                                                    \
+  do {                                                               \
+    cudaError_t e__ = (call);                                        \
+    if (e__ != cudaSuccess) return cuda_fail(nullptr, e__, #call);   \
+  } while (0)
+  *fits = false;
+  int dev = 0, sms = 0, l2 = 0;
+  PCK(cudaGetDevice(&dev));
+  PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PCK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+  if (!L.off_prows || !L.off_punits) return PYCOOL_E_INVALID;   // not a persistent layout
   std::vector<int4> units;
   std::vector<int> uoff;
-  int l2 = 0;
-  CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, sim->device));
-  PGeo g = plan_units(sim->cfg.n, word, sim->nf, sim->hdesc.prec, sms, l2, &units, &uoff,
-                      sim->hdesc.stencil == 13 ? 2 : 1);
-  PParams& p = sim->pp;
+  const PGeo g = plan_units(cfg.n, prec_word(hd.prec), model_nfields(cfg.model), hd.prec, sms,
+                            l2, &units, &uoff, hd.stencil == 13 ? 2 : 1);
   std::memset(&p, 0, sizeof(p));
   p.g = g;
-  int4* d_units = (int4*)(sim->ws + sim->L.off_punits);
-  int* d_uoff = (int*)(sim->ws + sim->L.off_punits +
+  int4* d_units = (int4*)(ws + L.off_punits);
+  int* d_uoff = (int*)(ws + L.off_punits +
                        align256((size_t)kMaxPBlocks * kMaxPUnits * sizeof(int4)));
   if (units.size() > (size_t)kMaxPBlocks * kMaxPUnits || uoff.size() > (size_t)kMaxPBlocks + 1 ||
       !check_plan(g, units, uoff))
     return PYCOOL_E_INVALID;
-  CK(cudaMemcpy(d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_uoff, uoff.data(), uoff.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PCK(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                      st));
+  PCK(cudaMemcpyAsync(d_uoff, uoff.data(), uoff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  PCK(cudaStreamSynchronize(st));   // the host vectors go out of scope below
   p.units = d_units;
   p.uoff = d_uoff;
-  CK(encode_persist_maps(sim->hdesc, g, p));
-  p.d = sim->d_desc;
-  p.bg = sim->d_bg;
-  p.bar = (unsigned long long*)(sim->ws + sim->L.off_ticket + 64);
+  PCK(encode_persist_maps(hd, g, p));
+  p.d = (const SimDesc*)(state + L.off_desc);
+  p.bg = (Background*)(state + L.off_bg);
+  p.bar = (unsigned long long*)(ws + L.off_ticket + 64);
   p.bar_base = 0;
-  p.rows = sim->ws + sim->L.off_prows;
-  p.fault = sim->hdesc.fault;
+  p.rows = ws + L.off_prows;
+  p.fault = hd.fault;
   p.wait_limit = kWaitLimit;
   p.bar_extra = 0;
+  p.flush = 1;
   int bps = 0;
-  CK(launch_persist(sim->hdesc, p, 0, sim->stream, &bps));
-  sim->persist = bps >= 1 && g.G <= bps * sms;
+  PCK(launch_persist(hd, p, 0, st, &bps));
+  *fits = bps >= 1 && g.G <= bps * sms;
+  return PYCOOL_OK;
+#undef PCK
+}
+
+static pycool_status setup_persist(pycool_sim* sim) {
+  bool fits = false;
+  const pycool_status st = persist_setup(sim->cfg, sim->hdesc, sim->L, sim->state, sim->ws,
+                                         sim->stream, sim->pp, &fits);
+  if (st == PYCOOL_E_CUDA) sim->poisoned = true;
+  if (st != PYCOOL_OK) return st;
+  sim->persist = fits;
   return PYCOOL_OK;
 }
 

@@ -185,7 +185,9 @@ struct PParams {
   const int* uoff;         // block b's units are units[uoff[b] .. uoff[b + 1])
   int32_t* fault;
   PGeo g;
-  long long nsweeps;       // stage sweeps of this launch (then one flush)
+  long long nsweeps;       // stage sweeps of this launch (then one flush if flush != 0)
+  int flush;               // 1: end with the flush; 0 (nsweeps >= 1, FP64 form only): end
+                           //    after the last sweep, the stage boundary pending
   long long wait_limit;    // clocks after which a device-side wait gives up
   unsigned long long bar_extra;  // added to every grid-barrier target: 0, or 1 to
                                  // make the first barrier unreachable (fault test)

@@ -1369,6 +1369,11 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
   for (int i = 0; i < sm.nunits; ++i) np += (uint32_t)s_units[i].w;
   uint32_t gq = 0;
   const long long K = p.nsweeps;
+  // the launch's last pass: the flush (k == K), or, for a launch that leaves
+  // the merged stage boundary pending for the next launch (p.flush == 0), the
+  // last stage sweep; the Background written back is then a sweep's, as after
+  // a per-stage launch
+  const long long KL = p.flush ? K : K - 1;
   bool fault = false;
   int ib = sbv[0].cur;
   // stage 0: its first planes are in flight while one thread derives the
@@ -1380,7 +1385,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     __syncthreads();
     fault = s_bad != 0;
   }
-  for (long long k = 0; k <= K && !fault; ++k) {
+  for (long long k = 0; k <= KL && !fault; ++k) {
     const int mode = (k < K) ? MODE_SWEEP : MODE_FLUSH;
     const C cx = sctxv[cb];
     // @stage-start
@@ -1488,7 +1493,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     // the next stage's PreCoef (it starts from a = k.a, h_prev = k.h)
     if (warp == kPWarps - 2 && lane == 0) {
       s_sc = sum_coef<MODEL, PREC>(sctxv[cb], d);
-      if (k < K) {
+      if (k < KL) {
         const int mn = k + 1 < K ? MODE_SWEEP : MODE_FLUSH;
         const int sn = sbv[cb].stage + 1 < d.nstages ? sbv[cb].stage + 1 : 0;
         const Coef& kc = sctxv[cb].k;
@@ -1510,7 +1515,7 @@ __global__ void __launch_bounds__(kPThreads, 1) evolve_persist(const __grid_cons
     //     planes, every PRE-th plane each (its buffers are known: a sweep
     //     swaps phi and pi, a flush swaps phi) ----
     const int ib_next = ib ^ (mode == MODE_SWEEP ? 3 : 1);
-    const bool pre = k < K;
+    const bool pre = k < KL;
     constexpr int kPreThreads = (1 + PRE) * 32;
     using FT = typename std::conditional<PREC != PREC_SPLIT, double, float2>::type;
     // every block's row arrives by one bulk copy into the (now free) reduction

@@ -43,6 +43,10 @@ Layout layout_for(const pycool_config& c);
 Layout sim_layout(const pycool_config& c);
 cudaError_t encode_persist_maps(const SimDesc& d, const PGeo& g, PParams& p);
 cudaError_t launch_persist(const SimDesc& d, const PParams& p, int grid, cudaStream_t s, int* bps);
+// The persistent kernel's parameters for a state and workspace laid out by
+// sim_layout() (api.cu); *fits: one block per SM fits.
+pycool_status persist_setup(const pycool_config& cfg, const SimDesc& hd, const Layout& L,
+                            char* state, char* ws, cudaStream_t st, PParams& p, bool* fits);
 pycool_status validate(const pycool_config* c);
 void fill_desc(SimDesc& d, const pycool_config& c, const Layout& L, char* state, char* ws);
 cudaError_t launch_sweep(const SimDesc& d, const LaunchTable& t, int grid, cudaStream_t s);

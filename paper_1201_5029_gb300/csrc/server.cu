@@ -15,12 +15,23 @@
 // a CUDA graph on its own stream, rebuilt only when its membership changes.
 // Finished members (record idle after their flush) are retired at graph
 // boundaries: their observables are read, the latency from submission is
-// recorded and their memory returns to the arena.  Per-member arithmetic and
-// reduction order depend only on that member's lattice, so a result is
-// bit-identical whether the simulation ran alone or in a mix.
+// recorded and their memory returns to the arena.
+//
+// Large FP64 members (side a multiple of 32, at least persist_min_n, 256 by
+// default) run on the persistent kernel instead: between the groups' graph
+// replays, each gets one cooperative launch of as many stage sweeps as a graph
+// holds, alone on the GPU (a cooperative grid holds every SM, so it never
+// shares the device with another launch).  The launch leaves the merged stage
+// boundary pending, as a per-stage launch does; the member's last launch ends
+// with the flush.  Which path a member takes depends on its own config only.
+//
+// Per-member arithmetic and reduction order depend only on that member's
+// lattice, so a result is bit-identical whether the simulation ran alone or in
+// a mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -45,6 +56,9 @@
 using namespace pycool;
 
 namespace {
+
+// default side from which FP64 members run on the persistent kernel
+constexpr int kPersistMinN = 256;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
@@ -185,7 +199,10 @@ struct Member {
   SimDesc hdesc;
   char* state = nullptr;
   char* ws = nullptr;
-  int group = -1;
+  int group = -1;              // per-stage members: their group; persistent members: -1
+  bool persist = false;        // advanced by the persistent kernel, alone on the GPU
+  PParams pp;                  // its launch parameters (plan, tensor maps, barrier count)
+  long long sweeps_left = 0;   // stage sweeps still to run (persistent members)
 };
 
 struct Group {
@@ -201,6 +218,9 @@ struct Group {
 struct pycool_server {
   int max_slots = 0;
   int stages_per_graph = 8;
+  // FP64 requests whose side is a multiple of 32 and at least this run on the
+  // persistent kernel (0: none); read at admission
+  std::atomic<int> persist_min_n{kPersistMinN};
   Arena arena;
   int device = 0;
   cudaStream_t setup = nullptr, capture = nullptr;
@@ -223,8 +243,25 @@ struct pycool_server {
 
 namespace {
 
-size_t footprint(const pycool_config& c) {
-  const Layout L = layout_for(c);
+// A request's layout: the persistent kernel's (sim_layout) for FP64 members on
+// a lattice it takes (side a multiple of 32, at least persist_min_n), else the
+// per-stage kernels'.
+Layout member_layout(const pycool_server* s, const pycool_config& c, bool* persist) {
+  const int mn = s->persist_min_n.load();
+  if (mn > 0 && c.precision == PYCOOL_FP64 && c.n >= mn && c.n % 32 == 0) {
+    const Layout L = sim_layout(c);
+    if (L.off_prows) {
+      *persist = true;
+      return L;
+    }
+  }
+  *persist = false;
+  return layout_for(c);
+}
+
+size_t footprint(const pycool_server* s, const pycool_config& c) {
+  bool persist = false;
+  const Layout L = member_layout(s, c, &persist);
   return round256(L.state_bytes) + round256(L.ws_bytes);
 }
 
@@ -255,7 +292,8 @@ int group_for(pycool_server* s, const SimDesc& d) {
 pycool_status admit(pycool_server* s, const Request& r, int slot) {
   auto m = std::make_unique<Member>();
   m->req = r;
-  m->L = layout_for(r.cfg);
+  bool persist = false;
+  m->L = member_layout(s, r.cfg, &persist);
   m->state = s->arena.alloc(m->L.state_bytes);
   if (!m->state) return PYCOOL_E_NOMEM;
   m->ws = s->arena.alloc(m->L.ws_bytes);
@@ -292,6 +330,20 @@ pycool_status admit(pycool_server* s, const Request& r, int slot) {
   t.cta_offset[1] = m->L.geo.ncta;
   t.desc[0] = (const SimDesc*)(m->state + m->L.off_desc);
   SCK(launch_sweep(d, t, m->L.geo.ncta, st));
+  if (persist) {   // the plan for this device, the tensor maps, the occupancy check
+    bool fits = false;
+    const pycool_status ps =
+        persist_setup(r.cfg, m->hdesc, m->L, m->state, m->ws, st, m->pp, &fits);
+    if (ps != PYCOOL_OK) return ps;
+    persist = fits;   // else the per-stage kernels (the layout holds theirs too)
+  }
+  if (persist) {
+    SCK(cudaStreamSynchronize(st));
+    m->persist = true;
+    m->sweeps_left = (long long)r.steps * d.nstages;
+    s->slots[slot] = std::move(m);
+    return PYCOOL_OK;
+  }
   SCK(launch_arm((Background*)(m->state + m->L.off_bg), (long long)r.steps * d.nstages, st));
   SCK(cudaStreamSynchronize(st));
   const int g = group_for(s, d);
@@ -362,9 +414,11 @@ void retire(pycool_server* s, int slot, const Background& b, int32_t fault, bool
     }
   }
   s->cv_done.notify_all();
-  Group& G = s->groups[m.group];
-  G.members.erase(std::find(G.members.begin(), G.members.end(), slot));
-  G.dirty = true;
+  if (m.group >= 0) {
+    Group& G = s->groups[m.group];
+    G.members.erase(std::find(G.members.begin(), G.members.end(), slot));
+    G.dirty = true;
+  }
   s->arena.free(m.ws, m.L.ws_bytes);
   s->arena.free(m.state, m.L.state_bytes);
   s->slots[slot].reset();
@@ -445,13 +499,43 @@ void server_loop(pycool_server* s) {
       }
       any = true;
     }
-    if (!any) continue;
+    bool persistent = false;
+    for (const auto& p : s->slots) persistent = persistent || (p && p->persist);
+    if (!any && !persistent) continue;
     for (Group& G : s->groups) {
       if (G.members.empty()) continue;
       if (cudaStreamSynchronize(G.stream) != cudaSuccess) { fail_all(s, PYCOOL_E_CUDA); return; }
     }
-    // 3. retire finished members (record idle after their flush, or stopped)
-    //    and cancelled ones (every launch of their group has completed here)
+    // 2b. persistent members, one after another, each alone on the GPU (every
+    //     group's launches have completed): one cooperative launch of up to a
+    //     graph's worth of stage sweeps; the last launch of a member ends with
+    //     the flush, the others leave the stage boundary pending
+    if (persistent) {
+      for (int slot = 0; slot < s->max_slots; ++slot) {
+        Member* m = s->slots[slot].get();
+        if (!m || !m->persist) continue;
+        if (m->sweeps_left > 0) {
+          const long long k = std::min<long long>(m->sweeps_left, s->stages_per_graph);
+          m->pp.nsweeps = k;
+          m->pp.flush = k == m->sweeps_left ? 1 : 0;
+          if (launch_persist(m->hdesc, m->pp, m->pp.g.G, s->setup, nullptr) != cudaSuccess) {
+            fail_all(s, PYCOOL_E_CUDA);
+            return;
+          }
+          // one grid barrier per pass (the sweeps and the flush, if any)
+          m->pp.bar_base += (unsigned long long)(k + m->pp.flush) * (unsigned long long)m->pp.g.G;
+          m->sweeps_left -= k;
+        }
+        cudaMemcpyAsync(&s->h_bg[slot], m->state + m->L.off_bg, sizeof(Background),
+                        cudaMemcpyDeviceToHost, s->setup);
+        cudaMemcpyAsync(&s->h_fault[slot], m->ws + m->L.off_ticket + 128, sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, s->setup);
+      }
+      if (cudaStreamSynchronize(s->setup) != cudaSuccess) { fail_all(s, PYCOOL_E_CUDA); return; }
+    }
+    // 3. retire finished members (per-stage: record idle after their flush;
+    //    persistent: every sweep and the flush launched), stopped ones (a
+    //    non-finite sum) and cancelled ones (every launch has completed here)
     std::vector<uint64_t> cancel;
     {
       std::lock_guard<std::mutex> lk(s->mu);
@@ -459,11 +543,12 @@ void server_loop(pycool_server* s) {
     }
     for (int slot = 0; slot < s->max_slots; ++slot) {
       if (!s->slots[slot]) continue;
+      const Member& m = *s->slots[slot];
       const Background& b = s->h_bg[slot];
-      const bool cut = std::find(cancel.begin(), cancel.end(), s->slots[slot]->req.ticket) !=
-                       cancel.end();
-      if (b.mode == MODE_IDLE || s->h_fault[slot] || cut)
-        retire(s, slot, b, s->h_fault[slot], cut && b.mode != MODE_IDLE);
+      const bool cut = std::find(cancel.begin(), cancel.end(), m.req.ticket) != cancel.end();
+      const bool done = m.persist ? m.sweeps_left == 0 : b.mode == MODE_IDLE;
+      if (done || b.error || s->h_fault[slot] || cut)
+        retire(s, slot, b, s->h_fault[slot], cut && !done);
     }
   }
 }
@@ -502,7 +587,7 @@ PYCOOL_API pycool_status pycool_server_submit(pycool_server* s, const pycool_con
   if (cfg->precision == PYCOOL_SPLIT_DD) return PYCOOL_E_INVALID;   // no per-stage DD kernel
   if (cfg->model >= kRuntimeModelBase) return PYCOOL_E_INVALID;     // one launch per group only
   if (!std::isfinite(ic->noise) || ic->noise < 0.0) return PYCOOL_E_INVALID;
-  if (footprint(*cfg) > s->arena.capacity()) return PYCOOL_E_NOMEM;  // could never fit
+  if (footprint(s, *cfg) > s->arena.capacity()) return PYCOOL_E_NOMEM;  // could never fit
   Request r;
   r.cfg = *cfg;
   r.ic = *ic;
@@ -558,6 +643,12 @@ PYCOOL_API pycool_status pycool_server_cancel(pycool_server* s, uint64_t ticket)
     s->cancel.push_back(ticket);                  // resident (or being admitted)
   }
   s->cv_work.notify_all();
+  return PYCOOL_OK;
+}
+
+PYCOOL_API pycool_status pycool_server_set_persistent_min_n(pycool_server* s, int32_t n) {
+  if (!s || n < 0 || (n > 0 && (n < 32 || n % 32))) return PYCOOL_E_INVALID;
+  s->persist_min_n.store(n);
   return PYCOOL_OK;
 }
 

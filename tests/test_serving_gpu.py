@@ -32,9 +32,11 @@ def _obs_tuple(e):
             e.sweeps_done)
 
 
-def _run(requests, budget=8 * GB, slots=32):
+def _run(requests, budget=8 * GB, slots=32, persist_min_n=None):
     srv = P.pycool_server_create(budget, slots)
     try:
+        if persist_min_n is not None:
+            P.pycool_server_set_persistent_min_n(srv, persist_min_n)
         tickets = [P.pycool_server_submit(srv, cfg, ic, seed, steps)
                    for (cfg, ic, seed, steps) in requests]
         out = [P.pycool_server_wait(srv, t, 120.0) for t in tickets]
@@ -67,6 +69,87 @@ def test_served_request_matches_oracle(name, n, order):
         assert math.isclose(e.mean[f], m, rel_tol=1e-10, abs_tol=1e-14)
         assert math.isclose(e.variance[f], v, rel_tol=1e-6)
     assert stats["completed"] == 1 and stats["p50_s"] > 0
+
+
+@pytest.mark.parametrize("name,n,order,stencil,steps", [("preheat128", 64, 8, "7pt", 3),
+                                                        ("qball256", 64, 6, "iso27", 4),
+                                                        ("oscillon256", 96, 4, "7pt", 5)])
+def test_persistent_member_matches_oracle(name, n, order, stencil, steps):
+    """An FP64 member on the persistent kernel (the threshold lowered to its
+    side): launches of 8 stage sweeps that end mid-step with the stage boundary
+    pending (45, 28 and 15 sweeps here), the last one with the flush.  The
+    result equals the oracle's on the same device-generated initial fields."""
+    w, cfg, ic = _req(name, n, order, stencil=stencil)
+    seed = 91 + n
+    [(st, e)], stats = _run([(cfg, ic, seed, steps)], persist_min_n=64)
+    assert st == P.OK
+    phi, pi = I.philox_white_ics(n, w["background"], w["momentum"], w["noise"], seed)
+    ocfg = O.LatticeConfig(n=n, L=w["L"], model=w["model"], params=w["params"], dt=w["dt"],
+                           order=order, stencil=stencil, mpl=w["mpl"])
+    s = O.make_state(ocfg, phi, pi)
+    O.evolve(ocfg, s, steps)
+    oe = O.energies(ocfg, s)
+    assert e.steps_done == steps
+    assert e.sweeps_done == steps * P.pycool_stages_per_step(order)   # stage sweeps only
+    for key in ("a", "pa", "rho", "P"):
+        assert math.isclose(getattr(e, key), oe[key], rel_tol=1e-10), key
+    for f in range(len(w["background"])):
+        m, v = O.field_stats(s, f)
+        assert math.isclose(e.mean[f], m, rel_tol=1e-10, abs_tol=1e-14)
+        assert math.isclose(e.variance[f], v, rel_tol=1e-6)
+    assert stats["completed"] == 1
+
+
+def test_persistent_members_bitwise_alone_and_in_mix():
+    """Threshold 64: FP64 members of 64^3, 96^3 and 128^3 run on the persistent
+    kernel, one after another between the per-stage groups' graphs, beside
+    per-stage members of every kind; each persistent member's result alone
+    equals its result in the mix bit for bit."""
+    extra = []
+    for i, (name, n, order) in enumerate([("qball256", 128, 8), ("preheat32", 64, 4),
+                                          ("oscillon256", 64, 6)]):
+        w, cfg, ic = _req(name, n, order)
+        extra.append((cfg, ic, 500 + i, 2 + i))
+    mix = _mix() + extra
+    out, stats = _run(mix, persist_min_n=64)
+    assert all(st == P.OK for st, _ in out) and stats["completed"] == len(mix)
+    persistent = [i for i, (cfg, _, _, _) in enumerate(mix)
+                  if cfg.precision == P.FP64 and cfg.n % 32 == 0 and cfg.n >= 64]
+    assert len(persistent) == 4
+    for i in persistent:
+        [(st, e)], _ = _run([mix[i]], persist_min_n=64)
+        assert st == P.OK
+        assert _obs_tuple(e) == _obs_tuple(out[i][1]), i
+
+
+def test_persistent_member_zero_steps_cancel_and_threshold():
+    """A persistent member with zero steps returns its initial state's
+    observables (the same admission flush as a per-stage member's, so the same
+    bits); a long one is cancelled at a boundary; invalid thresholds are
+    refused."""
+    w, cfg, ic = _req("preheat32", 64, 8)
+    [(st0, e0)], _ = _run([(cfg, ic, 5, 0)], persist_min_n=0)
+    [(st1, e1)], _ = _run([(cfg, ic, 5, 0)], persist_min_n=64)
+    assert st0 == st1 == P.OK and _obs_tuple(e0) == _obs_tuple(e1)
+    srv = P.pycool_server_create(4 * GB, 4)
+    try:
+        for bad in (-32, 16, 48, 100):
+            with pytest.raises(Exception):
+                P.pycool_server_set_persistent_min_n(srv, bad)
+        P.pycool_server_set_persistent_min_n(srv, 64)
+        t = P.pycool_server_submit(srv, cfg, ic, 6, 10 ** 6)
+        import time
+        time.sleep(0.5)
+        assert P.pycool_server_cancel(srv, t) == P.OK
+        st, e = P.pycool_server_wait(srv, t, 60.0)
+        assert st == P.E_CANCELLED
+        assert 0 < e.sweeps_done < 15 * 10 ** 6
+        # the server carries on: a short request after it completes
+        t2 = P.pycool_server_submit(srv, cfg, ic, 7, 2)
+        st2, e2 = P.pycool_server_wait(srv, t2, 60.0)
+        assert st2 == P.OK and e2.steps_done == 2
+    finally:
+        P.pycool_server_destroy(srv)
 
 
 def test_device_initial_conditions_match_numpy_generator():
