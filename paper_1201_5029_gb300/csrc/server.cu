@@ -334,8 +334,10 @@ pycool_status admit(pycool_server* s, const Request& r, int slot) {
     bool fits = false;
     const pycool_status ps =
         persist_setup(r.cfg, m->hdesc, m->L, m->state, m->ws, st, m->pp, &fits);
-    if (ps != PYCOOL_OK) return ps;
-    persist = fits;   // else the per-stage kernels (the layout holds theirs too)
+    if (ps == PYCOOL_E_CUDA) return ps;
+    // a plan the host check refuses, or one block per SM that does not fit:
+    // the per-stage kernels (the layout holds theirs too)
+    persist = ps == PYCOOL_OK && fits;
   }
   if (persist) {
     SCK(cudaStreamSynchronize(st));
